@@ -1,0 +1,333 @@
+"""FDFB oracle (test infrastructure only).
+
+Plain CPU implementation of the paper's method in `fdfb_oracle.c`, wrapped
+with ctypes.  Only the tests, `__graft_entry__.smoke()` and the CPU-baseline
+leg of `bench.py` may use it; the CUDA library never does.  Every array is
+handed to C as uint64 words (w-bit values, w <= 64) or int64 for signed
+quantities.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fdfb_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class or_params(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in
+                ("n", "N", "w", "t", "log2Bg", "lg", "log2Bks", "lks", "log2Bpk", "lpk")]
+
+
+class or_debug(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("ctN", "sgn", "cR", "accF", "accBR", "cQ")]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP for threads over items)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+            sig = {
+                "or_set_threads": ([i32], None),
+                "or_max_threads": ([], i32),
+                "or_poly_mul": ([i32, i32, vp, vp, vp], None),
+                "or_poly_mul_xk": ([i32, i32, vp, i64, vp], None),
+                "or_poly_mul_xk_signed": ([i32, vp, i64, vp], None),
+                "or_decomp_round": ([i32, i32, i32, C.c_uint64], C.c_uint64),
+                "or_decomp": ([i32, i32, i32, C.c_uint64, vp], None),
+                "or_gadget": ([i32, i32, i32, i32], C.c_uint64),
+                "or_lwe_encrypt": ([i32, i32, vp, vp, i64, C.c_uint64, vp], None),
+                "or_lwe_phase": ([i32, i32, vp, vp], C.c_uint64),
+                "or_lwe_decrypt": ([i32, i32, i32, vp, vp], C.c_uint64),
+                "or_rlwe_encrypt": ([i32, i32, vp, vp, vp, vp, vp], None),
+                "or_rlwe_phase": ([i32, i32, vp, vp, vp], None),
+                "or_keygen_bsk": ([vp, vp, vp, vp, vp, vp], None),
+                "or_keygen_pk": ([vp, vp, vp, vp, vp], None),
+                "or_keygen_ksk": ([vp, vp, vp, vp, vp, vp], None),
+                "or_modswitch": ([i32, i32, i32, vp, vp], None),
+                "or_extprod": ([vp, vp, vp, vp], None),
+                "or_cmux": ([vp, vp, vp, vp, vp], None),
+                "or_blind_rotate": ([vp, vp, vp, vp], None),
+                "or_sample_extract": ([i32, i32, vp, i32, vp], None),
+                "or_keyswitch": ([i32, i32, i32, i32, i32, vp, vp, vp], None),
+                "or_setup_polynomial": ([i32, i32, vp, vp, vp], None),
+                "or_pubmux": ([i32, i32, i32, vp, vp, vp, vp], None),
+                "or_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
+                "or_fdfb_batch": ([vp, vp, vp, vp, vp, vp, i64, vp, vp], None),
+                "or_lwe_affine": ([i32, i32, i32, i32, vp, vp, vp], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _u64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x).astype(np.uint64, copy=False))
+
+
+def _i64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x).astype(np.int64, copy=False))
+
+
+def _u8(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x).astype(np.uint8, copy=False))
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
+
+
+def params(ps) -> or_params:
+    return or_params(ps.n, ps.N, ps.w, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks,
+                     ps.log2Bpk, ps.lpk)
+
+
+# --------------------------------------------------------------------------
+# ring arithmetic
+# --------------------------------------------------------------------------
+
+def poly_mul(w: int, a, b) -> np.ndarray:
+    a, b = _u64(a), _u64(b)
+    N = a.shape[-1]
+    out = np.zeros(N, dtype=np.uint64)
+    lib().or_poly_mul(w, N, _p(a), _p(b), _p(out))
+    return out
+
+
+def poly_mul_xk(w: int, p, k: int) -> np.ndarray:
+    p = _u64(p)
+    out = np.zeros_like(p)
+    lib().or_poly_mul_xk(w, p.shape[-1], _p(p), int(k), _p(out))
+    return out
+
+
+def poly_mul_xk_signed(p, k: int) -> np.ndarray:
+    p = _i64(p)
+    out = np.zeros_like(p)
+    lib().or_poly_mul_xk_signed(p.shape[-1], _p(p), int(k), _p(out))
+    return out
+
+
+def decomp(w: int, log2B: int, ell: int, x: int) -> np.ndarray:
+    out = np.zeros(ell, dtype=np.uint64)
+    lib().or_decomp(w, log2B, ell, int(x), _p(out))
+    return out
+
+
+def decomp_round(w: int, log2B: int, ell: int, x: int) -> int:
+    return int(lib().or_decomp_round(w, log2B, ell, int(x)))
+
+
+def gadget(w: int, log2B: int, ell: int, j: int) -> int:
+    return int(lib().or_gadget(w, log2B, ell, j))
+
+
+# --------------------------------------------------------------------------
+# encryption
+# --------------------------------------------------------------------------
+
+def lwe_encrypt(w: int, s, a, e: int, mu: int) -> np.ndarray:
+    s, a = _u8(s), _u64(a)
+    out = np.zeros(len(s) + 1, dtype=np.uint64)
+    lib().or_lwe_encrypt(w, len(s), _p(s), _p(a), int(e), int(mu) & ((1 << 64) - 1), _p(out))
+    return out
+
+
+def lwe_phase(w: int, s, ct) -> int:
+    s, ct = _u8(s), _u64(ct)
+    return int(lib().or_lwe_phase(w, len(s), _p(s), _p(ct)))
+
+
+def lwe_decrypt(w: int, t: int, s, ct) -> int:
+    s, ct = _u8(s), _u64(ct)
+    return int(lib().or_lwe_decrypt(w, len(s), t, _p(s), _p(ct)))
+
+
+def rlwe_encrypt(w: int, sk, a, e, mu=None) -> np.ndarray:
+    sk, a, e = _u8(sk), _u64(a), _i64(e)
+    N = len(sk)
+    out = np.zeros(2 * N, dtype=np.uint64)
+    mu_p = None
+    if mu is not None:
+        mu = _u64(mu)
+        mu_p = _p(mu)
+    lib().or_rlwe_encrypt(w, N, _p(sk), _p(a), _p(e), mu_p, _p(out))
+    return out
+
+
+def rlwe_phase(w: int, sk, ct) -> np.ndarray:
+    sk, ct = _u8(sk), _u64(ct)
+    N = len(sk)
+    out = np.zeros(N, dtype=np.uint64)
+    lib().or_rlwe_phase(w, N, _p(sk), _p(ct), _p(out))
+    return out
+
+
+class Keys:
+    """Oracle key material in canonical layouts (uint64 words)."""
+
+    def __init__(self, ps, kr):
+        P = params(ps)
+        self.ps = ps
+        self.s = _u8(kr.s)
+        self.sk = _u8(kr.sk)
+        n, N = ps.n, ps.N
+        self.bsk = np.zeros((n, 2 * ps.lg, 2, N), dtype=np.uint64)
+        self.pk = np.zeros((N, ps.lpk, 2, N), dtype=np.uint64)
+        self.ksk = np.zeros((N, ps.lks, n + 1), dtype=np.uint64)
+        ba, be = _u64(kr.bsk_a), _i64(kr.bsk_e)
+        lib().or_keygen_bsk(C.byref(P), _p(self.s), _p(self.sk), _p(ba), _p(be), _p(self.bsk))
+        pa, pe = _u64(kr.pk_a), _i64(kr.pk_e)
+        lib().or_keygen_pk(C.byref(P), _p(self.sk), _p(pa), _p(pe), _p(self.pk))
+        ka, ke = _u64(kr.ksk_a), _i64(kr.ksk_e)
+        lib().or_keygen_ksk(C.byref(P), _p(self.sk), _p(self.s), _p(ka), _p(ke), _p(self.ksk))
+
+
+def encrypt_messages(ps, s, mr) -> np.ndarray:
+    """Fresh LWE ciphertexts [count][n+1] of Delta*m with the given randomness."""
+    count = len(mr.m)
+    out = np.zeros((count, ps.n + 1), dtype=np.uint64)
+    for i in range(count):
+        out[i] = lwe_encrypt(ps.w, s, mr.a[i], int(mr.e[i]), (ps.delta * int(mr.m[i])) % (1 << ps.w))
+    return out
+
+
+# --------------------------------------------------------------------------
+# homomorphic primitives
+# --------------------------------------------------------------------------
+
+def modswitch(w: int, k: int, ct) -> np.ndarray:
+    ct = _u64(ct)
+    out = np.zeros_like(ct)
+    lib().or_modswitch(w, k, len(ct) - 1, _p(ct), _p(out))
+    return out
+
+
+def extprod(ps, C_row, d) -> np.ndarray:
+    P = params(ps)
+    C_row, d = _u64(C_row), _u64(d)
+    out = np.zeros(2 * ps.N, dtype=np.uint64)
+    lib().or_extprod(C.byref(P), _p(C_row), _p(d), _p(out))
+    return out
+
+
+def cmux(ps, C_row, g, h) -> np.ndarray:
+    P = params(ps)
+    C_row, g, h = _u64(C_row), _u64(g), _u64(h)
+    out = np.zeros(2 * ps.N, dtype=np.uint64)
+    lib().or_cmux(C.byref(P), _p(C_row), _p(g), _p(h), _p(out))
+    return out
+
+
+def blind_rotate(ps, bsk, acc, ctN) -> np.ndarray:
+    P = params(ps)
+    bsk, ctN = _u64(bsk), _u64(ctN)
+    acc = _u64(acc).copy()
+    lib().or_blind_rotate(C.byref(P), _p(bsk), _p(acc), _p(ctN))
+    return acc
+
+
+def sample_extract(w: int, rlwe, k: int = 0) -> np.ndarray:
+    rlwe = _u64(rlwe)
+    N = len(rlwe) // 2
+    out = np.zeros(N + 1, dtype=np.uint64)
+    lib().or_sample_extract(w, N, _p(rlwe), k, _p(out))
+    return out
+
+
+def keyswitch(w: int, log2B: int, ell: int, key, ct) -> np.ndarray:
+    key, ct = _u64(key), _u64(ct)
+    n_in = len(ct) - 1
+    out_len = key.size // (n_in * ell)
+    out = np.zeros(out_len, dtype=np.uint64)
+    lib().or_keyswitch(w, n_in, log2B, ell, out_len, _p(key), _p(ct), _p(out))
+    return out
+
+
+def setup_polynomial(N: int, t: int, f):
+    f = _i64(f)
+    p0 = np.zeros(N, dtype=np.int64)
+    p1 = np.zeros(N, dtype=np.int64)
+    lib().or_setup_polynomial(N, t, _p(f), _p(p0), _p(p1))
+    return p0, p1
+
+
+def pubmux(w: int, t: int, c, p0, p1) -> np.ndarray:
+    c, p0, p1 = _u64(c), _i64(p0), _i64(p1)
+    N = len(p0)
+    out = np.zeros(2 * N, dtype=np.uint64)
+    lib().or_pubmux(w, N, t, _p(c), _p(p0), _p(p1), _p(out))
+    return out
+
+
+def fdfb_bootstrap(ps, keys: Keys, p0, p1, ct, debug: bool = False):
+    P = params(ps)
+    p0, p1, ct = _i64(p0), _i64(p1), _u64(ct)
+    out = np.zeros(ps.n + 1, dtype=np.uint64)
+    dbg = None
+    d = None
+    if debug:
+        N = ps.N
+        d = {"ctN": np.zeros(ps.n + 1, np.uint64), "sgn": np.zeros(N + 1, np.uint64),
+             "cR": np.zeros(2 * N, np.uint64), "accF": np.zeros(2 * N, np.uint64),
+             "accBR": np.zeros(2 * N, np.uint64), "cQ": np.zeros(N + 1, np.uint64)}
+        dbg = or_debug(*[d[k].ctypes.data for k in ("ctN", "sgn", "cR", "accF", "accBR", "cQ")])
+    lib().or_fdfb_bootstrap(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(p0), _p(p1),
+                            _p(ct), _p(out), C.byref(dbg) if dbg is not None else None)
+    return (out, d) if debug else out
+
+
+def fdfb_batch(ps, keys: Keys, rotP, lut_ids, cts, threads: int | None = None) -> np.ndarray:
+    """rotP: int64[n_luts][2][N]; lut_ids: int32[count]; cts: [count][n+1]."""
+    P = params(ps)
+    rotP, cts = _i64(rotP), _u64(cts)
+    ids = np.ascontiguousarray(np.asarray(lut_ids, dtype=np.int32))
+    out = np.zeros_like(cts)
+    if threads is not None:
+        set_threads(threads)
+    lib().or_fdfb_batch(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(rotP), _p(ids),
+                        len(ids), _p(cts), _p(out))
+    return out
+
+
+def lwe_affine(w: int, W, x) -> np.ndarray:
+    W, x = _i64(W), _u64(x)
+    n_out, n_in = W.shape
+    length = x.shape[1]
+    y = np.zeros((n_out, length), dtype=np.uint64)
+    lib().or_lwe_affine(w, length, n_in, n_out, _p(W), _p(x), _p(y))
+    return y

@@ -1,0 +1,287 @@
+"""Seeded synthetic inputs for FDFB workloads: parameter sets, workload
+definitions and random numbers.  Nothing here computes any part of the
+bootstrapping method (no encryption, no products, no decomposition): this
+module only draws the random numbers that key generation, encryption and the
+workloads consume, so the CUDA library and the CPU oracle can be fed the very
+same inputs.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): with a 64-bit state advanced
+by the odd constant GAMMA, output i of a stream is MIX(state0 + (i+1)*GAMMA),
+where MIX is the published variant-13 finaliser.  Every stream is counter
+based, so any slice can be regenerated without the preceding ones, and the
+bits are identical on every platform and numpy version.
+
+Gaussian noise is the rounded continuous Gaussian e = floor(sigma*z + 1/2),
+z drawn by the Box-Muller transform (Box and Muller, 1958) from two
+independent 53-bit uniforms.  The paper leaves the sampler unspecified
+(section "Parameters, Performance, and Tests" fixes only the standard
+deviation); this is the reading taken.
+
+Parameter sets follow the paper's notation (Table 1): n (LWE dimension),
+N (ring degree), q = 2^w (q = Q here), gadget bases B_g = 2^log2Bg with
+l_g digits for the bootstrapping key, B_ks/l_ks for the LWE key-switching
+key, B_pk/l_pk for the LWE-to-RLWE packing key, plaintext modulus t and the
+noise standard deviations.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_STREAM_MUL = np.uint64(0xD1B54A32D192ED03)
+
+
+@dataclasses.dataclass(frozen=True)
+class ParamSet:
+    """One FDFB parameter set (k = 1, u = {1}, q = Q = 2^w)."""
+    name: str
+    n: int          # LWE dimension
+    N: int          # ring degree, power of two
+    w: int          # word bits, q = 2^w (32 or 64)
+    t: int          # plaintext modulus, power of two
+    log2Bg: int     # bootstrapping-key gadget base
+    lg: int
+    log2Bks: int    # LWE->LWE key-switching gadget base
+    lks: int
+    log2Bpk: int    # LWE->RLWE packing-key gadget base
+    lpk: int
+    sigma_lwe: float   # fresh LWE ciphertexts and the key-switching key
+    sigma_glwe: float  # bootstrapping key and packing key
+
+    @property
+    def logN(self) -> int:
+        return int(self.N).bit_length() - 1
+
+    @property
+    def word_dtype(self):
+        return np.uint32 if self.w == 32 else np.uint64
+
+    @property
+    def delta(self) -> int:
+        return (1 << self.w) // self.t
+
+
+# Sets A-C come straight from the workload list; D and the bold choices of
+# the hot-path scope table (packing-key gadget, sigmas of the 2^64 sets) are
+# readings fixed in the design doc.  Z is the noiseless exact-decomposition set
+# used for the exhaustive correctness pin.
+PARAM_SETS: Dict[str, ParamSet] = {
+    "A": ParamSet("A", n=64, N=256, w=32, t=4, log2Bg=8, lg=3, log2Bks=4, lks=5,
+                  log2Bpk=8, lpk=3, sigma_lwe=2.0 ** 12, sigma_glwe=2.0 ** 7),
+    "B": ParamSet("B", n=630, N=1024, w=32, t=16, log2Bg=7, lg=3, log2Bks=2, lks=8,
+                  log2Bpk=7, lpk=3, sigma_lwe=2.0 ** 12, sigma_glwe=2.0 ** 7),
+    "C": ParamSet("C", n=744, N=4096, w=64, t=64, log2Bg=10, lg=4, log2Bks=3, lks=10,
+                  log2Bpk=10, lpk=4, sigma_lwe=2.0 ** 24, sigma_glwe=2.0 ** 14),
+    "D": ParamSet("D", n=744, N=2048, w=64, t=32, log2Bg=10, lg=4, log2Bks=3, lks=10,
+                  log2Bpk=10, lpk=4, sigma_lwe=2.0 ** 24, sigma_glwe=2.0 ** 14),
+    "Z": ParamSet("Z", n=16, N=256, w=32, t=4, log2Bg=8, lg=4, log2Bks=4, lks=8,
+                  log2Bpk=8, lpk=4, sigma_lwe=0.0, sigma_glwe=0.0),
+}
+
+
+@dataclasses.dataclass(frozen=True)
+class Group:
+    """A batch of ciphertexts under one parameter set."""
+    set_name: str
+    batch: int
+    n_luts: int
+    lut_assign: str   # "round_robin" or "uniform"
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    seed: int
+    groups: List[Group]
+    mlp_layers: Optional[List[int]] = None   # config 5 only
+    mlp_inputs: int = 0
+
+
+# Workloads: workload k uses master seed k-1.
+WORKLOADS: Dict[str, Workload] = {
+    "toy": Workload("toy", 0, [Group("A", 16, 1, "round_robin")]),
+    "tfhe_scale": Workload("tfhe_scale", 1, [Group("B", 1024, 4, "round_robin")]),
+    "large_t": Workload("large_t", 2, [Group("C", 4096, 16, "uniform")]),
+    "mixed": Workload("mixed", 3, [Group("B", 37, 4, "uniform"),
+                                   Group("D", 1000, 4, "uniform"),
+                                   Group("C", 2900, 4, "uniform")]),
+    "mlp": Workload("mlp", 4, [Group("D", 0, 2, "uniform")],
+                    mlp_layers=[784, 128, 64, 10], mlp_inputs=64),
+}
+
+# Sub-stream identifiers (xored into the master seed before mixing).
+STREAM_KEYS = 1
+STREAM_MESSAGES = 2
+STREAM_LUTS = 3
+STREAM_LUT_ASSIGN = 4
+STREAM_MLP = 5
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+class Stream:
+    """A SplitMix64 stream keyed by (master seed, path of stream ids)."""
+
+    def __init__(self, seed: int, *path: int):
+        with np.errstate(over="ignore"):
+            s = _mix64(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))
+            for p in path:
+                s = _mix64(s ^ (np.uint64(p & 0xFFFFFFFFFFFFFFFF) * _STREAM_MUL))
+        self.state0 = s[0]
+
+    def sub(self, *path: int) -> "Stream":
+        st = Stream.__new__(Stream)
+        s = np.array([self.state0], dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            for p in path:
+                s = _mix64(s ^ (np.uint64(p & 0xFFFFFFFFFFFFFFFF) * _STREAM_MUL))
+        st.state0 = s[0]
+        return st
+
+    def raw(self, count: int, start: int = 0) -> np.ndarray:
+        """Outputs start .. start+count-1 of the stream as uint64."""
+        out = np.empty(count, dtype=np.uint64)
+        chunk = 1 << 22
+        with np.errstate(over="ignore"):
+            for lo in range(0, count, chunk):
+                hi = min(count, lo + chunk)
+                idx = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
+                out[lo:hi] = _mix64(self.state0 + idx * GAMMA)
+        return out
+
+    def words(self, count: int, w: int) -> np.ndarray:
+        """Uniform words of Z_{2^w}, dtype uint32 (w=32) or uint64 (w=64)."""
+        r = self.raw(count)
+        if w == 64:
+            return r
+        return (r >> np.uint64(64 - w)).astype(np.uint64 if w > 32 else np.uint32)
+
+    def bits(self, count: int) -> np.ndarray:
+        return (self.raw(count) >> np.uint64(63)).astype(np.uint8)
+
+    def below(self, count: int, m: int) -> np.ndarray:
+        """Integers uniform in [0, m) for m < 2^32 (multiply-high method)."""
+        assert 0 < m < (1 << 32)
+        r = self.raw(count) >> np.uint64(32)
+        return ((r * np.uint64(m)) >> np.uint64(32)).astype(np.int64)
+
+    def uniform01(self, count: int, start: int = 0) -> np.ndarray:
+        """Doubles in (0, 1]: ((x >> 11) + 1) * 2^-53."""
+        r = self.raw(count, start)
+        return ((r >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+
+    def gaussian(self, count: int, sigma: float) -> np.ndarray:
+        """Rounded Gaussian integers floor(sigma*z + 1/2), int64."""
+        if sigma == 0.0 or count == 0:
+            return np.zeros(count, dtype=np.int64)
+        out = np.empty(count, dtype=np.int64)
+        chunk = 1 << 22
+        for lo in range(0, count, chunk):
+            hi = min(count, lo + chunk)
+            u = self.uniform01(2 * (hi - lo), 2 * lo)
+            u1, u2 = u[0::2], u[1::2]
+            z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+            out[lo:hi] = np.floor(sigma * z + 0.5).astype(np.int64)
+        return out
+
+
+@dataclasses.dataclass
+class KeyRandomness:
+    """Everything key generation draws, for one parameter set.
+
+    s      : uint8[n]              binary LWE secret key
+    sk     : uint8[N]              binary RLWE secret key (s_F = its coefficients)
+    bsk_a  : word[n][2*lg][N]      uniform masks of the GGSW rows
+    bsk_e  : int64[n][2*lg][N]     noise of the GGSW rows
+    pk_a   : word[N][lpk][N]       uniform masks of the packing key
+    pk_e   : int64[N][lpk][N]
+    ksk_a  : word[N][lks][n]       uniform masks of the key-switching key
+    ksk_e  : int64[N][lks]
+    """
+    s: np.ndarray
+    sk: np.ndarray
+    bsk_a: np.ndarray
+    bsk_e: np.ndarray
+    pk_a: np.ndarray
+    pk_e: np.ndarray
+    ksk_a: np.ndarray
+    ksk_e: np.ndarray
+
+
+def key_randomness(ps: ParamSet, seed: int) -> KeyRandomness:
+    st = Stream(seed, STREAM_KEYS, hash_name(ps.name))
+    n, N = ps.n, ps.N
+    s = st.sub(1).bits(n)
+    sk = st.sub(2).bits(N)
+    bsk_a = st.sub(3).words(n * 2 * ps.lg * N, ps.w).reshape(n, 2 * ps.lg, N)
+    bsk_e = st.sub(4).gaussian(n * 2 * ps.lg * N, ps.sigma_glwe).reshape(n, 2 * ps.lg, N)
+    pk_a = st.sub(5).words(N * ps.lpk * N, ps.w).reshape(N, ps.lpk, N)
+    pk_e = st.sub(6).gaussian(N * ps.lpk * N, ps.sigma_glwe).reshape(N, ps.lpk, N)
+    ksk_a = st.sub(7).words(N * ps.lks * n, ps.w).reshape(N, ps.lks, n)
+    ksk_e = st.sub(8).gaussian(N * ps.lks, ps.sigma_lwe).reshape(N, ps.lks)
+    return KeyRandomness(s, sk, bsk_a, bsk_e, pk_a, pk_e, ksk_a, ksk_e)
+
+
+def hash_name(name: str) -> int:
+    h = 0
+    for ch in name.encode():
+        h = (h * 131 + ch) & 0xFFFFFFFF
+    return h
+
+
+@dataclasses.dataclass
+class MessageRandomness:
+    """Plaintexts and encryption randomness of a batch of fresh LWE ciphertexts.
+
+    m : int64[count]        messages in Z_t
+    a : word[count][n]      uniform masks
+    e : int64[count]        noise
+    """
+    m: np.ndarray
+    a: np.ndarray
+    e: np.ndarray
+
+
+def message_randomness(ps: ParamSet, seed: int, count: int, group: int = 0,
+                       m: Optional[np.ndarray] = None) -> MessageRandomness:
+    st = Stream(seed, STREAM_MESSAGES, hash_name(ps.name), group)
+    if m is None:
+        m = st.sub(1).below(count, ps.t)
+    a = st.sub(2).words(count * ps.n, ps.w).reshape(count, ps.n)
+    e = st.sub(3).gaussian(count, ps.sigma_lwe)
+    return MessageRandomness(np.asarray(m, dtype=np.int64), a, e)
+
+
+def lut_tables(ps: ParamSet, seed: int, count: int, group: int = 0) -> np.ndarray:
+    """`count` random lookup tables f: Z_t -> Z_t, int64[count][t]."""
+    st = Stream(seed, STREAM_LUTS, hash_name(ps.name), group)
+    return st.below(count * ps.t, ps.t).reshape(count, ps.t)
+
+
+def lut_assignment(seed: int, count: int, n_luts: int, how: str, group: int = 0) -> np.ndarray:
+    if how == "round_robin":
+        return (np.arange(count) % n_luts).astype(np.int32)
+    st = Stream(seed, STREAM_LUT_ASSIGN, group)
+    return st.below(count, n_luts).astype(np.int32)
+
+
+def mlp_inputs_and_weights(seed: int, layers: List[int], n_inputs: int):
+    """Pixels uniform in Z_16 and integer weights uniform in [-8, 7]."""
+    st = Stream(seed, STREAM_MLP)
+    x = st.sub(0).below(n_inputs * layers[0], 16).reshape(n_inputs, layers[0])
+    ws = []
+    for i in range(len(layers) - 1):
+        w = st.sub(1 + i).below(layers[i + 1] * layers[i], 16).reshape(layers[i + 1], layers[i]) - 8
+        ws.append(w.astype(np.int64))
+    return x.astype(np.int64), ws

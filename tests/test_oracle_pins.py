@@ -1,0 +1,413 @@
+"""Pins for the CPU oracle: each test checks an oracle function against
+something other than itself -- a closed form, an invariant the paper states,
+an independent exact method, brute force on tiny inputs, or the paper's own
+correctness theorems -- chosen so that a dropped term, a wrong sign or index
+or a transposed operand fails at least one of them.  No GPU needed.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_2109_02731_gb300 import synth as S
+
+W32, W64 = 32, 64
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def rand_words(r, w, size):
+    if w == 64:
+        return r.integers(0, 1 << 63, size=size, dtype=np.uint64) * np.uint64(2) + \
+            r.integers(0, 2, size=size, dtype=np.uint64)
+    return r.integers(0, 1 << w, size=size, dtype=np.uint64)
+
+
+def kronecker_negacyclic(a, b, w):
+    """Independent exact product in Z_{2^w}[X]/(X^N+1): pack both operands
+    into big integers (Kronecker substitution), multiply with Python's
+    arbitrary-precision integers, unpack the 2N-1 coefficients of the plain
+    product and fold the upper half back with X^N = -1."""
+    N = len(a)
+    slot = 2 * w + N.bit_length() + 2
+    A = 0
+    B = 0
+    for i in reversed(range(N)):
+        A = (A << slot) | int(a[i])
+        B = (B << slot) | int(b[i])
+    Cp = A * B
+    mask = (1 << slot) - 1
+    c = [(Cp >> (slot * k)) & mask for k in range(2 * N)]
+    return np.array([(c[k] - c[k + N]) % (1 << w) for k in range(N)], dtype=np.uint64)
+
+
+def monomial(N, k, w):
+    """X^k as a coefficient vector from the closed form X^N = -1, X^{2N} = 1."""
+    k %= 2 * N
+    v = np.zeros(N, dtype=np.uint64)
+    if k < N:
+        v[k] = 1
+    else:
+        v[k - N] = (1 << w) - 1
+    return v
+
+
+# ---------------------------------------------------------------- ring ------
+
+@pytest.mark.parametrize("w", [W32, W64])
+def test_xn_is_minus_one(oracle, w):
+    N = 64
+    x = monomial(N, 1, w)
+    xn1 = monomial(N, N - 1, w)
+    prod = oracle.poly_mul(w, xn1, x)
+    expect = np.zeros(N, np.uint64)
+    expect[0] = (1 << w) - 1
+    assert np.array_equal(prod, expect)
+    one = np.zeros(N, np.uint64)
+    one[0] = 1
+    assert np.array_equal(oracle.poly_mul_xk(w, one, 2 * N), one)
+    assert np.array_equal(oracle.poly_mul_xk(w, one, N), expect)
+
+
+@pytest.mark.parametrize("w,N", [(W32, 16), (W32, 256), (W64, 64), (W64, 256), (12, 32)])
+def test_poly_mul_matches_kronecker(oracle, w, N):
+    r = rng(N + w)
+    for _ in range(3):
+        a = rand_words(r, w, N)
+        b = rand_words(r, w, N)
+        assert np.array_equal(oracle.poly_mul(w, a, b), kronecker_negacyclic(a, b, w))
+
+
+@pytest.mark.parametrize("w", [W32, W64])
+def test_monomial_rotation_group(oracle, w):
+    N = 32
+    r = rng(5)
+    p = rand_words(r, w, N)
+    for k in list(range(-2 * N - 3, 3 * N + 3, 7)) + [0, N, 2 * N, -N]:
+        via_mul = oracle.poly_mul(w, p, monomial(N, k, w))
+        assert np.array_equal(oracle.poly_mul_xk(w, p, k), via_mul), k
+    for a, b in [(3, 5), (N - 1, N + 2), (2 * N - 1, 2 * N - 1), (-7, 11)]:
+        lhs = oracle.poly_mul_xk(w, oracle.poly_mul_xk(w, p, a), b)
+        assert np.array_equal(lhs, oracle.poly_mul_xk(w, p, a + b))
+    mask = np.uint64((1 << w) - 1)
+    ps = np.arange(N, dtype=np.int64) - 10
+    for k in (0, 1, N - 1, N, N + 3, 2 * N - 1, -5):
+        got = oracle.poly_mul_xk_signed(ps, k)
+        ref = oracle.poly_mul_xk(w, ps.astype(np.uint64) & mask, k)
+        assert np.array_equal(got.astype(np.uint64) & mask, ref)
+
+
+def test_poly_mul_ring_axioms(oracle):
+    w, N = W64, 128
+    r = rng(9)
+    a, b, c = (rand_words(r, w, N) for _ in range(3))
+    assert np.array_equal(oracle.poly_mul(w, a, b), oracle.poly_mul(w, b, a))
+    lhs = oracle.poly_mul(w, a, (b + c))
+    rhs = oracle.poly_mul(w, a, b) + oracle.poly_mul(w, a, c)
+    assert np.array_equal(lhs, rhs)
+
+
+# ----------------------------------------------------------- decomposition --
+
+def test_decomp_closed_form_exact(oracle):
+    # exact base-256 digits of a 32-bit word, least significant first
+    d = oracle.decomp(32, 8, 4, 0x12345678)
+    assert list(d) == [0x78, 0x56, 0x34, 0x12]
+    assert [oracle.gadget(32, 8, 4, j) for j in range(4)] == [1, 1 << 8, 1 << 16, 1 << 24]
+    # truncated: l*beta = 24 < 32 keeps the top 24 bits, rounded half up
+    assert list(oracle.decomp(32, 8, 3, 0x12345678)) == [0x56, 0x34, 0x12]
+    assert list(oracle.decomp(32, 8, 3, 0x12345680)) == [0x57, 0x34, 0x12]
+    assert list(oracle.decomp(32, 8, 3, 0xFFFFFF80)) == [0, 0, 0]  # wraps to 0
+    assert [oracle.gadget(32, 8, 3, j) for j in range(3)] == [1 << 8, 1 << 16, 1 << 24]
+
+
+@pytest.mark.parametrize("log2B,ell", [(3, 2), (2, 3), (4, 3), (3, 4), (5, 2), (4, 2), (1, 7)])
+def test_decomp_recomposition_exhaustive_w12(oracle, log2B, ell):
+    w = 12
+    q = 1 << w
+    r = max(0, w - ell * log2B)
+    g = [oracle.gadget(w, log2B, ell, j) for j in range(ell)]
+    for x in range(q):
+        d = oracle.decomp(w, log2B, ell, x)
+        assert all(0 <= int(v) < (1 << log2B) for v in d)
+        rec = sum(int(v) * gj for v, gj in zip(d, g)) % q
+        eps = (x - rec) % q
+        if eps >= q // 2:
+            eps -= q
+        if r == 0:
+            assert eps == 0
+        else:
+            assert -(1 << (r - 1)) <= eps < (1 << (r - 1)), (x, eps)
+
+
+@pytest.mark.parametrize("w,log2B,ell", [(32, 7, 3), (32, 8, 3), (32, 2, 8), (64, 10, 4), (64, 3, 10),
+                                         (32, 8, 4), (64, 16, 4)])
+def test_decomp_recomposition_random(oracle, w, log2B, ell):
+    q = 1 << w
+    r = max(0, w - ell * log2B)
+    g = [oracle.gadget(w, log2B, ell, j) for j in range(ell)]
+    for x in rand_words(rng(w * ell), w, 300):
+        d = oracle.decomp(w, log2B, ell, int(x))
+        rec = sum(int(v) * gj for v, gj in zip(d, g)) % q
+        eps = (int(x) - rec) % q
+        if eps >= q // 2:
+            eps -= q
+        bound = (1 << (r - 1)) if r else 0
+        assert -bound <= eps <= max(0, bound - 1)
+
+
+# ------------------------------------------------------------- encryption ---
+
+@pytest.mark.parametrize("w", [W32, W64])
+def test_lwe_rlwe_phase_is_message_plus_error(oracle, w):
+    r = rng(1)
+    n, N = 40, 64
+    s = r.integers(0, 2, n).astype(np.uint8)
+    a = rand_words(r, w, n)
+    ct = oracle.lwe_encrypt(w, s, a, -37, 12345)
+    assert oracle.lwe_phase(w, s, ct) == (12345 - 37) % (1 << w)
+    sk = r.integers(0, 2, N).astype(np.uint8)
+    a = rand_words(r, w, N)
+    e = r.integers(-100, 100, N)
+    mu = rand_words(r, w, N)
+    c = oracle.rlwe_encrypt(w, sk, a, e, mu)
+    ph = oracle.rlwe_phase(w, sk, c)
+    assert np.array_equal(ph, (mu + e.astype(np.uint64)) & np.uint64((1 << w) - 1))
+    # b = a*sk + e + mu against the independent product
+    b = (kronecker_negacyclic(a, sk.astype(np.uint64), w) + e.astype(np.uint64) + mu)
+    if w < 64:
+        b &= np.uint64((1 << w) - 1)
+    assert np.array_equal(c[:N], b)
+
+
+# -------------------------------------------------------- sample extract ----
+
+@pytest.mark.parametrize("w", [W32, W64])
+def test_sample_extract_phase_identity(oracle, w):
+    """Lemma 'Correctness of Sample Extraction' is an exact identity: the
+    extracted LWE phase under Coefs(sk) is coefficient k of the RLWE phase."""
+    r = rng(2)
+    N = 64
+    sk = r.integers(0, 2, N).astype(np.uint8)
+    for trial in range(3):
+        c = rand_words(r, w, 2 * N)
+        ph = oracle.rlwe_phase(w, sk, c)
+        for k in range(N):
+            lwe = oracle.sample_extract(w, c, k)
+            assert oracle.lwe_phase(w, sk, lwe) == int(ph[k])
+
+
+# ----------------------------------------------------------- key switching --
+
+def _tiny_keys(oracle, ps, seed=0):
+    return oracle.Keys(ps, S.key_randomness(ps, seed))
+
+
+def test_keyswitch_exact_phase_noiseless(oracle):
+    """Noiseless keys and exact decomposition: KeySwitch preserves the phase
+    exactly (proof of Lemma 'Correctness of Key Switching')."""
+    ps = S.PARAM_SETS["Z"]
+    k = _tiny_keys(oracle, ps)
+    r = rng(3)
+    sF = k.sk
+    for _ in range(5):
+        ct = rand_words(r, ps.w, ps.N + 1)
+        ph = oracle.lwe_phase(ps.w, sF, ct)
+        out = oracle.keyswitch(ps.w, ps.log2Bks, ps.lks, k.ksk, ct)
+        assert oracle.lwe_phase(ps.w, k.s, out) == ph
+        outR = oracle.keyswitch(ps.w, ps.log2Bpk, ps.lpk, k.pk, ct)
+        phR = oracle.rlwe_phase(ps.w, k.sk, outR)
+        assert int(phR[0]) == ph and not phR[1:].any()
+
+
+def test_keyswitch_noise_within_lemma(oracle):
+    """Lemma 'Correctness of Key Switching': error variance <= B_c +
+    (1/3) n l B^2 B_ksK, plus the truncation term n * 4^r / 12 * E[s]."""
+    ps = S.PARAM_SETS["A"]
+    k = _tiny_keys(oracle, ps, 1)
+    r = rng(4)
+    errs = []
+    for _ in range(60):
+        mu = int(r.integers(0, ps.t)) * ps.delta
+        ct = oracle.lwe_encrypt(ps.w, k.sk, rand_words(r, ps.w, ps.N), 0, mu)
+        out = oracle.keyswitch(ps.w, ps.log2Bks, ps.lks, k.ksk, ct)
+        e = (oracle.lwe_phase(ps.w, k.s, out) - mu) % (1 << ps.w)
+        if e >= 1 << (ps.w - 1):
+            e -= 1 << ps.w
+        errs.append(e)
+    var = np.var(np.array(errs, dtype=np.float64)) + np.mean(np.array(errs, dtype=np.float64)) ** 2
+    rbits = ps.w - ps.lks * ps.log2Bks
+    bound = (1 / 3) * ps.N * ps.lks * (1 << ps.log2Bks) ** 2 * ps.sigma_lwe ** 2 \
+        + ps.N * (4.0 ** rbits) / 12 * 0.5
+    assert var <= 1.5 * bound
+    assert var >= bound / 16
+
+
+# ------------------------------------------------- external product / CMux --
+
+def _rgsw_noiseless(oracle, ps, sk, mbit, r):
+    """RGSW(m) with sigma = 0 (Definition 'Generalized-GSW Sample')."""
+    N, l = ps.N, ps.lg
+    rows = np.zeros((2 * l, 2, N), dtype=np.uint64)
+    for row in range(2 * l):
+        c = oracle.rlwe_encrypt(ps.w, sk, rand_words(r, ps.w, N), np.zeros(N, np.int64))
+        c = c.reshape(2, N)
+        cc, j = row // l, row % l
+        c[cc, 0] = (int(c[cc, 0]) + mbit * oracle.gadget(ps.w, ps.log2Bg, l, j)) % (1 << ps.w)
+        rows[row] = c
+    return rows
+
+
+def test_cmux_selects_exactly_noiseless(oracle):
+    ps = S.PARAM_SETS["Z"]
+    r = rng(6)
+    sk = r.integers(0, 2, ps.N).astype(np.uint8)
+    for mbit in (0, 1):
+        C = _rgsw_noiseless(oracle, ps, sk, mbit, r)
+        g = rand_words(r, ps.w, 2 * ps.N)
+        h = rand_words(r, ps.w, 2 * ps.N)
+        out = oracle.cmux(ps, C, g, h)
+        want = g if mbit else h
+        assert np.array_equal(oracle.rlwe_phase(ps.w, sk, out), oracle.rlwe_phase(ps.w, sk, want))
+
+
+def test_blind_rotate_noiseless_is_monomial_rotation(oracle):
+    """Noiseless BR of a trivial accumulator (v, 0) by ct_N gives an RLWE of
+    v * X^{-<a, s>} exactly (Lemma 'Correctness of TFHE-Style Blind-Rotation'
+    under reading G4)."""
+    ps = S.PARAM_SETS["Z"]
+    k = _tiny_keys(oracle, ps, 3)
+    r = rng(7)
+    N = ps.N
+    for _ in range(2):
+        v = rand_words(r, ps.w, N)
+        acc = np.concatenate([v, np.zeros(N, np.uint64)])
+        ctN = r.integers(0, 2 * N, ps.n + 1).astype(np.uint64)
+        out = oracle.blind_rotate(ps, k.bsk, acc, ctN)
+        rot = -int(np.dot(ctN[1:].astype(np.int64), k.s.astype(np.int64)))
+        assert np.array_equal(oracle.rlwe_phase(ps.w, k.sk, out), oracle.poly_mul_xk(ps.w, v, rot))
+
+
+def test_blind_rotate_noise_within_lemma(oracle):
+    """Error variance of BR vs Lemma 'Correctness of TFHE-Style Blind-Rotation'
+    (2/3 n N l B^2 B_brK) plus the truncation term of our decomposition."""
+    ps = S.PARAM_SETS["A"]
+    k = _tiny_keys(oracle, ps, 4)
+    r = rng(8)
+    N = ps.N
+    errs = []
+    for _ in range(4):
+        v = rand_words(r, ps.w, N)
+        acc = np.concatenate([v, np.zeros(N, np.uint64)])
+        ctN = r.integers(0, 2 * N, ps.n + 1).astype(np.uint64)
+        out = oracle.blind_rotate(ps, k.bsk, acc, ctN)
+        rot = -int(np.dot(ctN[1:].astype(np.int64), k.s.astype(np.int64)))
+        e = (oracle.rlwe_phase(ps.w, k.sk, out) - oracle.poly_mul_xk(ps.w, v, rot)).astype(np.int64)
+        errs.append(e.astype(np.int32).astype(np.float64))   # centred in 32 bits
+    var = float(np.mean(np.concatenate(errs) ** 2))
+    rb = ps.w - ps.lg * ps.log2Bg
+    B2 = (1 << ps.log2Bg) ** 2
+    bound = (2 / 3) * ps.n * N * ps.lg * B2 * ps.sigma_glwe ** 2 \
+        + ps.n * (N * 0.5 + 1) * (4.0 ** rb) / 12 * 2
+    assert var <= 1.5 * bound
+    assert var >= bound / 64
+
+
+# ------------------------------------------------------------- mod switch ---
+
+def test_modswitch_rounding_and_error(oracle):
+    w, k = 32, 9
+    # round half up at the exact midpoint, and wrap-around at the top
+    half = 1 << (w - k - 1)
+    assert list(oracle.modswitch(w, k, [half - 1, half, (1 << w) - 1])) == [0, 1, 0]
+    r = rng(10)
+    n = 50
+    s = r.integers(0, 2, n).astype(np.uint8)
+    for _ in range(50):
+        ph_target = int(r.integers(0, 1 << w))
+        ct = oracle.lwe_encrypt(w, s, rand_words(r, w, n), 0, ph_target)
+        ctN = oracle.modswitch(w, k, ct)
+        phN = (int(ctN[0]) - int(np.dot(ctN[1:].astype(np.int64), s.astype(np.int64)))) % (1 << k)
+        err = (phN - ph_target * (1 << k) / (1 << w)) % (1 << k)
+        if err > (1 << (k - 1)):
+            err -= 1 << k
+        assert abs(err) <= (1 + int(s.sum())) / 2
+
+
+# ------------------------------------------------------ SetupPolynomial -----
+
+@pytest.mark.parametrize("N,t", [(256, 4), (64, 8), (1024, 16), (128, 32), (64, 64)])
+def test_setup_polynomial_theorem_bruteforce(oracle, N, t):
+    """Theorem 'rotation-polynomial-correctness': for every m and every e with
+    |e| < N/t, coefficient 0 of rotP_0 * X^y (y in [0,N)) or rotP_1 * X^y
+    (y in [N,2N)) equals f(m)."""
+    r = rng(N * t)
+    for trial in range(3):
+        f = r.integers(0, t, t)
+        p0, p1 = oracle.setup_polynomial(N, t, f)
+        step = 2 * N // t
+        E = N // t
+        for m in range(t):
+            for e in range(-E + 1, E):
+                y = (step * m + e) % (2 * N)
+                p = p0 if y < N else p1
+                assert oracle.poly_mul_xk_signed(p, y)[0] == f[m], (m, e)
+
+
+def test_setup_polynomial_tie_rules(oracle):
+    """Reading G8: windows overlap at y = step*m + N/t; the later write (m+1)
+    wins inside, and m = t-1 wins at the wrap y = 2N - N/t."""
+    N, t = 64, 8
+    f = np.array([11, 12, 13, 14, 15, 16, 17, 18])
+    p0, p1 = oracle.setup_polynomial(N, t, f)
+    step, E = 2 * N // t, N // t
+    for m in range(t - 1):
+        y = step * m + E
+        p = p0 if y < N else p1
+        assert oracle.poly_mul_xk_signed(p, y)[0] == f[m + 1]
+    y = 2 * N - E
+    assert oracle.poly_mul_xk_signed(p1, y)[0] == f[t - 1]
+    # every slot is written, and by the sign pattern of the construction
+    assert (p0[1:] <= 0).all() and p0[0] >= 0 and (p1[1:] >= 0).all() and p1[0] <= 0
+
+
+# -------------------------------------------------------------- whole FDFB --
+
+def test_fdfb_noiseless_exhaustive(oracle):
+    """Theorem 'Correctness of the Bootstrapping' at sigma = 0 with exact
+    decompositions: for all m in Z_4 (both halves of the torus) and all 256
+    functions f: Z_4 -> Z_4 the output phase is exactly Delta * f(m)."""
+    ps = S.PARAM_SETS["Z"]
+    k = _tiny_keys(oracle, ps, 0)
+    t = ps.t
+    fs = np.array(list(itertools.product(range(t), repeat=t)), dtype=np.int64)   # 256 x 4
+    rot = np.zeros((len(fs), 2, ps.N), dtype=np.int64)
+    for i, f in enumerate(fs):
+        rot[i, 0], rot[i, 1] = oracle.setup_polynomial(ps.N, t, f)
+    ms = np.tile(np.arange(t), len(fs))
+    ids = np.repeat(np.arange(len(fs)), t).astype(np.int32)
+    mr = S.message_randomness(ps, 0, len(ms), m=ms)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
+    for c in range(len(ms)):
+        want = (ps.delta * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
+
+
+def test_fdfb_toy_decrypts(oracle):
+    """Toy workload (set A, seed 0): every output decrypts to f(m)."""
+    wl = S.WORKLOADS["toy"]
+    g = wl.groups[0]
+    ps = S.PARAM_SETS[g.set_name]
+    k = _tiny_keys(oracle, ps, wl.seed)
+    fs = S.lut_tables(ps, wl.seed, g.n_luts)
+    rot = np.stack([np.stack(oracle.setup_polynomial(ps.N, ps.t, f)) for f in fs])
+    ids = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign)
+    mr = S.message_randomness(ps, wl.seed, g.batch)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
+    got = [oracle.lwe_decrypt(ps.w, ps.t, k.s, o) for o in outs]
+    want = [int(fs[i][m]) for i, m in zip(ids, mr.m)]
+    assert got == want
