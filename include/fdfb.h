@@ -1,0 +1,229 @@
+/*
+ * fdfb.h -- C ABI of the GB300 library for full-domain functional
+ * bootstrapping (FDFB, Kluczniak and Schild, arXiv 2109.02731).
+ *
+ * The library evaluates an arbitrary lookup table f: Z_t -> Z_t on LWE
+ * ciphertexts, on the whole plaintext domain including its negacyclic half
+ * (Section 3, figure "functional-bootstrapping").  One bootstrap is
+ *   ModSwitch(q -> 2N); sign BlindRotate; SampleExtract + Delta/2;
+ *   BuildAcc = KeySwitch(LWE -> RLWE, pK) then PubMux of the two rotation
+ *   polynomials; function BlindRotate; SampleExtract; KeySwitch(ksK).
+ * All arithmetic is exact integer arithmetic modulo q = 2^w (w = 32 or 64):
+ * results are bit-for-bit those of the paper's algorithm under the readings
+ * stated with each call.
+ *
+ * Conventions (all calls):
+ *   - Words are little-endian uint32_t (log2q = 32) or uint64_t (log2q = 64)
+ *     holding residues mod q.  An LWE ciphertext is [b, a_1 .. a_n] with
+ *     b = <a, s> + e + m (Definition "Generalized Learning With Errors"); an
+ *     RLWE ciphertext is the two polynomials [b, a] of N words each, every
+ *     polynomial in ascending powers of X (Coefs()).
+ *   - k = 1 (RLWE) and u = {1} (binary LWE key): the paper's Table 1 setting.
+ *   - Gadget decomposition is unsigned and truncated: with r = max(0, w -
+ *     l*log2B), a word x is rounded to x~ = ((x + 2^(r-1)) mod q) >> r and
+ *     split into l base-B digits, least significant first, against the gadget
+ *     values B^(j-1) 2^r (Definitions "Gadget Matrix" and "Decomposition").
+ *     With l*log2B >= w this is the paper's exact decomposition.
+ *   - Pointers documented as "device" must be device memory of the context's
+ *     GPU; "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library owns keys, lookup tables and its scratch.
+ *   - Every call that takes a stream (a cudaStream_t passed as void*, NULL =
+ *     legacy default stream) is asynchronous and stream ordered.  Argument
+ *     errors are returned synchronously; device-side errors are latched and
+ *     reported by fdfb_sync().
+ *   - Return value: FDFB_OK (0) or a negative FDFB_E* code (fdfb_strerror).
+ *   - There is no CPU fallback: without a usable GPU, fdfb_create fails.
+ */
+#ifndef FDFB_H
+#define FDFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FDFB_OK = 0,
+  FDFB_EINVAL = -1,    /* bad argument, unsupported parameters or sizes */
+  FDFB_ENOMEM = -2,    /* device allocation failed */
+  FDFB_ECUDA = -3,     /* a CUDA runtime call failed */
+  FDFB_ETIMEOUT = -4,  /* a bounded device-side wait expired */
+  FDFB_ENOKEYS = -5,   /* keys of the parameter set were never installed */
+  FDFB_EBADLUT = -6    /* unknown lookup-table id, or table entry outside Z_t */
+};
+
+typedef struct fdfb_ctx fdfb_ctx;
+
+/* One parameter set (paper notation, Table 1).  k must be 1; log2q is 32 or
+ * 64 (q = Q: the final ModSwitch Q -> q of the Bootstrap figure is the
+ * identity).  t is a power of two with 2 <= t <= N.  log2Lboot / lboot
+ * describe the PubMux decomposition of Bootstrap step "l_boot"; the library
+ * implements L_boot = t, l_boot = 1 (log2Lboot = log2 t, lboot = 1): one sign
+ * blind rotation, and the PubMux selector (p_1 - p_0) mod t is one digit. */
+typedef struct {
+  uint32_t n, N, k, log2q, t;
+  uint32_t log2Bg, lg;     /* bootstrapping-key gadget: base 2^log2Bg, lg digits (lg <= 4) */
+  uint32_t log2Bks, lks;   /* LWE->LWE key-switching gadget */
+  uint32_t log2Bpk, lpk;   /* LWE->RLWE packing-key gadget */
+  uint32_t log2Lboot, lboot;
+} fdfb_params;
+
+/* Creates a context on CUDA device `device`.  *out receives the handle. */
+int fdfb_create(fdfb_ctx** out, int device);
+
+/* Destroys the context and frees every device buffer it owns.  The caller
+ * must make sure no work of the context is still running. */
+int fdfb_destroy(fdfb_ctx* ctx);
+
+/* Registers a parameter set; *set_id_out receives its id.  Fails with
+ * FDFB_EINVAL for unsupported shapes: N not in {256, 512, 1024, 2048, 4096},
+ * n > 4096, lg > 4, or a negacyclic product whose exact value could exceed
+ * what the library's primes lift exactly. */
+int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out);
+
+/* Size in words of each key in its canonical layout (what keys_upload reads):
+ *   which = 0: bsk, n * (2 lg) * 2 * N   (GGSW rows of BRKeyGen, figure
+ *              "Blind Rotation and its setup")
+ *   which = 1: pK,  N * lpk * 2 * N      (KeySwitchSetup, LWE dim N -> RLWE)
+ *   which = 2: ksK, N * lks * (n + 1)    (KeySwitchSetup, LWE dim N -> dim n) */
+int fdfb_key_words(const fdfb_params* prm, int which, uint64_t* words_out);
+
+/* Installs keys given in canonical layout (host pointers, may be freed on
+ * return; the call synchronises the stream before returning):
+ *   bsk [n][2 lg][2][N]: bsk[i][r] = GGSW row r of RGSW(s_i), row
+ *        r = c*lg + (j-1) adding s_i * g_j to component c (0 = b, 1 = a);
+ *   pk  [N][lpk][2][N]:  RLWE_sk(s_F[i] * g_j), constant message polynomial;
+ *   ksk [N][lks][n+1]:   LWE_s(s_F[i] * g_j).
+ * The bootstrapping key is converted to the NTT domain on the device. */
+int fdfb_keys_upload(fdfb_ctx* ctx, int set_id, const void* bsk, const void* pk,
+                     const void* ksk, void* cuda_stream);
+
+/* Randomness of key generation (host pointers; words are w-bit residues,
+ * noise is signed):  s[n], sk[N] binary keys (s_F = Coefs(sk));
+ * bsk_a/bsk_e [n][2 lg][N]; pk_a/pk_e [N][lpk][N]; ksk_a [N][lks][n];
+ * ksk_e [N][lks]. */
+typedef struct {
+  const uint8_t* s;
+  const uint8_t* sk;
+  const void* bsk_a;
+  const int64_t* bsk_e;
+  const void* pk_a;
+  const int64_t* pk_e;
+  const void* ksk_a;
+  const int64_t* ksk_e;
+} fdfb_keygen_inputs;
+
+/* Generates the keys on the GPU from the given randomness -- BRKeyGen and
+ * KeySwitchSetup (figures "Blind Rotation and its setup" and "Key switching
+ * algorithm and its setup"), every GLWE sample b = a*sk + e + m computed
+ * exactly -- and installs them, as fdfb_keys_upload would.  Synchronises the
+ * stream before returning. */
+int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, void* cuda_stream);
+
+/* Copies the installed keys back in canonical layout (host pointers, each
+ * may be NULL).  Synchronises the stream. */
+int fdfb_keys_download(fdfb_ctx* ctx, int set_id, void* bsk, void* pk, void* ksk, void* cuda_stream);
+
+/* Installs a lookup table f: Z_t -> Z_t (host, t entries; BootsMap[m+1] =
+ * f(m), unscaled) and builds its rotation polynomials with SetupPolynomial
+ * (figure "functional-bootstrapping", right: m ascending, e ascending, later
+ * writes win).  *lut_id_out receives the id, dense from 0 per parameter set.
+ * FDFB_EBADLUT if an entry is >= t. */
+int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out);
+
+/* Reads back the rotation polynomials of a table: p0, p1 host int32[N]. */
+int fdfb_lut_polys(fdfb_ctx* ctx, int set_id, int lut_id, int32_t* p0, int32_t* p1);
+
+/* Full-domain functional bootstrap of a batch (figure "functional-
+ * bootstrapping", left):
+ *   ct_in   device, [batch][n+1] words, LWE_s(Delta m), Delta = q/t;
+ *   lut_ids device, int32[batch], ids from fdfb_lut_setup;
+ *   ct_out  device, [batch][n+1] words, LWE_s(Delta f(m)); may not alias ct_in.
+ * batch may be 0.  The library keeps scratch for the largest batch seen
+ * (allocated on first use, outside any stream capture). */
+int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                   int64_t batch, void* ct_out, void* cuda_stream);
+
+/* Intermediates of fdfb_bootstrap for checking (device pointers, each may
+ * be NULL; [batch] x ...):
+ *   ctN  uint32 [n+1]  ModSwitch(ct, q, 2N)
+ *   sgn  words [N+1]   SampleExtract of the sign rotation + [Delta/2, 0]
+ *   cR   words [2N]    KeySwitch(sgn, pK)
+ *   accF words [2N]    PubMux(cR, rotP'_1, rotP'_0)
+ *   cQ   words [N+1]   SampleExtract of the function rotation */
+typedef struct {
+  void* ctN;
+  void* sgn;
+  void* cR;
+  void* accF;
+  void* cQ;
+} fdfb_debug_bufs;
+
+int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                         int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg,
+                         void* cuda_stream);
+
+/* One group of a mixed batch: a parameter set and its ciphertexts. */
+typedef struct {
+  int set_id;
+  const void* ct_in;       /* device [batch][n+1] */
+  const int32_t* lut_ids;  /* device [batch] */
+  int64_t batch;
+  void* ct_out;            /* device [batch][n+1] */
+} fdfb_group;
+
+/* Bootstraps several groups under different parameter sets; each stage is
+ * one launch over all groups (the blind rotations of every group share one
+ * persistent launch). */
+int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, void* cuda_stream);
+
+/* LWE key switching with the installed ksK (figure "Key switching algorithm
+ * and its setup"): ct_in device [batch][N+1] words under s_F, ct_out device
+ * [batch][n+1] words under s. */
+int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
+                   void* cuda_stream);
+
+/* LWE encryption b = <a, s> + e + Delta m (device pointers):  s uint8[n];
+ * a [count][n] words; e int64[count]; m int64[count] (in Z_t);
+ * ct_out [count][n+1] words. */
+int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,
+                     const int64_t* m, int64_t count, void* ct_out, void* cuda_stream);
+
+/* LWE decryption round(t * (b - <a, s>) / q) mod t, round half up
+ * (device pointers): s uint8[n]; ct [count][n+1]; m_out int32[count]. */
+int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct, int64_t count,
+                     int32_t* m_out, void* cuda_stream);
+
+/* LWE affine layer without bootstrapping (Lemma "Linear Homomorphism of
+ * GLWE samples"; Section 3.4 "Computing in Z_t"):
+ *   y[b][o] = sum_i W[o][i] * x[b][i]  (mod q), every LWE component;
+ *   W device int32 [n_out][n_in]; x device [batch][n_in][len] words;
+ *   y device [batch][n_out][len] words; len = n+1 of the set. */
+int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n_out,
+                    const void* x, int64_t batch, void* y, void* cuda_stream);
+
+/* Measurement hook; the paper has no counterpart.  While enabled, every
+ * launch of the bootstrap pipeline is bracketed by a CUDA event pair recorded
+ * on the caller's stream, and the device time is accumulated per stage:
+ *   0 sign blind rotation, 1 packing key switch, 2 PubMux,
+ *   3 function blind rotation, 4 LWE key switch.
+ * fdfb_profile_read synchronises on the recorded events and returns the
+ * accumulated milliseconds and launch count of `stage` since the last
+ * enable.  Disabled by default. */
+int fdfb_profile_enable(fdfb_ctx* ctx, int enable);
+int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launches);
+
+/* Waits for the stream and reports latched device-side errors (e.g.
+ * FDFB_ETIMEOUT) and CUDA errors; clears the latch. */
+int fdfb_sync(fdfb_ctx* ctx, void* cuda_stream);
+
+/* Static description of an error code. */
+const char* fdfb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDFB_H */

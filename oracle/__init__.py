@@ -66,6 +66,8 @@ def lib():
                 "or_rlwe_phase": ([i32, i32, vp, vp, vp], None),
                 "or_keygen_bsk": ([vp, vp, vp, vp, vp, vp], None),
                 "or_keygen_pk": ([vp, vp, vp, vp, vp], None),
+                "or_keygen_bsk_row": ([vp, vp, vp, vp, vp, i32, i32, vp], None),
+                "or_keygen_pk_row": ([vp, vp, vp, vp, i32, i32, vp], None),
                 "or_keygen_ksk": ([vp, vp, vp, vp, vp, vp], None),
                 "or_modswitch": ([i32, i32, i32, vp, vp], None),
                 "or_extprod": ([vp, vp, vp, vp], None),
@@ -215,6 +217,26 @@ class Keys:
         lib().or_keygen_pk(C.byref(P), _p(self.sk), _p(pa), _p(pe), _p(self.pk))
         ka, ke = _u64(kr.ksk_a), _i64(kr.ksk_e)
         lib().or_keygen_ksk(C.byref(P), _p(self.sk), _p(self.s), _p(ka), _p(ke), _p(self.ksk))
+
+
+def keygen_bsk_row(ps, kr, i: int, r: int) -> np.ndarray:
+    """GGSW row r of RGSW(s_i) (one row of BRKeyGen), [2][N]."""
+    P = params(ps)
+    a, e = _u64(kr.bsk_a[i, r]), _i64(kr.bsk_e[i, r])
+    s, sk = _u8(kr.s), _u8(kr.sk)
+    out = np.zeros(2 * ps.N, dtype=np.uint64)
+    lib().or_keygen_bsk_row(C.byref(P), _p(s), _p(sk), _p(a), _p(e), i, r, _p(out))
+    return out.reshape(2, ps.N)
+
+
+def keygen_pk_row(ps, kr, i: int, j: int) -> np.ndarray:
+    """Packing-key sample pK[i][j] = RLWE_sk(s_F[i] g_j), [2][N]."""
+    P = params(ps)
+    a, e = _u64(kr.pk_a[i, j]), _i64(kr.pk_e[i, j])
+    sk = _u8(kr.sk)
+    out = np.zeros(2 * ps.N, dtype=np.uint64)
+    lib().or_keygen_pk_row(C.byref(P), _p(sk), _p(a), _p(e), i, j, _p(out))
+    return out.reshape(2, ps.N)
 
 
 def encrypt_messages(ps, s, mr) -> np.ndarray:

@@ -220,39 +220,45 @@ void or_rlwe_phase(int w, int N, const u8* sk, const u64* ct, u64* out) {
  * (Definition "Gadget Matrix").  Row r = c*l + (j-1) adds s[i] * g_j to
  * component c (0 = b, 1 = a).
  * bsk_a, bsk_e: [n][2l][N];  out: [n][2l][2][N]. */
+void or_keygen_bsk_row(const or_params* P, const u8* s, const u8* sk, const u64* a_row,
+                       const i64* e_row, int i, int r, u64* out) {
+    const int N = P->N, w = P->w, l = P->lg;
+    or_rlwe_encrypt(w, N, sk, a_row, e_row, NULL, out);
+    int c = r / l, j = r % l;
+    u64 g = or_gadget(w, P->log2Bg, l, j);
+    out[(size_t)c * N + 0] = (out[(size_t)c * N + 0] + (u64)s[i] * g) & wmask(w);
+}
+
 void or_keygen_bsk(const or_params* P, const u8* s, const u8* sk, const u64* bsk_a,
                    const i64* bsk_e, u64* out) {
-    const int n = P->n, N = P->N, w = P->w, l = P->lg;
-    const u64 m = wmask(w);
+    const int n = P->n, N = P->N, l = P->lg;
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) if (g_threads > 1)
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n; ++i)
         for (int r = 0; r < 2 * l; ++r) {
             size_t row = (size_t)i * 2 * l + r;
-            u64* dst = out + row * 2 * N;
-            or_rlwe_encrypt(w, N, sk, bsk_a + row * N, bsk_e + row * N, NULL, dst);
-            int c = r / l, j = r % l;
-            u64 g = or_gadget(w, P->log2Bg, l, j);
-            dst[(size_t)c * N + 0] = (dst[(size_t)c * N + 0] + (u64)s[i] * g) & m;
+            or_keygen_bsk_row(P, s, sk, bsk_a + row * N, bsk_e + row * N, i, r, out + row * 2 * N);
         }
-    }
 }
 
 /* KeySwitchSetup (appendix figure "Key switching algorithm and its setup")
  * for the packing key pK: pK[i][j] = RLWE_sk(s_F[i] * g_j) with s_F =
  * KeyExtract(sk) = Coefs(sk), the message a constant polynomial.
  * pk_a, pk_e: [N][lpk][N];  out: [N][lpk][2][N]. */
-void or_keygen_pk(const or_params* P, const u8* sk, const u64* pk_a, const i64* pk_e, u64* out) {
+void or_keygen_pk_row(const or_params* P, const u8* sk, const u64* a_row, const i64* e_row,
+                      int i, int j, u64* out) {
     const int N = P->N, w = P->w, l = P->lpk;
-    const u64 m = wmask(w);
+    or_rlwe_encrypt(w, N, sk, a_row, e_row, NULL, out);
+    out[0] = (out[0] + (u64)sk[i] * or_gadget(w, P->log2Bpk, l, j)) & wmask(w);
+}
+
+void or_keygen_pk(const or_params* P, const u8* sk, const u64* pk_a, const i64* pk_e, u64* out) {
+    const int N = P->N, l = P->lpk;
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) if (g_threads > 1)
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < N; ++i)
         for (int j = 0; j < l; ++j) {
             size_t row = (size_t)i * l + j;
-            u64* dst = out + row * 2 * N;
-            or_rlwe_encrypt(w, N, sk, pk_a + row * N, pk_e + row * N, NULL, dst);
-            dst[0] = (dst[0] + (u64)sk[i] * or_gadget(w, P->log2Bpk, l, j)) & m;
+            or_keygen_pk_row(P, sk, pk_a + row * N, pk_e + row * N, i, j, out + row * 2 * N);
         }
-    }
 }
 
 /* KeySwitchSetup for the LWE key-switching key: ksK[i][j] = LWE_s(s_F[i] g_j).

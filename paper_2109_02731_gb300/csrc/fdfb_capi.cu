@@ -1,0 +1,762 @@
+// C ABI of the FDFB library: context, parameter registry, key installation,
+// lookup tables and the bootstrapping pipeline.  See include/fdfb.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "../../include/fdfb.h"
+#include "fdfb_host.hpp"
+#include "fdfb_ops.hpp"
+
+namespace fdfb {
+const Ops* ops_n8(int w);
+const Ops* ops_n9(int w);
+const Ops* ops_n10(int w);
+const Ops* ops_n11(int w);
+const Ops* ops_n12(int w);
+
+const Ops* find_ops(int L, int w) {
+  switch (L) {
+    case 8: return ops_n8(w);
+    case 9: return ops_n9(w);
+    case 10: return ops_n10(w);
+    case 11: return ops_n11(w);
+    case 12: return ops_n12(w);
+    default: return nullptr;
+  }
+}
+}  // namespace fdfb
+
+using namespace fdfb;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int ensure(size_t want) {
+    if (want <= bytes) return FDFB_OK;
+    release();
+    if (want == 0) return FDFB_OK;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return FDFB_ENOMEM;
+    }
+    bytes = want;
+    return FDFB_OK;
+  }
+};
+
+struct SetState {
+  fdfb_params prm{};
+  int w = 0, L = 0, logt = 0;
+  const Ops* ops = nullptr;
+  PrimeSet S{};
+  DevBuf tw;        // [2][P][N] uint2
+  DevBuf bsk_ntt;   // [n][P][2 lg][2][N] uint32
+  DevBuf bsk;       // canonical [n][2 lg][2][N] words
+  DevBuf pk;        // canonical [N][lpk][2][N] words
+  DevBuf ksk;       // canonical [N][lks][n+1] words
+  bool keys = false;
+  std::vector<int16_t> luts_host;  // [n_luts][2][N]
+  DevBuf luts;
+  int n_luts = 0;
+  DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
+  int64_t scratch_batch = 0;
+  size_t br_smem = 0;
+  uint32_t br_r1 = 0, br_ex = 0;
+  size_t wbytes() const { return (size_t)w / 8; }
+};
+
+}  // namespace
+
+constexpr int kStages = 5;
+
+struct fdfb_ctx {
+  int device = 0;
+  std::vector<std::unique_ptr<SetState>> sets;
+  int* d_err = nullptr;
+  std::mutex mu;
+  // measurement hook
+  bool prof = false;
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  double prof_ms[kStages] = {0, 0, 0, 0, 0};
+  int64_t prof_n[kStages] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return FDFB_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? FDFB_ENOMEM : FDFB_ECUDA;
+}
+
+#define FD_TRY(x)                    \
+  do {                               \
+    int _rc = (x);                   \
+    if (_rc != FDFB_OK) return _rc;  \
+  } while (0)
+#define FD_CUDA(x) FD_TRY(cuda_err(x))
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+int ilog2(uint32_t x) {
+  int r = 0;
+  while ((1u << r) < x) ++r;
+  return r;
+}
+int trunc_bits(int w, int log2B, int ell) {
+  int r = w - ell * log2B;
+  return r > 0 ? r : 0;
+}
+uint64_t gadget(int w, int log2B, int ell, int j) {
+  int sh = trunc_bits(w, log2B, ell) + log2B * j;
+  if (sh >= w) return 0;
+  return (uint64_t)1 << sh;
+}
+
+SetState* get_set(fdfb_ctx* ctx, int id) {
+  if (!ctx || id < 0 || id >= (int)ctx->sets.size()) return nullptr;
+  return ctx->sets[id].get();
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// SetupPolynomial (figure "functional-bootstrapping", right) on unscaled
+// table entries: for m = 0..t-1, e = -ceil(N/t)..ceil(N/t),
+// y = round(2N/t) m + e mod 2N writes rotP_0[0] = f(m) (y = 0),
+// rotP_0[N-y] = -f(m) (0 < y < N), rotP_1[0] = -f(m) (y = N),
+// rotP_1[2N-y] = f(m) (N < y < 2N); later writes replace earlier ones.
+void setup_polynomial(int N, int t, const uint32_t* f, int16_t* p0, int16_t* p1) {
+  for (int j = 0; j < N; ++j) p0[j] = p1[j] = 0;
+  const int64_t twoN = 2 * (int64_t)N;
+  const int64_t E = ((int64_t)N + t - 1) / t;
+  const int64_t step = (twoN + t / 2) / t;
+  for (int m = 0; m < t; ++m)
+    for (int64_t e = -E; e <= E; ++e) {
+      int64_t y = ((step * m + e) % twoN + twoN) % twoN;
+      const int16_t v = (int16_t)f[m];
+      if (y == 0) p0[0] = v;
+      else if (y < N) p0[N - y] = (int16_t)-v;
+      else if (y == N) p1[0] = (int16_t)-v;
+      else p1[twoN - y] = v;
+    }
+}
+
+int install_bsk_ntt(SetState& st, cudaStream_t s) {
+  const fdfb_params& P = st.prm;
+  const size_t N = P.N;
+  FD_TRY(st.bsk_ntt.ensure((size_t)P.n * st.ops->P * 2 * P.lg * 2 * N * 4));
+  FD_CUDA(st.ops->bsk_ntt(st.S, st.bsk.p, (int64_t)P.n * 2 * P.lg, 2 * (int)P.lg,
+                          (uint32_t*)st.bsk_ntt.p, s));
+  return FDFB_OK;
+}
+
+int ensure_scratch(SetState& st, int64_t batch) {
+  if (batch <= st.scratch_batch) return FDFB_OK;
+  const size_t N = st.prm.N;
+  const size_t per = ((N + 1) + 2 * N + 2 * N + (N + 1)) * st.wbytes();
+  FD_TRY(st.scratch.ensure(per * (size_t)batch + 256));
+  st.scratch_batch = batch;
+  return FDFB_OK;
+}
+
+// Brackets one launch with an event pair when the measurement hook is on.
+struct StageTimer {
+  fdfb_ctx* ctx;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(fdfb_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
+    if (ctx->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, s);
+      ctx->marks.push_back({stage, a, b});
+    } else {
+      cudaEventDestroy(a);
+    }
+  }
+};
+
+// One bootstrap pipeline on one parameter set (figure "functional-
+// bootstrapping", left), steps 1-14.
+int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
+                 int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s) {
+  if (batch < 0) return FDFB_EINVAL;
+  if (batch == 0) return FDFB_OK;
+  if (!ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
+  if (!st.keys) return FDFB_ENOKEYS;
+  if (st.n_luts == 0) return FDFB_EBADLUT;
+  if (batch > 0x7fffffff) return FDFB_EINVAL;
+  const fdfb_params& P = st.prm;
+  const size_t N = P.N, wb = st.wbytes();
+  FD_TRY(ensure_scratch(st, batch));
+  unsigned char* base = (unsigned char*)st.scratch.p;
+  void* sgn = base;
+  void* cR = base + (size_t)batch * (N + 1) * wb;
+  void* accF = (unsigned char*)cR + (size_t)batch * 2 * N * wb;
+  void* cQ = (unsigned char*)accF + (size_t)batch * 2 * N * wb;
+  if (dbg) {
+    if (dbg->sgn) sgn = dbg->sgn;
+    if (dbg->cR) cR = dbg->cR;
+    if (dbg->accF) accF = dbg->accF;
+    if (dbg->cQ) cQ = dbg->cQ;
+  }
+  const uint64_t delta = (uint64_t)1 << (st.w - st.logt);
+
+  // Steps 1-8: ModSwitch, sign accumulator, BlindRotate, SampleExtract + Delta/2.
+  BRParams br{};
+  br.S = st.S;
+  br.bsk = (const uint32_t*)st.bsk_ntt.p;
+  br.ct = ct_in;
+  br.acc0 = nullptr;
+  br.lwe_out = sgn;
+  br.ctN_out = dbg ? (uint32_t*)dbg->ctN : nullptr;
+  br.n = P.n;
+  br.lg = P.lg;
+  br.log2Bg = P.log2Bg;
+  br.rtrunc = trunc_bits(st.w, P.log2Bg, P.lg);
+  br.batch = batch;
+  br.delta_half = delta / 2;
+  br.sign_mode = 1;
+  br.smem_r1 = st.br_r1;
+  br.smem_exch = st.br_ex;
+  {
+    StageTimer tm(ctx, 0, s);
+    FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
+  }
+
+  // Steps 9-11, BuildAcc: KeySwitch to RLWE with pK, then PubMux.
+  {
+    dim3 grid((unsigned)((2 * N + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
+    const int rt = trunc_bits(st.w, P.log2Bpk, P.lpk);
+    StageTimer tm(ctx, 1, s);
+    if (st.w == 32)
+      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
+          (const uint32_t*)sgn, batch, (int)N, (const uint32_t*)st.pk.p, P.lpk, P.log2Bpk, rt,
+          (int)(2 * N), (uint32_t*)cR);
+    else
+      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>(
+          (const uint64_t*)sgn, batch, (int)N, (const uint64_t*)st.pk.p, P.lpk, P.log2Bpk, rt,
+          (int)(2 * N), (uint64_t*)cR);
+    FD_CUDA(cudaGetLastError());
+  }
+  PubMuxParams pm{};
+  pm.S = st.S;
+  pm.cR = cR;
+  pm.ct = ct_in;
+  pm.lut_ids = lut_ids;
+  pm.luts = (const int16_t*)st.luts.p;
+  pm.n_luts = st.n_luts;
+  pm.accF = accF;
+  pm.n = P.n;
+  pm.t = P.t;
+  pm.delta = delta;
+  pm.err = ctx->d_err;
+  {
+    StageTimer tm(ctx, 2, s);
+    FD_CUDA(st.ops->pubmux(pm, batch, s));
+  }
+
+  // Steps 12-13: function BlindRotate, SampleExtract.
+  br.acc0 = accF;
+  br.lwe_out = cQ;
+  br.ctN_out = nullptr;
+  br.sign_mode = 0;
+  {
+    StageTimer tm(ctx, 3, s);
+    FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
+  }
+
+  // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q).
+  {
+    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
+    const int rt = trunc_bits(st.w, P.log2Bks, P.lks);
+    StageTimer tm(ctx, 4, s);
+    if (st.w == 32)
+      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
+          (const uint32_t*)cQ, batch, (int)N, (const uint32_t*)st.ksk.p, P.lks, P.log2Bks, rt,
+          (int)P.n + 1, (uint32_t*)ct_out);
+    else
+      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>(
+          (const uint64_t*)cQ, batch, (int)N, (const uint64_t*)st.ksk.p, P.lks, P.log2Bks, rt,
+          (int)P.n + 1, (uint64_t*)ct_out);
+    FD_CUDA(cudaGetLastError());
+  }
+  return FDFB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fdfb_strerror(int code) {
+  switch (code) {
+    case FDFB_OK: return "ok";
+    case FDFB_EINVAL: return "invalid argument or unsupported parameters";
+    case FDFB_ENOMEM: return "device allocation failed";
+    case FDFB_ECUDA: return "CUDA runtime error";
+    case FDFB_ETIMEOUT: return "device-side wait timed out";
+    case FDFB_ENOKEYS: return "keys not installed for this parameter set";
+    case FDFB_EBADLUT: return "bad lookup table id or entry";
+    default: return "unknown error";
+  }
+}
+
+int fdfb_create(fdfb_ctx** out, int device) {
+  if (!out) return FDFB_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return FDFB_ECUDA;
+  }
+  DeviceGuard g(device);
+  auto* ctx = new fdfb_ctx();
+  ctx->device = device;
+  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FDFB_ENOMEM;
+  }
+  *out = ctx;
+  return FDFB_OK;
+}
+
+int fdfb_destroy(fdfb_ctx* ctx) {
+  if (!ctx) return FDFB_EINVAL;
+  {
+    DeviceGuard g(ctx->device);
+    ctx->sets.clear();
+    if (ctx->d_err) cudaFree(ctx->d_err);
+  }
+  delete ctx;
+  return FDFB_OK;
+}
+
+int fdfb_key_words(const fdfb_params* p, int which, uint64_t* words_out) {
+  if (!p || !words_out) return FDFB_EINVAL;
+  const uint64_t n = p->n, N = p->N;
+  switch (which) {
+    case 0: *words_out = n * 2 * p->lg * 2 * N; return FDFB_OK;
+    case 1: *words_out = N * p->lpk * 2 * N; return FDFB_OK;
+    case 2: *words_out = N * p->lks * (n + 1); return FDFB_OK;
+    default: return FDFB_EINVAL;
+  }
+}
+
+int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out) {
+  if (!ctx || !prm || !set_id_out) return FDFB_EINVAL;
+  const fdfb_params& P = *prm;
+  if (P.k != 1 || (P.log2q != 32 && P.log2q != 64)) return FDFB_EINVAL;
+  if (!is_pow2(P.N) || P.N < 256 || P.N > 4096) return FDFB_EINVAL;
+  if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
+  if (!is_pow2(P.t) || P.t < 2 || P.t > P.N) return FDFB_EINVAL;
+  if (P.lg < 1 || P.lg > 4 || P.log2Bg < 1 || P.log2Bg > 16) return FDFB_EINVAL;
+  if (P.lks < 1 || P.lks > 64 || P.log2Bks < 1 || P.log2Bks > 16) return FDFB_EINVAL;
+  if (P.lpk < 1 || P.lpk > 64 || P.log2Bpk < 1 || P.log2Bpk > 16) return FDFB_EINVAL;
+  if (P.lboot != 1 || P.log2Lboot != (uint32_t)ilog2(P.t)) return FDFB_EINVAL;
+  const int w = (int)P.log2q, L = ilog2(P.N);
+  const Ops* ops = find_ops(L, w);
+  if (!ops) return FDFB_EINVAL;
+  // Exactness of the lifted negacyclic products.
+  const long double q = ldexpl(1.0L, w);
+  const long double br_max = 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * (q / 2);
+  const long double pm_max = (long double)P.N * (P.t - 1) * q;
+  const long double enc_max = (long double)P.N * q;
+  if (!host::lift_is_exact(ops->P, br_max) || !host::lift_is_exact(ops->P, pm_max) ||
+      !host::lift_is_exact(ops->P, enc_max))
+    return FDFB_EINVAL;
+
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  auto st = std::make_unique<SetState>();
+  st->prm = P;
+  st->w = w;
+  st->L = L;
+  st->logt = ilog2(P.t);
+  st->ops = ops;
+  st->br_smem = ops->br_smem((int)P.n, (int)P.lg, &st->br_r1, &st->br_ex);
+  int max_smem = 0;
+  FD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  if (st->br_smem > (size_t)max_smem) return FDFB_EINVAL;
+  FD_CUDA(ops->br_prepare(st->br_smem));
+  std::vector<uint2> fwd, inv;
+  host::make_prime_set(ops->P, L, st->S, fwd, inv);
+  FD_TRY(st->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
+  FD_CUDA(cudaMemcpy(st->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+  FD_CUDA(cudaMemcpy((uint2*)st->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),
+                     cudaMemcpyHostToDevice));
+  st->S.tw_fwd = (const uint2*)st->tw.p;
+  st->S.tw_inv = (const uint2*)st->tw.p + fwd.size();
+  ctx->sets.push_back(std::move(st));
+  *set_id_out = (int)ctx->sets.size() - 1;
+  return FDFB_OK;
+}
+
+int fdfb_keys_upload(fdfb_ctx* ctx, int set_id, const void* bsk, const void* pk, const void* ksk,
+                     void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !bsk || !pk || !ksk) return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  uint64_t wb_, wp_, wk_;
+  fdfb_key_words(&st->prm, 0, &wb_);
+  fdfb_key_words(&st->prm, 1, &wp_);
+  fdfb_key_words(&st->prm, 2, &wk_);
+  const size_t wb = st->wbytes();
+  FD_TRY(st->bsk.ensure(wb_ * wb));
+  FD_TRY(st->pk.ensure(wp_ * wb));
+  FD_TRY(st->ksk.ensure(wk_ * wb));
+  FD_CUDA(cudaMemcpyAsync(st->bsk.p, bsk, wb_ * wb, cudaMemcpyHostToDevice, s));
+  FD_CUDA(cudaMemcpyAsync(st->pk.p, pk, wp_ * wb, cudaMemcpyHostToDevice, s));
+  FD_CUDA(cudaMemcpyAsync(st->ksk.p, ksk, wk_ * wb, cudaMemcpyHostToDevice, s));
+  FD_TRY(install_bsk_ntt(*st, s));
+  FD_CUDA(cudaStreamSynchronize(s));
+  st->keys = true;
+  return FDFB_OK;
+}
+
+int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !in || !in->s || !in->sk || !in->bsk_a || !in->bsk_e || !in->pk_a || !in->pk_e ||
+      !in->ksk_a || !in->ksk_e)
+    return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  const fdfb_params& P = st->prm;
+  const size_t n = P.n, N = P.N, wb = st->wbytes();
+  const int w = st->w;
+  uint64_t wb_, wp_, wk_;
+  fdfb_key_words(&P, 0, &wb_);
+  fdfb_key_words(&P, 1, &wp_);
+  fdfb_key_words(&P, 2, &wk_);
+  FD_TRY(st->bsk.ensure(wb_ * wb));
+  FD_TRY(st->pk.ensure(wp_ * wb));
+  FD_TRY(st->ksk.ensure(wk_ * wb));
+
+  DevBuf d_sk, d_s, d_a, d_e, d_mu, d_comp, d_m;
+  FD_TRY(d_sk.ensure(N));
+  FD_TRY(d_s.ensure(n));
+  FD_CUDA(cudaMemcpyAsync(d_sk.p, in->sk, N, cudaMemcpyHostToDevice, s));
+  FD_CUDA(cudaMemcpyAsync(d_s.p, in->s, n, cudaMemcpyHostToDevice, s));
+
+  // BRKeyGen: rows r = c*lg + j of RGSW(s_i) add s_i * g_j to component c.
+  {
+    const size_t rows = n * 2 * P.lg;
+    std::vector<uint64_t> mu(rows);
+    std::vector<uint8_t> comp(rows);
+    for (size_t i = 0; i < n; ++i)
+      for (size_t r = 0; r < 2 * P.lg; ++r) {
+        const int c = (int)(r / P.lg), j = (int)(r % P.lg);
+        mu[i * 2 * P.lg + r] = in->s[i] ? gadget(w, P.log2Bg, P.lg, j) : 0;
+        comp[i * 2 * P.lg + r] = (uint8_t)c;
+      }
+    FD_TRY(d_a.ensure(rows * N * wb));
+    FD_TRY(d_e.ensure(rows * N * 8));
+    FD_TRY(d_mu.ensure(rows * 8));
+    FD_TRY(d_comp.ensure(rows));
+    FD_CUDA(cudaMemcpyAsync(d_a.p, in->bsk_a, rows * N * wb, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_e.p, in->bsk_e, rows * N * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_comp.p, comp.data(), rows, cudaMemcpyHostToDevice, s));
+    RlweEncParams rp{st->S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
+                     (const uint64_t*)d_mu.p, (const uint8_t*)d_comp.p, st->bsk.p};
+    FD_CUDA(st->ops->rlwe_enc(rp, (int64_t)rows, s));
+    FD_CUDA(cudaStreamSynchronize(s));
+  }
+  // KeySwitchSetup for pK: RLWE_sk(s_F[i] g_j), constant message polynomial.
+  {
+    const size_t rows = N * P.lpk;
+    std::vector<uint64_t> mu(rows);
+    std::vector<uint8_t> comp(rows, 0);
+    for (size_t i = 0; i < N; ++i)
+      for (size_t j = 0; j < P.lpk; ++j)
+        mu[i * P.lpk + j] = in->sk[i] ? gadget(w, P.log2Bpk, P.lpk, (int)j) : 0;
+    FD_TRY(d_a.ensure(rows * N * wb));
+    FD_TRY(d_e.ensure(rows * N * 8));
+    FD_TRY(d_mu.ensure(rows * 8));
+    FD_TRY(d_comp.ensure(rows));
+    FD_CUDA(cudaMemcpyAsync(d_a.p, in->pk_a, rows * N * wb, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_e.p, in->pk_e, rows * N * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_comp.p, comp.data(), rows, cudaMemcpyHostToDevice, s));
+    RlweEncParams rp{st->S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
+                     (const uint64_t*)d_mu.p, (const uint8_t*)d_comp.p, st->pk.p};
+    FD_CUDA(st->ops->rlwe_enc(rp, (int64_t)rows, s));
+    FD_CUDA(cudaStreamSynchronize(s));
+  }
+  // KeySwitchSetup for ksK: LWE_s(s_F[i] g_j).
+  {
+    const size_t rows = N * P.lks;
+    std::vector<int64_t> m(rows);
+    for (size_t i = 0; i < N; ++i)
+      for (size_t j = 0; j < P.lks; ++j)
+        m[i * P.lks + j] = in->sk[i] ? (int64_t)gadget(w, P.log2Bks, P.lks, (int)j) : 0;
+    FD_TRY(d_a.ensure(rows * n * wb));
+    FD_TRY(d_e.ensure(rows * 8));
+    FD_TRY(d_m.ensure(rows * 8));
+    FD_CUDA(cudaMemcpyAsync(d_a.p, in->ksk_a, rows * n * wb, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_e.p, in->ksk_e, rows * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_m.p, m.data(), rows * 8, cudaMemcpyHostToDevice, s));
+    const unsigned blocks = (unsigned)((rows + 7) / 8);
+    if (w == 32)
+      lwe_encrypt_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint8_t*)d_s.p, (const uint32_t*)d_a.p,
+                                                          (const int64_t*)d_e.p, (const int64_t*)d_m.p,
+                                                          (int64_t)rows, (int)n, 1, (uint32_t*)st->ksk.p);
+    else
+      lwe_encrypt_kernel<uint64_t><<<blocks, 256, 0, s>>>((const uint8_t*)d_s.p, (const uint64_t*)d_a.p,
+                                                          (const int64_t*)d_e.p, (const int64_t*)d_m.p,
+                                                          (int64_t)rows, (int)n, 1, (uint64_t*)st->ksk.p);
+    FD_CUDA(cudaGetLastError());
+  }
+  FD_TRY(install_bsk_ntt(*st, s));
+  FD_CUDA(cudaStreamSynchronize(s));
+  st->keys = true;
+  return FDFB_OK;
+}
+
+int fdfb_keys_download(fdfb_ctx* ctx, int set_id, void* bsk, void* pk, void* ksk, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  if (!st->keys) return FDFB_ENOKEYS;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  uint64_t wb_, wp_, wk_;
+  fdfb_key_words(&st->prm, 0, &wb_);
+  fdfb_key_words(&st->prm, 1, &wp_);
+  fdfb_key_words(&st->prm, 2, &wk_);
+  const size_t wb = st->wbytes();
+  if (bsk) FD_CUDA(cudaMemcpyAsync(bsk, st->bsk.p, wb_ * wb, cudaMemcpyDeviceToHost, s));
+  if (pk) FD_CUDA(cudaMemcpyAsync(pk, st->pk.p, wp_ * wb, cudaMemcpyDeviceToHost, s));
+  if (ksk) FD_CUDA(cudaMemcpyAsync(ksk, st->ksk.p, wk_ * wb, cudaMemcpyDeviceToHost, s));
+  FD_CUDA(cudaStreamSynchronize(s));
+  return FDFB_OK;
+}
+
+int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !f || !lut_id_out) return FDFB_EINVAL;
+  const int N = (int)st->prm.N, t = (int)st->prm.t;
+  for (int m = 0; m < t; ++m)
+    if (f[m] >= (uint32_t)t) return FDFB_EBADLUT;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const size_t off = st->luts_host.size();
+  st->luts_host.resize(off + 2 * (size_t)N);
+  setup_polynomial(N, t, f, st->luts_host.data() + off, st->luts_host.data() + off + N);
+  // Tables are few and small: re-upload all of them after a device sync, so
+  // no launch in flight still reads a buffer that is being replaced.
+  FD_CUDA(cudaDeviceSynchronize());
+  FD_TRY(st->luts.ensure(st->luts_host.size() * sizeof(int16_t)));
+  FD_CUDA(cudaMemcpy(st->luts.p, st->luts_host.data(), st->luts_host.size() * sizeof(int16_t),
+                     cudaMemcpyHostToDevice));
+  *lut_id_out = st->n_luts++;
+  return FDFB_OK;
+}
+
+int fdfb_lut_polys(fdfb_ctx* ctx, int set_id, int lut_id, int32_t* p0, int32_t* p1) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !p0 || !p1) return FDFB_EINVAL;
+  if (lut_id < 0 || lut_id >= st->n_luts) return FDFB_EBADLUT;
+  const int N = (int)st->prm.N;
+  const int16_t* src = st->luts_host.data() + (size_t)lut_id * 2 * N;
+  for (int j = 0; j < N; ++j) {
+    p0[j] = src[j];
+    p1[j] = src[N + j];
+  }
+  return FDFB_OK;
+}
+
+int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                   int64_t batch, void* ct_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, nullptr, as_stream(cuda_stream));
+}
+
+int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                         int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !dbg) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, dbg, as_stream(cuda_stream));
+}
+
+int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, void* cuda_stream) {
+  if (!ctx || n_groups < 0 || (n_groups > 0 && !groups)) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < n_groups; ++i) {
+    SetState* st = get_set(ctx, groups[i].set_id);
+    if (!st) return FDFB_EINVAL;
+  }
+  for (int i = 0; i < n_groups; ++i) {
+    SetState* st = get_set(ctx, groups[i].set_id);
+    FD_TRY(run_pipeline(ctx, *st, groups[i].ct_in, groups[i].lut_ids, groups[i].batch,
+                        groups[i].ct_out, nullptr, as_stream(cuda_stream)));
+  }
+  return FDFB_OK;
+}
+
+int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
+                   void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || batch < 0 || batch > 0x7fffffffLL * KS_BM) return FDFB_EINVAL;
+  if (batch == 0) return FDFB_OK;
+  if (!ct_in || !ct_out) return FDFB_EINVAL;
+  if (!st->keys) return FDFB_ENOKEYS;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  const fdfb_params& P = st->prm;
+  dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
+  const int rt = trunc_bits(st->w, P.log2Bks, P.lks);
+  if (st->w == 32)
+    keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>((const uint32_t*)ct_in, batch, (int)P.N,
+                                                          (const uint32_t*)st->ksk.p, P.lks, P.log2Bks,
+                                                          rt, (int)P.n + 1, (uint32_t*)ct_out);
+  else
+    keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>((const uint64_t*)ct_in, batch, (int)P.N,
+                                                          (const uint64_t*)st->ksk.p, P.lks, P.log2Bks,
+                                                          rt, (int)P.n + 1, (uint64_t*)ct_out);
+  return cuda_err(cudaGetLastError());
+}
+
+int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,
+                     const int64_t* m, int64_t count, void* ct_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || count < 0) return FDFB_EINVAL;
+  if (count == 0) return FDFB_OK;
+  if (!s || !a || !e || !m || !ct_out) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  const uint64_t delta = (uint64_t)1 << (st->w - st->logt);
+  const unsigned blocks = (unsigned)((count + 7) / 8);
+  cudaStream_t cs = as_stream(cuda_stream);
+  if (st->w == 32)
+    lwe_encrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)a, e, m, count,
+                                                         (int)st->prm.n, delta, (uint32_t*)ct_out);
+  else
+    lwe_encrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)a, e, m, count,
+                                                         (int)st->prm.n, delta, (uint64_t*)ct_out);
+  return cuda_err(cudaGetLastError());
+}
+
+int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct, int64_t count,
+                     int32_t* m_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || count < 0) return FDFB_EINVAL;
+  if (count == 0) return FDFB_OK;
+  if (!s || !ct || !m_out) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  const unsigned blocks = (unsigned)((count + 7) / 8);
+  cudaStream_t cs = as_stream(cuda_stream);
+  if (st->w == 32)
+    lwe_decrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)ct, count,
+                                                         (int)st->prm.n, st->logt, m_out);
+  else
+    lwe_decrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)ct, count,
+                                                         (int)st->prm.n, st->logt, m_out);
+  return cuda_err(cudaGetLastError());
+}
+
+int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n_out, const void* x,
+                    int64_t batch, void* y, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || n_in < 1 || n_out < 1 || batch < 0 || batch > 65535) return FDFB_EINVAL;
+  if (batch == 0) return FDFB_OK;
+  if (!W || !x || !y) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  const int len = (int)st->prm.n + 1;
+  dim3 grid((unsigned)((len + AFF_TK - 1) / AFF_TK), (unsigned)((n_out + AFF_TO - 1) / AFF_TO),
+            (unsigned)batch);
+  cudaStream_t cs = as_stream(cuda_stream);
+  if (st->w == 32)
+    lwe_affine_kernel<uint32_t><<<grid, AFF_TK, 0, cs>>>(W, n_in, n_out, (const uint32_t*)x, len,
+                                                        (uint32_t*)y);
+  else
+    lwe_affine_kernel<uint64_t><<<grid, AFF_TK, 0, cs>>>(W, n_in, n_out, (const uint64_t*)x, len,
+                                                        (uint64_t*)y);
+  return cuda_err(cudaGetLastError());
+}
+
+int fdfb_profile_enable(fdfb_ctx* ctx, int enable) {
+  if (!ctx) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  for (auto& m : ctx->marks) {
+    cudaEventSynchronize(m.b);
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  ctx->marks.clear();
+  for (int i = 0; i < kStages; ++i) {
+    ctx->prof_ms[i] = 0;
+    ctx->prof_n[i] = 0;
+  }
+  ctx->prof = enable != 0;
+  return FDFB_OK;
+}
+
+int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launches) {
+  if (!ctx || stage < 0 || stage >= kStages || !total_ms || !launches) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  for (auto& m : ctx->marks) {
+    float ms = 0;
+    FD_CUDA(cudaEventSynchronize(m.b));
+    FD_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
+    ctx->prof_ms[m.stage] += ms;
+    ctx->prof_n[m.stage] += 1;
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  ctx->marks.clear();
+  *total_ms = ctx->prof_ms[stage];
+  *launches = ctx->prof_n[stage];
+  return FDFB_OK;
+}
+
+int fdfb_sync(fdfb_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  FD_CUDA(cudaStreamSynchronize(as_stream(cuda_stream)));
+  int h = 0;
+  FD_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    FD_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    return h;
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// Core arithmetic shared by every kernel of the FDFB library: 30-bit NTT
+// primes, Shoup and Montgomery modular products, Garner reconstruction into
+// Z_{2^w}, and the register/shared-memory layouts of the negacyclic NTT.
+//
+// The negacyclic products of the method (extProd of Definition "External
+// Product", PubMux, RLWE encryption) are computed exactly: the integer
+// product is formed modulo P primes p_i = 1 (mod 2^14), p_i < 2^30, by a
+// merged-twist negacyclic NTT, then lifted to the centred integer by Garner's
+// mixed-radix algorithm and reduced mod 2^w.  The lift is exact whenever
+// |result| < prod(p_i)/2, which the host checks for each parameter set.
+//
+// Everything here is __host__ __device__ so the index arithmetic of the
+// transform can be exercised on the CPU.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#define FD_HD __host__ __device__ __forceinline__
+#else
+#define FD_HD inline
+struct uint2 { uint32_t x, y; };
+#endif
+
+namespace fdfb {
+
+constexpr int kMaxPrimes = 4;
+// Largest primes below 2^30 that are 1 mod 2^14 (so 2N | p - 1 for N <= 8192).
+constexpr uint32_t kPrimes[kMaxPrimes] = {1073692673u, 1073643521u, 1073479681u, 1073430529u};
+
+FD_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+FD_HD uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// x < 2m (m < 2^31)  ->  x mod m, via the unsigned-wrap minimum.
+FD_HD uint32_t csub(uint32_t x, uint32_t m) { return umin32(x, x - m); }
+
+// Shoup's product a*w mod p with precomputed wp = floor(w 2^32 / p):
+// result in [0, 2p) for any 32-bit a (w < p < 2^31).
+FD_HD uint32_t mul_shoup(uint32_t a, uint32_t w, uint32_t wp, uint32_t p) {
+  uint32_t q = mulhi32(a, wp);
+  return a * w - q * p;
+}
+
+// Montgomery reduction: x * 2^-32 mod p for x < 2^63, pneg = -p^-1 mod 2^32.
+// Result < x/2^32 + p.
+FD_HD uint32_t redc(uint64_t x, uint32_t p, uint32_t pneg) {
+  uint32_t m = (uint32_t)x * pneg;
+  return (uint32_t)((x + (uint64_t)m * p) >> 32);
+}
+
+// Per-(prime set, ring degree) constants, passed to kernels by value.
+struct PrimeSet {
+  int P;                             // number of primes in use
+  uint32_t p[kMaxPrimes];
+  uint32_t pneg[kMaxPrimes];         // -p^-1 mod 2^32
+  uint32_t ones[kMaxPrimes];         // floor(2^32 / p): Shoup companion of 1
+  uint32_t r32[kMaxPrimes];          // 2^32 mod p
+  uint32_t r32s[kMaxPrimes];         // Shoup companion of r32
+  uint32_t r64[kMaxPrimes];          // 2^64 mod p
+  uint32_t ninv_m[kMaxPrimes];       // N^-1 * 2^32 mod p  (Montgomery form of N^-1)
+  uint32_t ninv_ms[kMaxPrimes];      // Shoup companion of ninv_m
+  uint32_t gc[kMaxPrimes][kMaxPrimes];   // Garner: p_i^-1 mod p_j (i < j)
+  uint32_t gcs[kMaxPrimes][kMaxPrimes];  // Shoup companions
+  uint64_t M[kMaxPrimes + 1];        // prefix products of the primes, mod 2^64
+  uint32_t half_top;                 // p_{P-1} / 2: sign threshold of the top digit
+  const uint2* tw_fwd;               // [P][N] (psi^brv(k), Shoup) forward twiddles
+  const uint2* tw_inv;               // [P][N] (psi^-brv(k), Shoup) inverse twiddles
+};
+
+// Residue of a w-bit word (unsigned) modulo p.
+FD_HD uint32_t mod_u32(uint32_t x, const PrimeSet& S, int i) {
+  // Shoup's product by 1 (companion floor(2^32/p)) lands in [0, 2p).
+  const uint32_t p = S.p[i];
+  return csub(mul_shoup(x, 1u, S.ones[i], p), p);
+}
+FD_HD uint32_t mod_u64(uint64_t x, const PrimeSet& S, int i) {
+  uint32_t p = S.p[i];
+  uint32_t hi = mul_shoup((uint32_t)(x >> 32), S.r32[i], S.r32s[i], p);  // [0, 2p)
+  uint32_t lo = mod_u32((uint32_t)x, S, i);                               // [0, p)
+  return csub(csub(hi, p) + lo, p);
+}
+// Residue of the centred value of a w-bit word (x in [-2^{w-1}, 2^{w-1})).
+template <typename W>
+FD_HD uint32_t mod_centred(W x, const PrimeSet& S, int i);
+template <>
+FD_HD uint32_t mod_centred<uint32_t>(uint32_t x, const PrimeSet& S, int i) {
+  uint32_t r = mod_u32(x, S, i);
+  uint32_t c = (x >> 31) ? S.r32[i] : 0u;
+  return csub(r + S.p[i] - c, S.p[i]);
+}
+template <>
+FD_HD uint32_t mod_centred<uint64_t>(uint64_t x, const PrimeSet& S, int i) {
+  uint32_t r = mod_u64(x, S, i);
+  uint32_t c = (x >> 63) ? S.r64[i] : 0u;
+  return csub(r + S.p[i] - c, S.p[i]);
+}
+template <typename W>
+FD_HD uint32_t mod_word(W x, const PrimeSet& S, int i);
+template <>
+FD_HD uint32_t mod_word<uint32_t>(uint32_t x, const PrimeSet& S, int i) { return mod_u32(x, S, i); }
+template <>
+FD_HD uint32_t mod_word<uint64_t>(uint64_t x, const PrimeSet& S, int i) { return mod_u64(x, S, i); }
+
+// Garner reconstruction of the centred integer with residues x[i] in [0, p_i),
+// reduced mod 2^64 (callers truncate to w bits).
+FD_HD uint64_t garner(const uint32_t* x, const PrimeSet& S) {
+  uint32_t y[kMaxPrimes];
+  y[0] = x[0];
+  uint64_t X = y[0];
+#pragma unroll
+  for (int j = 1; j < kMaxPrimes; ++j) {
+    if (j < S.P) {
+      uint32_t pj = S.p[j];
+      uint32_t v = x[j];
+#pragma unroll
+      for (int i = 0; i < kMaxPrimes; ++i) {
+        if (i < j) {
+          // v <- (v - y_i) * p_i^-1 mod p_j ; y_i < p_i < 2 p_j
+          uint32_t d = v + 2 * pj - y[i];
+          v = csub(mul_shoup(d, S.gc[i][j], S.gcs[i][j], pj), pj);
+        }
+      }
+      y[j] = v;
+      X += S.M[j] * (uint64_t)v;
+    }
+  }
+  if (y[S.P - 1] > S.half_top) X -= S.M[S.P];
+  return X;
+}
+
+// ---------------------------------------------------------------------------
+// NTT register layouts.
+//
+// One NTT of size N = 2^L is computed by G = 2^(L-EL) threads, each holding
+// E = 2^EL coefficients in registers.  The L butterfly stages are split into
+// K passes of at most EL stages; inside a pass all butterflies are between
+// registers of one thread, and between passes the coefficients are exchanged
+// through shared memory.  Pass k < K-1 holds, in thread t and register r, the
+// element
+//     j = (t_hi << (L - k EL)) | (r << (L - (k+1) EL)) | t_lo,
+// t_lo the low L-(k+1)EL bits of t; the last pass holds j = t E + r.
+// The forward transform (Cooley-Tukey, merged psi twist, natural order in,
+// bit-reversed order out) runs the passes 0..K-1; the inverse
+// (Gentleman-Sande, bit-reversed in, natural out) runs them backwards.
+// Stage s of the forward transform pairs bit L-1-s of j and uses twiddle
+// index 2^s + (j >> (L - s)); the inverse stage on bit b uses
+// (N >> (b+1)) + (j >> (b+1)).
+// ---------------------------------------------------------------------------
+template <int L, int EL>
+struct Layout {
+  static constexpr int N = 1 << L;
+  static constexpr int E = 1 << EL;
+  static constexpr int G = 1 << (L - EL);
+  static constexpr int K = (L + EL - 1) / EL;
+  static constexpr int LAST = L - (K - 1) * EL;  // stages in the last pass
+
+  FD_HD static int j_of(int pass, int t, int r) {
+    if (pass == K - 1) return t * E + r;
+    const int lo_bits = L - (pass + 1) * EL;
+    const int tlo = t & ((1 << lo_bits) - 1);
+    const int thi = t >> lo_bits;
+    return (thi << (L - pass * EL)) | (r << lo_bits) | tlo;
+  }
+  // stages of pass k: [first, first + len)
+  FD_HD static constexpr int first(int pass) { return pass * EL; }
+  FD_HD static constexpr int len(int pass) { return pass == K - 1 ? LAST : EL; }
+  // register-bit of the butterfly partner for stage s of pass k
+  FD_HD static constexpr int rbit(int pass, int s) {
+    return pass == K - 1 ? (LAST - 1 - (s - first(pass))) : (EL - 1 - (s - first(pass)));
+  }
+};
+
+// Forward Cooley-Tukey butterfly (Harvey's lazy form): X, Y in [0, 4p) ->
+// X + WY, X - WY + 2p, both in [0, 4p).
+FD_HD void bfly_fwd(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p) {
+  uint32_t x = csub(X, 2 * p);
+  uint32_t t = mul_shoup(Y, w.x, w.y, p);
+  X = x + t;
+  Y = x - t + 2 * p;
+}
+// Inverse Gentleman-Sande butterfly: X, Y in [0, 2p) -> X + Y, (X - Y) W.
+FD_HD void bfly_inv(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p) {
+  uint32_t s = csub(X + Y, 2 * p);
+  uint32_t d = X - Y + 2 * p;
+  X = s;
+  Y = mul_shoup(d, w.x, w.y, p);
+}
+
+#ifdef __CUDA_ARCH__
+#define FD_LDG(ptr) __ldg(ptr)
+#else
+#define FD_LDG(ptr) (*(ptr))
+#endif
+
+// All stages of forward pass `pass` on the E registers of thread t.
+template <int L, int EL, int PASS>
+FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) {
+  using Y = Layout<L, EL>;
+  constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
+#pragma unroll
+  for (int s = F; s < F + LEN; ++s) {
+    const int rb = Y::rbit(PASS, s);
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      if (!(r & (1 << rb))) {
+        const int j = Y::j_of(PASS, t, r);
+        const uint2 w = FD_LDG(tw + (1 << s) + (j >> (L - s)));
+        bfly_fwd(v[r], v[r | (1 << rb)], w, p);
+      }
+    }
+  }
+}
+
+// All stages of inverse pass `pass` (bits ascending) on thread t.
+template <int L, int EL, int PASS>
+FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) {
+  using Y = Layout<L, EL>;
+  constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
+  // stage s of the forward order touches j-bit L-1-s; run them in reverse
+#pragma unroll
+  for (int s = F + LEN - 1; s >= F; --s) {
+    const int b = L - 1 - s;
+    const int rb = Y::rbit(PASS, s);
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      if (!(r & (1 << rb))) {
+        const int j = Y::j_of(PASS, t, r);
+        const uint2 w = FD_LDG(tw + (Y::N >> (b + 1)) + (j >> (b + 1)));
+        bfly_inv(v[r], v[r | (1 << rb)], w, p);
+      }
+    }
+  }
+}
+
+// Shared-memory swizzle for the exchange buffers: XORs the five bank bits of
+// j with a GF(2)-linear function of its higher bits, so that for every pass
+// layout the 32 lanes of a warp hit 32 distinct banks for each register
+// index.  Row b-5 of the table is the 5-bit mask that bit b of j flips; the
+// tables were found by exhaustive search over the lane-bit patterns of the
+// layouts above.
+template <int L, int EL>
+FD_HD constexpr uint32_t swz_mask(int b) {
+  if (L == 8 && EL == 3) { constexpr uint8_t m[] = {4, 9, 18}; return m[b - 5]; }
+  if (L == 9 && EL == 4) { constexpr uint8_t m[] = {2, 4, 8, 17}; return m[b - 5]; }
+  if (L == 10 && EL == 4) { constexpr uint8_t m[] = {1, 4, 8, 18, 0}; return m[b - 5]; }
+  if (L == 10 && EL == 5) { constexpr uint8_t m[] = {1, 2, 4, 8, 16}; return m[b - 5]; }
+  if (L == 11 && EL == 4) { constexpr uint8_t m[] = {1, 2, 8, 20, 0, 0}; return m[b - 5]; }
+  if (L == 11 && EL == 5) { constexpr uint8_t m[] = {1, 2, 4, 8, 16, 0}; return m[b - 5]; }
+  if (L == 12 && EL == 4) { constexpr uint8_t m[] = {1, 2, 4, 24, 0, 0, 0}; return m[b - 5]; }
+  return 0;
+}
+
+template <int L, int EL>
+FD_HD uint32_t swz(uint32_t j) {
+  uint32_t h = 0;
+#pragma unroll
+  for (int b = 5; b < L; ++b)
+    if ((j >> b) & 1u) h ^= swz_mask<L, EL>(b);
+  return j ^ h;
+}
+
+}  // namespace fdfb

@@ -1,0 +1,110 @@
+// Host-side construction of the NTT constants: roots of unity, bit-reversed
+// twiddle tables with Shoup companions, Montgomery and Garner constants.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "fdfb_core.cuh"
+
+namespace fdfb {
+namespace host {
+
+inline uint64_t mulmod(uint64_t a, uint64_t b, uint64_t m) {
+  return (uint64_t)((unsigned __int128)a * b % m);
+}
+inline uint64_t powmod(uint64_t a, uint64_t e, uint64_t m) {
+  uint64_t r = 1 % m;
+  a %= m;
+  while (e) {
+    if (e & 1) r = mulmod(r, a, m);
+    a = mulmod(a, a, m);
+    e >>= 1;
+  }
+  return r;
+}
+inline uint32_t shoup(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+inline uint32_t inv_mod(uint32_t a, uint32_t p) { return (uint32_t)powmod(a, p - 2, p); }
+inline uint32_t bitrev(uint32_t x, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+// Smallest generator of Z_p^* (p prime).
+inline uint32_t generator(uint32_t p) {
+  uint32_t m = p - 1;
+  std::vector<uint32_t> fac;
+  for (uint32_t d = 2; (uint64_t)d * d <= m; ++d)
+    if (m % d == 0) {
+      fac.push_back(d);
+      while (m % d == 0) m /= d;
+    }
+  if (m > 1) fac.push_back(m);
+  for (uint32_t g = 2;; ++g) {
+    bool ok = true;
+    for (uint32_t f : fac)
+      if (powmod(g, (p - 1) / f, p) == 1) { ok = false; break; }
+    if (ok) return g;
+  }
+}
+
+// Fills S (except the table pointers) and the [P][N] forward/inverse twiddle
+// tables for ring degree N = 2^L with the first P primes.
+inline void make_prime_set(int P, int L, PrimeSet& S, std::vector<uint2>& fwd,
+                           std::vector<uint2>& inv) {
+  const uint32_t N = 1u << L;
+  S.P = P;
+  fwd.assign((size_t)P * N, uint2{0, 0});
+  inv.assign((size_t)P * N, uint2{0, 0});
+  for (int i = 0; i < kMaxPrimes; ++i) {
+    const uint32_t p = kPrimes[i];
+    S.p[i] = p;
+    uint32_t x = 1;  // Newton iteration for p^-1 mod 2^32
+    for (int it = 0; it < 5; ++it) x *= 2u - p * x;
+    S.pneg[i] = 0u - x;
+    S.ones[i] = shoup(1, p);
+    S.r32[i] = (uint32_t)(((uint64_t)1 << 32) % p);
+    S.r32s[i] = shoup(S.r32[i], p);
+    S.r64[i] = (uint32_t)mulmod(S.r32[i], S.r32[i], p);
+    const uint32_t ninv = inv_mod(N % p, p);
+    S.ninv_m[i] = (uint32_t)mulmod(ninv, S.r32[i], p);
+    S.ninv_ms[i] = shoup(S.ninv_m[i], p);
+    for (int j = 0; j < kMaxPrimes; ++j) {
+      S.gc[i][j] = 0;
+      S.gcs[i][j] = 0;
+    }
+  }
+  for (int i = 0; i < kMaxPrimes; ++i)
+    for (int j = i + 1; j < kMaxPrimes; ++j) {
+      S.gc[i][j] = inv_mod(kPrimes[i] % kPrimes[j], kPrimes[j]);
+      S.gcs[i][j] = shoup(S.gc[i][j], kPrimes[j]);
+    }
+  S.M[0] = 1;
+  for (int i = 0; i < kMaxPrimes; ++i) S.M[i + 1] = S.M[i] * (uint64_t)kPrimes[i];
+  S.half_top = kPrimes[P - 1] / 2;
+  for (int i = 0; i < P; ++i) {
+    const uint32_t p = kPrimes[i];
+    const uint32_t g = generator(p);
+    const uint32_t psi = (uint32_t)powmod(g, (p - 1) / (2 * N), p);  // primitive 2N-th root
+    const uint32_t psi_inv = inv_mod(psi, p);
+    for (uint32_t k = 0; k < N; ++k) {
+      uint32_t e = bitrev(k, L);
+      uint32_t wf = (uint32_t)powmod(psi, e, p);
+      uint32_t wi = (uint32_t)powmod(psi_inv, e, p);
+      fwd[(size_t)i * N + k] = uint2{wf, shoup(wf, p)};
+      inv[(size_t)i * N + k] = uint2{wi, shoup(wi, p)};
+    }
+  }
+}
+
+// log2 of the largest |centred result| the prime set can lift exactly:
+// the top Garner digit must stay below p_{P-1}/2 - 1 for both signs.
+inline bool lift_is_exact(int P, long double max_abs) {
+  long double m = 1;
+  for (int i = 0; i < P - 1; ++i) m *= (long double)kPrimes[i];
+  return max_abs / m + 2.0L < (long double)(kPrimes[P - 1] / 2);
+}
+
+}  // namespace host
+}  // namespace fdfb

@@ -1,0 +1,55 @@
+// Explicit instantiation of the kernels for one (L, EL, P, W) combination.
+#pragma once
+#include "fdfb_ops.hpp"
+
+namespace fdfb {
+
+template <int L, int EL, int P, typename W>
+struct Inst {
+  using Sh = BRShape<L, EL, P, W>;
+  static constexpr int THREADS = Sh::THREADS;
+  static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
+  static cudaError_t br_prepare(size_t smem) {
+    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    blind_rotate_kernel<L, EL, P, W><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    return cudaGetLastError();
+  }
+  static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    constexpr size_t sm = product_smem_bytes<L, EL, P>();
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(pubmux_kernel<L, EL, P, W>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    pubmux_kernel<L, EL, P, W><<<(unsigned)batch, THREADS, sm, st>>>(prm);
+    return cudaGetLastError();
+  }
+  static cudaError_t rlwe_enc(const RlweEncParams& prm, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    constexpr size_t sm = product_smem_bytes<L, EL, P>();
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(rlwe_encrypt_kernel<L, EL, P, W>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    rlwe_encrypt_kernel<L, EL, P, W><<<(unsigned)count, THREADS, sm, st>>>(prm);
+    return cudaGetLastError();
+  }
+  static cudaError_t bsk_ntt(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
+                             cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    constexpr size_t sm = (size_t)P * (1 << L) * 4;
+    bsk_to_ntt_kernel<L, EL, P, W><<<(unsigned)rows, THREADS, sm, st>>>(S, bsk, R, out);
+    return cudaGetLastError();
+  }
+  static Ops ops() {
+    return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, &br_smem, &br_prepare, &br, &pubmux, &rlwe_enc, &bsk_ntt};
+  }
+};
+
+}  // namespace fdfb

@@ -1,0 +1,576 @@
+// Device kernels of the FDFB pipeline (templated on the ring degree 2^L, the
+// registers per thread 2^EL, the prime count P and the word type W).
+#pragma once
+#include <stdint.h>
+
+#include "fdfb_core.cuh"
+
+namespace fdfb {
+
+template <typename W> struct Word;
+template <> struct Word<uint32_t> { static constexpr int bits = 32; };
+template <> struct Word<uint64_t> { static constexpr int bits = 64; };
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Forward negacyclic NTT of one polynomial by one thread group: v holds the
+// pass-0 layout (natural order) on entry and the last-pass layout
+// (bit-reversed order, values in [0, 4p)) on exit.  xb is the group's
+// exchange buffer (N words), bar its named barrier.
+template <int L, int EL, int PASS>
+__device__ __forceinline__ void ntt_fwd(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
+                                        uint32_t* xb, int bar) {
+  using Y = Layout<L, EL>;
+  if constexpr (PASS < Y::K) {
+    if constexpr (PASS > 0) {
+      const uint32_t wb = swz<L, EL>(Y::j_of(PASS - 1, t, 0));
+#pragma unroll
+      for (int r = 0; r < Y::E; ++r) xb[wb ^ swz<L, EL>(Y::j_of(PASS - 1, 0, r))] = v[r];
+      named_bar(bar, Y::G);
+      const uint32_t rb = swz<L, EL>(Y::j_of(PASS, t, 0));
+#pragma unroll
+      for (int r = 0; r < Y::E; ++r) v[r] = xb[rb ^ swz<L, EL>(Y::j_of(PASS, 0, r))];
+      named_bar(bar, Y::G);
+    }
+    fwd_pass<L, EL, PASS>(v, t, tw, p);
+    ntt_fwd<L, EL, PASS + 1>(v, t, tw, p, xb, bar);
+  }
+}
+
+// Inverse transform: last-pass layout, values in [0, 2p) -> pass-0 layout
+// (natural order), values in [0, 2p).  The 1/N factor is not applied.
+template <int L, int EL, int PASS>
+__device__ __forceinline__ void ntt_inv(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
+                                        uint32_t* xb, int bar) {
+  using Y = Layout<L, EL>;
+  if constexpr (PASS >= 0) {
+    inv_pass<L, EL, PASS>(v, t, tw, p);
+    if constexpr (PASS > 0) {
+      const uint32_t wb = swz<L, EL>(Y::j_of(PASS, t, 0));
+#pragma unroll
+      for (int r = 0; r < Y::E; ++r) xb[wb ^ swz<L, EL>(Y::j_of(PASS, 0, r))] = v[r];
+      named_bar(bar, Y::G);
+      const uint32_t rb = swz<L, EL>(Y::j_of(PASS - 1, t, 0));
+#pragma unroll
+      for (int r = 0; r < Y::E; ++r) v[r] = xb[rb ^ swz<L, EL>(Y::j_of(PASS - 1, 0, r))];
+      named_bar(bar, Y::G);
+    }
+    ntt_inv<L, EL, PASS - 1>(v, t, tw, p, xb, bar);
+  }
+}
+
+// Coefficient j of poly * X^k (k in [0, 2N)): reads poly[j - k] with the sign
+// of the wrap (X^N = -1).  get(m) returns coefficient m.
+template <int L>
+__device__ __forceinline__ int rot_src(int j, int k, bool& neg) {
+  constexpr int N = 1 << L;
+  int m = j - k;
+  neg = false;
+  if (m < 0) { m += N; neg = true; }
+  if (m < 0) { m += N; neg = false; }
+  return m;
+}
+
+// ModSwitch q = 2^w -> 2N = 2^(L+1), round half up (appendix figure
+// "Modulus switching algorithm").
+template <typename W, int L>
+__device__ __forceinline__ uint32_t modswitch_2n(W x) {
+  constexpr int sh = Word<W>::bits - (L + 1);
+  return (uint32_t)((W)(x + ((W)1 << (sh - 1))) >> sh);
+}
+
+// ---------------------------------------------------------------------------
+// Blind rotation (appendix figure "Blind Rotation and its setup", u = {1}):
+// one CTA per ciphertext, P thread groups of G threads, group g computing
+// every product modulo prime g.  For i = 1..n:
+//   d = acc * X^{-a_i} - acc;  D = Decomp(d) (2 lg digit polynomials);
+//   acc += sum_r D_r * bsk[i][r]    (CMux = extProd(C, g - h) + h)
+// The digits are transformed on the fly; the key rows are pre-transformed
+// (centred, scaled by N^-1 in Montgomery form) and stored in the order the
+// transform emits, so each thread reads its own E consecutive words.
+// ---------------------------------------------------------------------------
+struct BRParams {
+  PrimeSet S;
+  const uint32_t* bsk;    // [n][P][2 lg][2][N]
+  const void* ct;         // [batch][n+1] words (input LWE, modulus q)
+  const void* acc0;       // function mode: [batch][2N] words; sign mode: nullptr
+  void* lwe_out;          // [batch][N+1] words: SampleExtract(acc, 0) (+ Delta/2 in sign mode)
+  uint32_t* ctN_out;      // optional [batch][n+1]: ModSwitch(ct, q, 2N)
+  int n, lg, log2Bg, rtrunc;
+  int64_t batch;
+  uint64_t delta_half;
+  int sign_mode;
+  uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
+};
+
+template <int L, int EL, int P, typename W>
+struct BRShape {
+  using Y = Layout<L, EL>;
+  static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  static size_t smem_bytes(int n, int lg, uint32_t* r1_off, uint32_t* exch_off) {
+    size_t acc = 2 * (size_t)N * sizeof(W);
+    size_t an = ((size_t)n * 2 + 15) & ~(size_t)15;
+    size_t dig = 2 * (size_t)lg * N * 2;
+    size_t stage = (size_t)P * 2 * N * 4;
+    size_t r1 = dig > stage ? dig : stage;
+    *r1_off = (uint32_t)(acc + an);
+    *exch_off = (uint32_t)(acc + an + r1);
+    return acc + an + r1 + (size_t)P * N * 4;
+  }
+};
+
+template <int L, int EL, int P, typename W>
+__global__ void __launch_bounds__(P * (1 << (L - EL)))
+blind_rotate_kernel(const BRParams prm) {
+  using Y = Layout<L, EL>;
+  constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  constexpr int WB = Word<W>::bits;
+  extern __shared__ __align__(16) unsigned char smem[];
+  W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
+  uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
+  uint16_t* dig = reinterpret_cast<uint16_t*>(smem + prm.smem_r1);          // [2 lg][N]
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem + prm.smem_r1);        // [P][2][N]
+  uint32_t* exch = reinterpret_cast<uint32_t*>(smem + prm.smem_exch);       // [P][N]
+
+  const int tid = threadIdx.x;
+  const int grp = tid / G;
+  const int t = tid - grp * G;
+  const int64_t ci = blockIdx.x;
+  const int n = prm.n, lg = prm.lg, log2Bg = prm.log2Bg;
+  const W* ct = reinterpret_cast<const W*>(prm.ct) + ci * (n + 1);
+
+  // ModSwitch of the mask; b_N for the sign accumulator.
+  for (int i = tid; i < n; i += THREADS) {
+    uint32_t a = modswitch_2n<W, L>(ct[1 + i]);
+    aN[i] = (uint16_t)a;
+    if (prm.ctN_out) prm.ctN_out[ci * (n + 1) + 1 + i] = a;
+  }
+  if (prm.sign_mode) {
+    const int bN = (int)modswitch_2n<W, L>(ct[0]);
+    if (prm.ctN_out && tid == 0) prm.ctN_out[ci * (n + 1)] = (uint32_t)bN;
+    // acc = [(Delta/2) sgnP X^{b_N}, 0], sgnP = 1 - sum_{i>=2} X^{i-1}
+    const W h = (W)prm.delta_half;
+    for (int j = tid; j < N; j += THREADS) {
+      bool neg;
+      int m = rot_src<L>(j, bN, neg);
+      W c = (m == 0) ? h : (W)(0 - h);
+      acc[j] = neg ? (W)(0 - c) : c;
+      acc[N + j] = 0;
+    }
+  } else {
+    const W* a0 = reinterpret_cast<const W*>(prm.acc0) + ci * 2 * N;
+    for (int j = tid; j < 2 * N; j += THREADS) acc[j] = a0[j];
+  }
+  __syncthreads();
+
+  const uint32_t p = prm.S.p[grp];
+  const uint32_t pneg = prm.S.pneg[grp];
+  const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
+  const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
+  uint32_t* xb = exch + grp * N;
+  const int bar = 1 + grp;
+  const int rt = prm.rtrunc;
+  const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
+  const uint32_t dmask = (1u << log2Bg) - 1;
+  const int R = 2 * lg;
+
+  for (int i = 0; i < n; ++i) {
+    const int a = aN[i];
+    // d = acc X^{-a} - acc, rounded and split into digits (component major).
+    for (int idx = tid; idx < 2 * N; idx += THREADS) {
+      const int c = idx >> L, j = idx & (N - 1);
+      int m = j + a;
+      bool neg = false;
+      if (m >= N) { m -= N; neg = true; }
+      if (m >= N) { m -= N; neg = false; }
+      W rv = acc[c * N + m];
+      if (neg) rv = (W)(0 - rv);
+      const W d = (W)(rv - acc[c * N + j]);
+      const W xt = rt ? (W)((W)(d + half_rt) >> rt) : d;
+      for (int l = 0; l < lg; ++l)
+        dig[(c * lg + l) * N + j] = (uint16_t)((uint32_t)(xt >> (l * log2Bg)) & dmask);
+    }
+    __syncthreads();
+
+    uint64_t macc[2][E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
+    const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N + (size_t)t * E;
+    for (int r = 0; r < R; ++r) {
+      uint32_t v[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k) v[k] = dig[r * N + Y::j_of(0, t, k)];
+      ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + c) * N);
+#pragma unroll
+        for (int q4 = 0; q4 < E / 4; ++q4) {
+          const uint4 kk = __ldg(kp + q4);
+          const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t x = csub(csub(v[q4 * 4 + u], 2 * p), p);
+            macc[c][q4 * 4 + u] += (uint64_t)x * kv[u];
+          }
+        }
+      }
+    }
+    __syncthreads();  // every group is done with the digits: the region becomes `stage`
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint32_t v[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k) v[k] = csub(redc(macc[c][k], p, pneg), p);
+      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar);
+#pragma unroll
+      for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 2 * N; idx += THREADS) {
+      uint32_t x[kMaxPrimes];
+#pragma unroll
+      for (int g = 0; g < kMaxPrimes; ++g) x[g] = g < P ? stage[g * 2 * N + idx] : 0u;
+      acc[idx] = (W)(acc[idx] + (W)garner(x, prm.S));
+    }
+    __syncthreads();
+  }
+
+  // SampleExtract of coefficient 0 (appendix figure "Sample and key
+  // extraction", NSgn(x) = 1 iff x > 0): b' = b_0, a'_0 = a_0, a'_k = -a_{N-k}.
+  W* out = reinterpret_cast<W*>(prm.lwe_out) + ci * (N + 1);
+  for (int k = tid; k <= N; k += THREADS) {
+    W v;
+    if (k == 0) v = (W)(acc[0] + (prm.sign_mode ? (W)prm.delta_half : (W)0));
+    else if (k == 1) v = acc[N];
+    else v = (W)(0 - acc[N + (N - (k - 1))]);
+    out[k] = v;
+  }
+  (void)WB;
+}
+
+// ---------------------------------------------------------------------------
+// Exact product of a small unsigned polynomial (coefficients < 2^16) with one
+// or two word polynomials, all modulo X^N + 1 and 2^w, plus an addend.  Used
+// by PubMux (BuildAcc, figure "cmux-accumulator-builder") and by RLWE
+// encryption during key generation.  One CTA per item, P groups.
+// ---------------------------------------------------------------------------
+template <int L, int EL, int P, typename W, typename SmallF, typename WordF, typename OutF>
+__device__ __forceinline__ void small_word_product(const PrimeSet& S, int ncols, SmallF small,
+                                                   WordF word, OutF out, unsigned char* smem) {
+  using Y = Layout<L, EL>;
+  constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);          // [P][2][N]
+  uint32_t* exch = stage + P * 2 * N;                           // [P][N]
+  const int tid = threadIdx.x;
+  const int grp = tid / G;
+  const int t = tid - grp * G;
+  const uint32_t p = S.p[grp];
+  const uint32_t pneg = S.pneg[grp];
+  const uint2* twf = S.tw_fwd + (size_t)grp * N;
+  const uint2* twi = S.tw_inv + (size_t)grp * N;
+  uint32_t* xb = exch + grp * N;
+  const int bar = 1 + grp;
+
+  uint32_t sv[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) sv[k] = small(Y::j_of(0, t, k));
+  ntt_fwd<L, EL, 0>(sv, t, twf, p, xb, bar);
+#pragma unroll
+  for (int k = 0; k < E; ++k) sv[k] = csub(csub(sv[k], 2 * p), p);
+  for (int c = 0; c < ncols; ++c) {
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) v[k] = mod_word<W>(word(c, Y::j_of(0, t, k)), S, grp);
+    ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint32_t x = csub(csub(v[k], 2 * p), p);
+      const uint32_t m = csub(redc((uint64_t)x * sv[k], p, pneg), p);          // x s 2^-32
+      v[k] = csub(mul_shoup(m, S.ninv_m[grp], S.ninv_ms[grp], p), p);         // * N^-1 2^32
+    }
+    ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar);
+#pragma unroll
+    for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ncols * N; idx += THREADS) {
+    uint32_t x[kMaxPrimes];
+#pragma unroll
+    for (int g = 0; g < kMaxPrimes; ++g) x[g] = g < P ? stage[g * 2 * N + idx] : 0u;
+    out(idx / N, idx % N, (W)garner(x, S));
+  }
+}
+
+template <int L, int EL, int P>
+constexpr size_t product_smem_bytes() {
+  return (size_t)P * 3 * (1 << L) * 4;
+}
+
+// PubMux with L_boot = t (one digit): acc_F = [Delta p0, 0] + ((p1 - p0) mod t) * c_R
+// with (p0, p1) = (rotP'_1, rotP'_0), rotP'_j = rotP_j X^{b_N}.
+struct PubMuxParams {
+  PrimeSet S;
+  const void* cR;          // [batch][2N]
+  const void* ct;          // [batch][n+1] input LWE (for b_N)
+  const int32_t* lut_ids;  // [batch]
+  const int16_t* luts;     // [n_luts][2][N]  (rotP_0, rotP_1)
+  int n_luts;
+  void* accF;              // [batch][2N]
+  int n, t;
+  uint64_t delta;
+  int* err;                // device error latch
+};
+
+template <int L, int EL, int P, typename W>
+__global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_kernel(const PubMuxParams prm) {
+  constexpr int N = 1 << L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t ci = blockIdx.x;
+  const W* ct = reinterpret_cast<const W*>(prm.ct) + ci * (prm.n + 1);
+  const int bN = (int)modswitch_2n<W, L>(ct[0]);
+  int lut = prm.lut_ids[ci];
+  if (lut < 0 || lut >= prm.n_luts) {
+    if (threadIdx.x == 0) atomicExch(prm.err, -6);
+    lut = 0;
+  }
+  const int16_t* r0 = prm.luts + (size_t)lut * 2 * N;
+  const int16_t* r1 = r0 + N;
+  const int tmask = prm.t - 1;
+  auto rotated = [&](const int16_t* poly, int j) -> int {
+    bool neg;
+    int m = rot_src<L>(j, bN, neg);
+    int v = poly[m];
+    return neg ? -v : v;
+  };
+  const W* cR = reinterpret_cast<const W*>(prm.cR) + ci * 2 * N;
+  W* out = reinterpret_cast<W*>(prm.accF) + ci * 2 * N;
+  const W delta = (W)prm.delta;
+  small_word_product<L, EL, P, W>(
+      prm.S, 2,
+      [&](int j) -> uint32_t { return (uint32_t)((rotated(r0, j) - rotated(r1, j)) & tmask); },
+      [&](int c, int j) -> W { return cR[c * N + j]; },
+      [&](int c, int j, W x) {
+        if (c == 0) x = (W)(x + delta * (W)(int64_t)rotated(r1, j));
+        out[c * N + j] = x;
+      },
+      smem);
+}
+
+// RLWE encryption: out[item] = [a sk + e, a], then mu[item] added to the
+// constant coefficient of component comp[item] (GGSW rows and packing-key
+// samples).  sk is binary.
+struct RlweEncParams {
+  PrimeSet S;
+  const uint8_t* sk;       // [N]
+  const void* a;           // [count][N] words
+  const int64_t* e;        // [count][N]
+  const uint64_t* mu;      // [count]
+  const uint8_t* comp;     // [count]
+  void* out;               // [count][2][N]
+};
+
+template <int L, int EL, int P, typename W>
+__global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_kernel(const RlweEncParams prm) {
+  constexpr int N = 1 << L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t it = blockIdx.x;
+  const W* a = reinterpret_cast<const W*>(prm.a) + it * N;
+  const int64_t* e = prm.e + it * N;
+  W* out = reinterpret_cast<W*>(prm.out) + it * 2 * N;
+  const W mu = (W)prm.mu[it];
+  const int comp = prm.comp[it];
+  small_word_product<L, EL, P, W>(
+      prm.S, 1, [&](int j) -> uint32_t { return prm.sk[j]; },
+      [&](int, int j) -> W { return a[j]; },
+      [&](int, int j, W x) {
+        W b = (W)(x + (W)e[j]);
+        W av = a[j];
+        if (j == 0) {
+          if (comp == 0) b = (W)(b + mu); else av = (W)(av + mu);
+        }
+        out[j] = b;
+        out[N + j] = av;
+      },
+      smem);
+}
+
+// Converts canonical GGSW rows [n][2 lg][2][N] into the transform domain:
+// out[i][g][r][c][.] = NTT(centred(bsk[i][r][c]) mod p_g) * N^-1 * 2^32 mod p_g,
+// stored in the transform's output order.
+template <int L, int EL, int P, typename W>
+__global__ void __launch_bounds__(P * (1 << (L - EL)))
+bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
+  using Y = Layout<L, EL>;
+  constexpr int N = Y::N, E = Y::E, G = Y::G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* exch = reinterpret_cast<uint32_t*>(smem);
+  const int64_t row = blockIdx.x;  // i * R + r
+  const int64_t i = row / R;
+  const int r = (int)(row % R);
+  const int tid = threadIdx.x, grp = tid / G, t = tid - grp * G;
+  const uint32_t p = S.p[grp];
+  const W* src = reinterpret_cast<const W*>(bsk) + row * 2 * N;
+  for (int c = 0; c < 2; ++c) {
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) v[k] = mod_centred<W>(src[c * N + Y::j_of(0, t, k)], S, grp);
+    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * N, 1 + grp);
+    uint32_t* dst = out + (((size_t)i * P + grp) * R + r) * 2 * N + (size_t)c * N;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint32_t x = csub(csub(v[k], 2 * p), p);
+      dst[Y::j_of(Y::K - 1, t, k)] = csub(mul_shoup(x, S.ninv_m[grp], S.ninv_ms[grp], p), p);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Key switching (appendix figure "Key switching algorithm and its setup"):
+//   out[m] = [b_m, 0, ..] - sum_{i<n_in} sum_{j<l} Decomp(a_{m,i})_j key[i][j]
+// as a tiled integer GEMM: rows m (ciphertexts), columns (output words),
+// reduction over (i, j) with the digits generated on the fly.
+// ---------------------------------------------------------------------------
+constexpr int KS_BM = 32, KS_BN = 64, KS_BK = 32, KS_THREADS = 256;  // 2 x 4 outputs per thread
+
+template <typename W>
+__global__ void __launch_bounds__(KS_THREADS)
+keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __restrict__ key,
+                 int ell, int log2B, int rtrunc, int out_len, W* __restrict__ out) {
+  __shared__ uint16_t sa[KS_BK][KS_BM];
+  __shared__ W sb[KS_BK][KS_BN];
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.y * KS_BM;
+  const int c0 = blockIdx.x * KS_BN;
+  const int tm = tid / 16, tn = tid % 16;  // 16 x 16 threads; thread owns rows tm*2.., cols tn*4..
+  W accv[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) accv[a][b] = 0;
+  const int K = n_in * ell;
+  const W half_rt = rtrunc ? ((W)1 << (rtrunc - 1)) : (W)0;
+  const uint32_t dmask = (1u << log2B) - 1;
+  for (int k0 = 0; k0 < K; k0 += KS_BK) {
+    // digits: KS_BK x KS_BM
+    for (int e = tid; e < KS_BK * KS_BM; e += KS_THREADS) {
+      const int kk = e / KS_BM, mm = e % KS_BM;
+      const int k = k0 + kk;
+      const int64_t m = m0 + mm;
+      uint16_t d = 0;
+      if (k < K && m < batch) {
+        const int i = k / ell, j = k - i * ell;
+        const W x = ct[m * (n_in + 1) + 1 + i];
+        const W xt = rtrunc ? (W)((W)(x + half_rt) >> rtrunc) : x;
+        d = (uint16_t)((uint32_t)(xt >> (j * log2B)) & dmask);
+      }
+      sa[kk][mm] = d;
+    }
+    for (int e = tid; e < KS_BK * KS_BN; e += KS_THREADS) {
+      const int kk = e / KS_BN, cc = e % KS_BN;
+      const int k = k0 + kk, c = c0 + cc;
+      sb[kk][cc] = (k < K && c < out_len) ? key[(size_t)k * out_len + c] : (W)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < KS_BK; ++kk) {
+      const uint32_t d0 = sa[kk][tm * 2], d1 = sa[kk][tm * 2 + 1];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const W kv = sb[kk][tn * 4 + b];
+        accv[0][b] += (W)d0 * kv;
+        accv[1][b] += (W)d1 * kv;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int64_t m = m0 + tm * 2 + a;
+    if (m >= batch) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tn * 4 + b;
+      if (c >= out_len) continue;
+      W v = (W)(0 - accv[a][b]);
+      if (c == 0) v = (W)(v + ct[m * (n_in + 1)]);
+      out[m * out_len + c] = v;
+    }
+  }
+}
+
+// LWE encryption b = <a, s> + e + Delta m, one warp per ciphertext.
+template <typename W>
+__global__ void lwe_encrypt_kernel(const uint8_t* s, const W* a, const int64_t* e, const int64_t* m,
+                                   int64_t count, int n, uint64_t delta, W* out) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= count) return;
+  W acc = 0;
+  for (int i = lane; i < n; i += 32) {
+    const W ai = a[c * n + i];
+    acc = (W)(acc + ai * (W)s[i]);
+    out[c * (n + 1) + 1 + i] = ai;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = (W)(acc + __shfl_xor_sync(0xffffffffu, acc, o));
+  if (lane == 0) out[c * (n + 1)] = (W)(acc + (W)e[c] + (W)delta * (W)m[c]);
+}
+
+// Decryption round(t * phase / q) mod t (power-of-two t, round half up).
+template <typename W>
+__global__ void lwe_decrypt_kernel(const uint8_t* s, const W* ct, int64_t count, int n, int logt,
+                                   int32_t* m) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= count) return;
+  W acc = 0;
+  for (int i = lane; i < n; i += 32) acc = (W)(acc + ct[c * (n + 1) + 1 + i] * (W)s[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = (W)(acc + __shfl_xor_sync(0xffffffffu, acc, o));
+  if (lane == 0) {
+    constexpr int WB = Word<W>::bits;
+    const W ph = (W)(ct[c * (n + 1)] - acc);
+    const W r = (W)((W)(ph + ((W)1 << (WB - logt - 1))) >> (WB - logt));
+    m[c] = (int32_t)r;
+  }
+}
+
+// y[b][o][k] = sum_i W[o][i] x[b][i][k] mod q: one block per (b, o-tile, k-tile).
+constexpr int AFF_TO = 8, AFF_TK = 128;
+template <typename W>
+__global__ void __launch_bounds__(AFF_TK)
+lwe_affine_kernel(const int32_t* __restrict__ Wm, int n_in, int n_out, const W* __restrict__ x,
+                  int len, W* __restrict__ y) {
+  const int64_t b = blockIdx.z;
+  const int o0 = blockIdx.y * AFF_TO;
+  const int k = blockIdx.x * AFF_TK + threadIdx.x;
+  __shared__ int32_t sw[AFF_TO][64];
+  W acc[AFF_TO];
+#pragma unroll
+  for (int o = 0; o < AFF_TO; ++o) acc[o] = 0;
+  for (int i0 = 0; i0 < n_in; i0 += 64) {
+    for (int e = threadIdx.x; e < AFF_TO * 64; e += AFF_TK) {
+      const int oo = e / 64, ii = e % 64;
+      sw[oo][ii] = (o0 + oo < n_out && i0 + ii < n_in) ? Wm[(size_t)(o0 + oo) * n_in + i0 + ii] : 0;
+    }
+    __syncthreads();
+    if (k < len) {
+      const int iend = min(64, n_in - i0);
+      for (int ii = 0; ii < iend; ++ii) {
+        const W xv = x[((size_t)b * n_in + i0 + ii) * len + k];
+#pragma unroll
+        for (int o = 0; o < AFF_TO; ++o) acc[o] = (W)(acc[o] + (W)(int64_t)sw[o][ii] * xv);
+      }
+    }
+    __syncthreads();
+  }
+  if (k < len)
+#pragma unroll
+    for (int o = 0; o < AFF_TO; ++o)
+      if (o0 + o < n_out) y[((size_t)b * n_out + o0 + o) * len + k] = acc[o];
+}
+
+}  // namespace fdfb

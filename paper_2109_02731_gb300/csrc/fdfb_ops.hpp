@@ -1,0 +1,25 @@
+// Per-(ring degree, word size) table of launchers for the templated kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fdfb_kernels.cuh"
+
+namespace fdfb {
+
+struct Ops {
+  int L, EL, P, w, threads;
+  size_t (*br_smem)(int n, int lg, uint32_t* r1_off, uint32_t* exch_off);
+  cudaError_t (*br_prepare)(size_t smem);
+  cudaError_t (*br)(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st);
+  cudaError_t (*pubmux)(const PubMuxParams& prm, int64_t batch, cudaStream_t st);
+  cudaError_t (*rlwe_enc)(const RlweEncParams& prm, int64_t count, cudaStream_t st);
+  cudaError_t (*bsk_ntt)(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
+                         cudaStream_t st);
+};
+
+// Returns the launcher table for N = 2^L and word size w, or nullptr.
+const Ops* find_ops(int L, int w);
+
+}  // namespace fdfb

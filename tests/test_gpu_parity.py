@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU
+oracle on the same seeded inputs.  Ciphertext arithmetic is exact integer
+arithmetic mod 2^w, so every comparison is bit-exact (tolerance 0)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2109_02731_gb300 import synth as S
+
+from _fdfb_cases import fresh_cts, luts, oracle_keys
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def F(torch_cuda):
+    from paper_2109_02731_gb300 import fdfb
+    return fdfb
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context(0)
+    yield c
+    c.close()
+
+
+_installed = {}
+
+
+def install(ctx, oracle, name, seed, luts_count=1, group=0, generate=False):
+    """Registers set `name`, installs the oracle's keys (or generates them on
+    the GPU from the same randomness) and the lookup tables."""
+    key = (id(ctx), name, seed, luts_count, group, generate)
+    if key in _installed:
+        return _installed[key]
+    ps = S.PARAM_SETS[name]
+    sid = ctx.register(ps)
+    if generate:
+        ctx.keys_generate(sid, S.key_randomness(ps, seed))
+    else:
+        K = oracle_keys(name, seed)
+        ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    fs, _ = luts(name, seed, luts_count, group)
+    ids = [ctx.lut_setup(sid, f) for f in fs]
+    assert ids == list(range(luts_count))
+    _installed[key] = sid
+    return sid
+
+
+def run_gpu(F, torch, ctx, sid, ps, cts, lut_ids, debug=True):
+    dev = "cuda"
+    b = len(cts)
+    ct_d = F.to_device_words(ps, cts)
+    ids_d = torch.tensor(np.asarray(lut_ids, dtype=np.int32), device=dev)
+    out_d = torch.empty_like(ct_d)
+    wt = F.word_torch(ps)
+    dbg = None
+    if debug:
+        dbg = dict(ctN=torch.empty((b, ps.n + 1), dtype=torch.int32, device=dev),
+                   sgn=torch.empty((b, ps.N + 1), dtype=wt, device=dev),
+                   cR=torch.empty((b, 2 * ps.N), dtype=wt, device=dev),
+                   accF=torch.empty((b, 2 * ps.N), dtype=wt, device=dev),
+                   cQ=torch.empty((b, ps.N + 1), dtype=wt, device=dev))
+        ctx.bootstrap_debug(sid, ct_d, ids_d, out_d, dbg)
+    else:
+        ctx.bootstrap(sid, ct_d, ids_d, out_d)
+    ctx.sync()
+    out = F.to_host_words(ps, out_d).astype(np.uint64)
+    if not debug:
+        return out, None
+    host = {k: (v.cpu().numpy().view(np.uint32) if k == "ctN" else F.to_host_words(ps, v)).astype(np.uint64)
+            for k, v in dbg.items()}
+    return out, host
+
+
+def check_against_oracle(oracle, ps, K, rot, cts, lut_ids, out, dbg, idx):
+    for c in idx:
+        o, d = oracle.fdfb_bootstrap(ps, K, rot[lut_ids[c]][0], rot[lut_ids[c]][1], cts[c], debug=True)
+        assert np.array_equal(dbg["ctN"][c], d["ctN"]), f"ModSwitch differs, ct {c}"
+        assert np.array_equal(dbg["sgn"][c], d["sgn"]), f"sign LWE differs, ct {c}"
+        assert np.array_equal(dbg["cR"][c], d["cR"]), f"packing key switch differs, ct {c}"
+        assert np.array_equal(dbg["accF"][c], d["accF"]), f"PubMux differs, ct {c}"
+        assert np.array_equal(dbg["cQ"][c], d["cQ"]), f"function rotation differs, ct {c}"
+        assert np.array_equal(out[c], o), f"output differs, ct {c}"
+
+
+# ------------------------------------------------------------------ keygen --
+
+@pytest.mark.parametrize("name", ["Z", "A", "B"])
+def test_keygen_parity_full(ctx, oracle, name):
+    """GPU key generation (exact NTT products) equals the oracle's schoolbook
+    keys word for word."""
+    ps = S.PARAM_SETS[name]
+    sid = ctx.register(ps)
+    kr = S.key_randomness(ps, 11)
+    ctx.keys_generate(sid, kr)
+    bsk, pk, ksk = ctx.keys_download(sid)
+    K = oracle.Keys(ps, kr)
+    assert np.array_equal(bsk.astype(np.uint64), K.bsk)
+    assert np.array_equal(pk.astype(np.uint64), K.pk)
+    assert np.array_equal(ksk.astype(np.uint64), K.ksk)
+
+
+@pytest.mark.parametrize("name", ["D", "C"])
+def test_keygen_parity_sampled(ctx, oracle, name):
+    """Full-size key generation on the GPU; sampled rows recomputed by the oracle."""
+    ps = S.PARAM_SETS[name]
+    sid = ctx.register(ps)
+    kr = S.key_randomness(ps, 12)
+    ctx.keys_generate(sid, kr)
+    bsk, pk, ksk = ctx.keys_download(sid)
+    rng = np.random.default_rng(0)
+    for i, r in [(0, 0), (ps.n - 1, 2 * ps.lg - 1)] + [(int(rng.integers(ps.n)), int(rng.integers(2 * ps.lg)))
+                                                      for _ in range(3)]:
+        assert np.array_equal(bsk[i, r].astype(np.uint64), oracle.keygen_bsk_row(ps, kr, i, r)), (i, r)
+    for i, j in [(0, 0), (ps.N - 1, ps.lpk - 1), (int(rng.integers(ps.N)), int(rng.integers(ps.lpk)))]:
+        assert np.array_equal(pk[i, j].astype(np.uint64), oracle.keygen_pk_row(ps, kr, i, j)), (i, j)
+    for i, j in [(0, 0), (ps.N - 1, ps.lks - 1), (7, 3)]:
+        mu = int(kr.sk[i]) * oracle.gadget(ps.w, ps.log2Bks, ps.lks, j)
+        ref = oracle.lwe_encrypt(ps.w, kr.s, kr.ksk_a[i, j], int(kr.ksk_e[i, j]), mu)
+        assert np.array_equal(ksk[i, j].astype(np.uint64), ref)
+
+
+# -------------------------------------------------------------- bootstrap --
+
+def test_fdfb_noiseless_all_functions(F, torch_cuda, ctx, oracle):
+    """Set Z (sigma = 0, exact gadgets): every m in Z_4 and a spread of the
+    256 functions Z_4 -> Z_4; bit-exact with the oracle at every stage, and
+    the output phase is exactly Delta f(m)."""
+    import itertools
+    ps = S.PARAM_SETS["Z"]
+    K = oracle_keys("Z", 0)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    fs = np.array(list(itertools.product(range(4), repeat=4)))[::5]
+    rot = np.stack([np.stack(oracle.setup_polynomial(ps.N, ps.t, f)) for f in fs])
+    for f in fs:
+        ctx.lut_setup(sid, f)
+    ms = np.tile(np.arange(4), len(fs))
+    ids = np.repeat(np.arange(len(fs)), 4).astype(np.int32)
+    mr, cts = fresh_cts("Z", 0, len(ms), K, m=ms)
+    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, range(0, len(ms), 7))
+    for c in range(len(ms)):
+        assert oracle.lwe_phase(ps.w, K.s, out[c]) == ps.delta * int(fs[ids[c], ms[c]])
+
+
+def test_lut_polys_match_oracle(ctx, oracle):
+    """SetupPolynomial on the library side (host code of the C ABI) equals the
+    oracle's, ties included."""
+    for name in ("A", "B", "D"):
+        ps = S.PARAM_SETS[name]
+        sid = ctx.register(ps)
+        fs = S.lut_tables(ps, 5, 3)
+        for f in fs:
+            lid = ctx.lut_setup(sid, f)
+            p0, p1 = ctx.lut_polys(sid, lid)
+            q0, q1 = oracle.setup_polynomial(ps.N, ps.t, f)
+            assert np.array_equal(p0, q0) and np.array_equal(p1, q1)
+
+
+def test_fdfb_toy_workload(F, torch_cuda, ctx, oracle):
+    """The toy workload (set A, 16 ciphertexts, seed 0): all outputs and
+    intermediates bit-exact, and every output decrypts to f(m)."""
+    wl = S.WORKLOADS["toy"]
+    g = wl.groups[0]
+    ps = S.PARAM_SETS[g.set_name]
+    K = oracle_keys(g.set_name, wl.seed)
+    sid = install(ctx, oracle, g.set_name, wl.seed, g.n_luts)
+    fs, rot = luts(g.set_name, wl.seed, g.n_luts)
+    ids = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign)
+    mr, cts = fresh_cts(g.set_name, wl.seed, g.batch, K)
+    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, range(g.batch))
+    got = [oracle.lwe_decrypt(ps.w, ps.t, K.s, o) for o in out]
+    assert got == [int(fs[i][m]) for i, m in zip(ids, mr.m)]
+
+
+@pytest.mark.parametrize("batch", [1, 33, 37, 70])
+def test_fdfb_ragged_batches(F, torch_cuda, ctx, oracle, batch):
+    """Batches that leave partial tiles in the key-switching GEMM."""
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 3)
+    sid = install(ctx, oracle, "A", 3, 3)
+    fs, rot = luts("A", 3, 3)
+    ids = (np.arange(batch) % 3).astype(np.int32)
+    mr, cts = fresh_cts("A", 3, batch, K, group=batch)
+    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, sorted({0, batch // 2, batch - 1}))
+    ref = oracle.fdfb_batch(ps, K, rot, ids, cts)
+    assert np.array_equal(out, ref)
+
+
+def test_fdfb_tfhe_scale_sampled(F, torch_cuda, ctx, oracle):
+    """The TFHE-scale workload (set B) at its full size, 1024 ciphertexts in
+    one call with four tables round robin; sampled ciphertexts recomputed by
+    the oracle, all stages bit-exact."""
+    wl = S.WORKLOADS["tfhe_scale"]
+    g = wl.groups[0]
+    ps = S.PARAM_SETS[g.set_name]
+    K = oracle_keys(g.set_name, wl.seed)
+    sid = install(ctx, oracle, g.set_name, wl.seed, g.n_luts)
+    fs, rot = luts(g.set_name, wl.seed, g.n_luts)
+    ids = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign)
+    mr, cts = fresh_cts(g.set_name, wl.seed, g.batch, K)
+    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, [0, 1, 2, 3, 517, g.batch - 1])
+
+
+def _big_workload(F, torch_cuda, ctx, oracle, name, batch, n_luts, seed, sample):
+    ps = S.PARAM_SETS[name]
+    K = oracle_keys(name, seed)
+    sid = install(ctx, oracle, name, seed, n_luts)
+    fs, rot = luts(name, seed, n_luts)
+    ids = S.lut_assignment(seed, batch, n_luts, "uniform")
+    mr, cts = fresh_cts(name, seed, batch, K)
+    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, sample)
+    # every output decrypts to f(m): decryption on the GPU, checked on the host
+    dev_s = torch_cuda.tensor(K.s, device="cuda")
+    out_d = F.to_device_words(ps, out)
+    m_d = torch_cuda.empty(batch, dtype=torch_cuda.int32, device="cuda")
+    ctx.lwe_decrypt(sid, dev_s, out_d, m_d)
+    ctx.sync()
+    got = m_d.cpu().numpy()
+    want = np.array([fs[i][m] for i, m in zip(ids, mr.m)])
+    assert np.array_equal(got, want), f"{int((got != want).sum())} wrong decryptions"
+
+
+@pytest.mark.slow
+def test_fdfb_set_D_full_batch(F, torch_cuda, ctx, oracle):
+    """Set D (N = 2048, q = 2^64, t = 32) at the mixed workload's batch of
+    1000: sampled bit-exact parity, every output decrypts correctly."""
+    _big_workload(F, torch_cuda, ctx, oracle, "D", 1000, 4, 3, [0, 999])
+
+
+@pytest.mark.slow
+def test_fdfb_large_t_full_batch(F, torch_cuda, ctx, oracle):
+    """The large-plaintext workload (set C, N = 4096, t = 64) at its full
+    4096 ciphertexts and 16 tables: one ciphertext recomputed by the oracle,
+    every output decrypts correctly."""
+    wl = S.WORKLOADS["large_t"]
+    g = wl.groups[0]
+    _big_workload(F, torch_cuda, ctx, oracle, "C", g.batch, g.n_luts, wl.seed, [g.batch - 1])
+
+
+def test_keygen_then_bootstrap_matches_upload(F, torch_cuda, ctx, oracle):
+    """Keys generated on the GPU give the same bootstrap as the oracle's keys."""
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 4)
+    sid_u = install(ctx, oracle, "A", 4, 2)
+    sid_g = install(ctx, oracle, "A", 4, 2, generate=True)
+    ids = np.array([0, 1, 1, 0, 1], np.int32)
+    mr, cts = fresh_cts("A", 4, len(ids), K)
+    out_u, _ = run_gpu(F, torch_cuda, ctx, sid_u, ps, cts, ids, debug=False)
+    out_g, _ = run_gpu(F, torch_cuda, ctx, sid_g, ps, cts, ids, debug=False)
+    assert np.array_equal(out_u, out_g)
+
+
+# ------------------------------------------------------ other entry points --
+
+@pytest.mark.parametrize("name", ["A", "D"])
+def test_keyswitch_entry(F, torch_cuda, ctx, oracle, name):
+    ps = S.PARAM_SETS[name]
+    K = oracle_keys(name, 5)
+    sid = install(ctx, oracle, name, 5, 1)
+    rng = np.random.default_rng(1)
+    cts = rng.integers(0, 1 << 62, size=(45, ps.N + 1), dtype=np.uint64) * np.uint64(4) + \
+        rng.integers(0, 4, size=(45, ps.N + 1), dtype=np.uint64)
+    cts &= np.uint64((1 << ps.w) - 1)
+    ci = F.to_device_words(ps, cts)
+    co = torch_cuda.empty((45, ps.n + 1), dtype=F.word_torch(ps), device="cuda")
+    ctx.keyswitch(sid, ci, co)
+    ctx.sync()
+    got = F.to_host_words(ps, co).astype(np.uint64)
+    for c in range(45):
+        assert np.array_equal(got[c], oracle.keyswitch(ps.w, ps.log2Bks, ps.lks, K.ksk, cts[c]))
+
+
+@pytest.mark.parametrize("name", ["B", "D"])
+def test_lwe_encrypt_decrypt_entries(F, torch_cuda, ctx, oracle, name):
+    ps = S.PARAM_SETS[name]
+    sid = ctx.register(ps)
+    s = S.key_randomness(ps, 6).s
+    mr = S.message_randomness(ps, 6, 300)
+    d = "cuda"
+    ct = torch_cuda.empty((300, ps.n + 1), dtype=F.word_torch(ps), device=d)
+    ctx.lwe_encrypt(sid, torch_cuda.tensor(s, device=d), F.to_device_words(ps, mr.a),
+                    torch_cuda.tensor(mr.e, device=d), torch_cuda.tensor(mr.m, device=d), ct)
+    m = torch_cuda.empty(300, dtype=torch_cuda.int32, device=d)
+    ctx.lwe_decrypt(sid, torch_cuda.tensor(s, device=d), ct, m)
+    ctx.sync()
+    ref = oracle.encrypt_messages(ps, s, mr)
+    assert np.array_equal(F.to_host_words(ps, ct).astype(np.uint64), ref)
+    assert np.array_equal(m.cpu().numpy(), [oracle.lwe_decrypt(ps.w, ps.t, s, r) for r in ref])
+
+
+def test_lwe_affine_entry(F, torch_cuda, ctx, oracle):
+    ps = S.PARAM_SETS["D"]
+    sid = ctx.register(ps)
+    rng = np.random.default_rng(2)
+    batch, n_in, n_out = 3, 70, 11
+    W = rng.integers(-8, 8, size=(n_out, n_in)).astype(np.int32)
+    x = rng.integers(0, 1 << 63, size=(batch, n_in, ps.n + 1), dtype=np.uint64)
+    y = torch_cuda.empty((batch, n_out, ps.n + 1), dtype=torch_cuda.int64, device="cuda")
+    ctx.lwe_affine(sid, torch_cuda.tensor(W, device="cuda"), F.to_device_words(ps, x), y)
+    ctx.sync()
+    got = F.to_host_words(ps, y)
+    for b in range(batch):
+        assert np.array_equal(got[b], oracle.lwe_affine(ps.w, W, x[b]))
+
+
+def test_errors_and_edge_cases(F, torch_cuda, ctx, oracle):
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 0)
+    sid = install(ctx, oracle, "A", 0, 1)
+    d = "cuda"
+    ct = torch_cuda.zeros((2, ps.n + 1), dtype=torch_cuda.int32, device=d)
+    out = torch_cuda.zeros_like(ct)
+    # empty batch is a no-op
+    ctx.bootstrap(sid, ct[:0], torch_cuda.zeros(0, dtype=torch_cuda.int32, device=d), out[:0])
+    ctx.sync()
+    # unknown table id is latched and reported by fdfb_sync
+    ctx.bootstrap(sid, ct, torch_cuda.tensor([0, 7], dtype=torch_cuda.int32, device=d), out)
+    with pytest.raises(F.FDFBError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+    ctx.sync()  # latch cleared
+    # keys missing
+    sid2 = ctx.register(ps)
+    ctx.lut_setup(sid2, [0, 1, 2, 3])
+    with pytest.raises(F.FDFBError) as e:
+        ctx.bootstrap(sid2, ct, torch_cuda.zeros(2, dtype=torch_cuda.int32, device=d), out)
+    assert e.value.code == -5
+    # bad table entry, unsupported parameters
+    with pytest.raises(F.FDFBError):
+        ctx.lut_setup(sid, [0, 1, 2, 4])
+    import dataclasses
+    with pytest.raises(F.FDFBError):
+        ctx.register(dataclasses.replace(ps, N=128))
+    with pytest.raises(F.FDFBError):
+        ctx.register(dataclasses.replace(ps, lg=5))
