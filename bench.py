@@ -39,7 +39,8 @@ UNIT = "bootstraps/s"
 L2_FLUSH_BYTES = 512 << 20
 
 # Integer multiplier pipe of the GB300: 152 SMs x 64 IMAD lanes per clock x
-# 2.07 GHz maximum SM clock (derivation and probe measurement in the design doc).
+# 2.07 GHz maximum SM clock; multiply-high issues at half that rate (the
+# probe in paper_2109_02731_gb300/probe/int_pipe.cu measures both).
 SMS = 152
 IMAD_LANES_PER_SM = 64
 SM_MAX_GHZ = 2.07
@@ -52,16 +53,17 @@ def workload_desc(name: str):
     return wl, g, ps
 
 
-def br_algorithmic_muls(ps, batch: int) -> float:
-    """Word multiplications the blind rotation needs per launch (one BR over
-    `batch` ciphertexts): every NTT butterfly is one modular product (3 word
-    multiplies in Shoup's method), every pointwise product-accumulate 1.
-    Per CMux: (2l + 2) P transforms of (N/2) log2 N butterflies and 4 l N P
-    pointwise products; n CMux steps per ciphertext."""
+def br_algorithmic_slots(ps, batch: int) -> float:
+    """Integer-multiplier issue slots the blind rotation needs per launch (one
+    BR over `batch` ciphertexts), counting only the method's modular products:
+    per CMux (2l + 2) P transforms of (N/2) log2 N butterflies, each one Shoup
+    product = 1 multiply-high (2 slots: the pipe runs it at half rate) + 2
+    multiply-low (1 slot each), and 4 l N P pointwise products, each one
+    32x32->64 multiply-add (2 slots); n CMux steps per ciphertext."""
     P = 2 if ps.w == 32 else 3
     bfly = (2 * ps.lg + 2) * P * (ps.N // 2) * ps.logN
     mac = 4 * ps.lg * ps.N * P
-    return float(batch) * ps.n * (3.0 * bfly + mac)
+    return float(batch) * ps.n * (4.0 * bfly + 2.0 * mac)
 
 
 def sample_clocks(path: str):
@@ -99,6 +101,22 @@ def read_clocks(path: str, gpu_index: int):
         return None
     return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def probe_rates(dev_index: int):
+    """Measured integer-pipe rates of this GPU (T ops/s): IMAD, IMAD.HI, LOP
+    and Harvey butterflies, from paper_2109_02731_gb300/probe/int_pipe.cu."""
+    import ctypes
+    from paper_2109_02731_gb300 import build as B
+    try:
+        lib = ctypes.CDLL(B.build_probe())
+        rates = (ctypes.c_double * 4)()
+        if lib.probe_int_rates(dev_index, rates) != 0:
+            return None
+        return {"imad": rates[0] / 1e12, "imad_hi": rates[1] / 1e12, "lop": rates[2] / 1e12,
+                "butterfly": rates[3] / 1e12, "unit": "T/s"}
+    except Exception as e:  # the probe is evidence, not the measurement
+        return {"error": str(e)[:200]}
 
 
 def dist_setup():
@@ -323,9 +341,9 @@ def main():
     br_ms, br_n = prof["blind_rotate_sign"]
     br2_ms, br2_n = prof["blind_rotate_func"]
     br_avg_s = (br_ms + br2_ms) / max(1, br_n + br2_n) / 1e3
-    muls = br_algorithmic_muls(ps, batch)
-    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T mul/s
-    achieved = muls / br_avg_s / 1e12
+    slots = br_algorithmic_slots(ps, batch)
+    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T slots/s
+    achieved = slots / br_avg_s / 1e12
     stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4) for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -335,9 +353,9 @@ def main():
         "config": config_of(args, wl, g, ps),
         "decrypt_ok": decrypt_ok,
         "roofline": {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "Tmul/s (32-bit integer multiplies)", "frac": achieved / peak,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes x 2.07 GHz",
-                     "launch_ms": br_avg_s * 1e3, "muls_per_launch": muls},
+                     "unit": "T IMAD slots/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
+                     "launch_ms": br_avg_s * 1e3, "slots_per_launch": slots},
         "stage_share": stage_share,
         "gpu_launches": 5 * args.steps,
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
@@ -345,6 +363,9 @@ def main():
                 "d2h_bytes_per_step": int(out.numel() * out.element_size())},
         "clocks": clocks,
     }
+    probe = probe_rates(dev.index)
+    if probe:
+        line["roofline"]["probe"] = probe
     if plain:
         line["plain_path"] = plain
         line["batched_over_plain"] = value / plain["value"]

@@ -411,7 +411,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   if (st->br_smem > (size_t)max_smem) return FDFB_EINVAL;
   FD_CUDA(ops->br_prepare(st->br_smem));
   std::vector<uint2> fwd, inv;
-  host::make_prime_set(ops->P, L, st->S, fwd, inv);
+  host::make_prime_set(ops->P, L, ops->EL, st->S, fwd, inv);
   FD_TRY(st->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
   FD_CUDA(cudaMemcpy(st->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
   FD_CUDA(cudaMemcpy((uint2*)st->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),

@@ -48,6 +48,9 @@ FD_HD uint32_t mul_shoup(uint32_t a, uint32_t w, uint32_t wp, uint32_t p) {
   return a * w - q * p;
 }
 
+// Shoup companion floor(w 2^32 / p) (host side helper).
+inline uint32_t host_shoup(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+
 // Montgomery reduction: x * 2^-32 mod p for x < 2^63, pneg = -p^-1 mod 2^32.
 // Result < x/2^32 + p.
 FD_HD uint32_t redc(uint64_t x, uint32_t p, uint32_t pneg) {
@@ -193,6 +196,23 @@ FD_HD void bfly_inv(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p) {
   Y = mul_shoup(d, w.x, w.y, p);
 }
 
+// Twiddle table position used by butterfly (thread t, register r) of stage s
+// (forward stage s, or the inverse stage on bit L-1-s; both read the block
+// [2^s, 2^(s+1)) at the same offsets).  The natural position is
+// 2^s + (j >> (L - s)).  In the last pass j = t E + r, so thread t needs the
+// C = 2^s / G consecutive entries 2^s + t C + c, c = r >> (L - s); the host
+// stores those blocks transposed, at 2^s + c G + t, so the lanes of a warp
+// read consecutive entries.
+template <int L, int EL, int PASS>
+FD_HD int tw_index(int s, int t, int r) {
+  using Y = Layout<L, EL>;
+  if (PASS == Y::K - 1) {
+    const int c = r >> (L - s);
+    return (1 << s) + c * Y::G + t;
+  }
+  return (1 << s) + (Y::j_of(PASS, t, r) >> (L - s));
+}
+
 #ifdef __CUDA_ARCH__
 #define FD_LDG(ptr) __ldg(ptr)
 #else
@@ -210,8 +230,8 @@ FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) 
 #pragma unroll
     for (int r = 0; r < Y::E; ++r) {
       if (!(r & (1 << rb))) {
-        const int j = Y::j_of(PASS, t, r);
-        const uint2 w = FD_LDG(tw + (1 << s) + (j >> (L - s)));
+        const int ti = tw_index<L, EL, PASS>(s, t, r);
+        const uint2 w = FD_LDG(tw + ti);
         bfly_fwd(v[r], v[r | (1 << rb)], w, p);
       }
     }
@@ -231,8 +251,8 @@ FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) 
 #pragma unroll
     for (int r = 0; r < Y::E; ++r) {
       if (!(r & (1 << rb))) {
-        const int j = Y::j_of(PASS, t, r);
-        const uint2 w = FD_LDG(tw + (Y::N >> (b + 1)) + (j >> (b + 1)));
+        const int ti = tw_index<L, EL, PASS>(L - 1 - b, t, r);
+        const uint2 w = FD_LDG(tw + ti);
         bfly_inv(v[r], v[r | (1 << rb)], w, p);
       }
     }

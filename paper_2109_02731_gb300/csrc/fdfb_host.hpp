@@ -50,8 +50,10 @@ inline uint32_t generator(uint32_t p) {
 }
 
 // Fills S (except the table pointers) and the [P][N] forward/inverse twiddle
-// tables for ring degree N = 2^L with the first P primes.
-inline void make_prime_set(int P, int L, PrimeSet& S, std::vector<uint2>& fwd,
+// tables for ring degree N = 2^L with the first P primes, for transforms that
+// keep 2^EL coefficients per thread: the blocks [2^s, 2^(s+1)) read by the
+// last register pass are stored transposed (see tw_index).
+inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>& fwd,
                            std::vector<uint2>& inv) {
   const uint32_t N = 1u << L;
   S.P = P;
@@ -94,6 +96,17 @@ inline void make_prime_set(int P, int L, PrimeSet& S, std::vector<uint2>& fwd,
       uint32_t wi = (uint32_t)powmod(psi_inv, e, p);
       fwd[(size_t)i * N + k] = uint2{wf, shoup(wf, p)};
       inv[(size_t)i * N + k] = uint2{wi, shoup(wi, p)};
+    }
+    // transpose the last-pass blocks: entry 2^s + t C + c -> 2^s + c G + t
+    const int K = (L + EL - 1) / EL, last = L - (K - 1) * EL;
+    const uint32_t G = 1u << (L - EL);
+    for (int s = L - last; s < L; ++s) {
+      const uint32_t base = 1u << s, C = base / G;
+      for (std::vector<uint2>* tab : {&fwd, &inv}) {
+        std::vector<uint2> blk(tab->begin() + (size_t)i * N + base, tab->begin() + (size_t)i * N + 2 * base);
+        for (uint32_t t = 0; t < G; ++t)
+          for (uint32_t c = 0; c < C; ++c) (*tab)[(size_t)i * N + base + c * G + t] = blk[t * C + c];
+      }
     }
   }
 }

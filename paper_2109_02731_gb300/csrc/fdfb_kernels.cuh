@@ -88,8 +88,9 @@ __device__ __forceinline__ uint32_t modswitch_2n(W x) {
 //   d = acc * X^{-a_i} - acc;  D = Decomp(d) (2 lg digit polynomials);
 //   acc += sum_r D_r * bsk[i][r]    (CMux = extProd(C, g - h) + h)
 // The digits are transformed on the fly; the key rows are pre-transformed
-// (centred, scaled by N^-1 in Montgomery form) and stored in the order the
-// transform emits, so each thread reads its own E consecutive words.
+// (centred, scaled by N^-1 in Montgomery form) and stored so that thread t's
+// E outputs of the transform meet their key words in E/4 128-bit loads that
+// are contiguous across the warp.
 // ---------------------------------------------------------------------------
 struct BRParams {
   PrimeSet S;
@@ -121,8 +122,11 @@ struct BRShape {
   }
 };
 
+// Resident CTAs per SM the register budget is sized for (512 threads per SM).
+constexpr int br_min_blocks(int threads) { return threads >= 512 ? 1 : 512 / threads; }
+
 template <int L, int EL, int P, typename W>
-__global__ void __launch_bounds__(P * (1 << (L - EL)))
+__global__ void __launch_bounds__(P * (1 << (L - EL)), br_min_blocks(P * (1 << (L - EL))))
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -197,7 +201,7 @@ blind_rotate_kernel(const BRParams prm) {
     uint64_t macc[2][E];
 #pragma unroll
     for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
-    const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N + (size_t)t * E;
+    const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N;
     for (int r = 0; r < R; ++r) {
       uint32_t v[E];
 #pragma unroll
@@ -205,10 +209,10 @@ blind_rotate_kernel(const BRParams prm) {
       ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + c) * N);
+        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + c) * N) + t;
 #pragma unroll
         for (int q4 = 0; q4 < E / 4; ++q4) {
-          const uint4 kk = __ldg(kp + q4);
+          const uint4 kk = __ldg(kp + q4 * G);
           const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -398,8 +402,10 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_kernel(const
 }
 
 // Converts canonical GGSW rows [n][2 lg][2][N] into the transform domain:
-// out[i][g][r][c][.] = NTT(centred(bsk[i][r][c]) mod p_g) * N^-1 * 2^32 mod p_g,
-// stored in the transform's output order.
+// out[i][g][r][c][.] = NTT(centred(bsk[i][r][c]) mod p_g) * N^-1 * 2^32 mod p_g.
+// Transform output j = t E + k (thread t of the last pass, register k) is
+// stored at (k / 4) 4G + 4t + k % 4, so that the blind rotation's 128-bit
+// key loads are contiguous across a warp.
 template <int L, int EL, int P, typename W>
 __global__ void __launch_bounds__(P * (1 << (L - EL)))
 bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
@@ -422,7 +428,7 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
 #pragma unroll
     for (int k = 0; k < E; ++k) {
       const uint32_t x = csub(csub(v[k], 2 * p), p);
-      dst[Y::j_of(Y::K - 1, t, k)] = csub(mul_shoup(x, S.ninv_m[grp], S.ninv_ms[grp], p), p);
+      dst[(k >> 2) * 4 * G + t * 4 + (k & 3)] = csub(mul_shoup(x, S.ninv_m[grp], S.ninv_ms[grp], p), p);
     }
   }
 }
