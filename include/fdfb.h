@@ -165,6 +165,32 @@ int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
                          int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg,
                          void* cuda_stream);
 
+/* fdfb_bootstrap for callers that cannot allocate GPU memory -- code that
+ * runs where cudaMalloc is not allowed or not safe (inside a stream capture,
+ * in a real-time or memory-budgeted service loop, in a host callback) -- and
+ * so cannot let fdfb_bootstrap grow its scratch on first use.  The paper has
+ * no counterpart; this is a library convenience.
+ *
+ * Same arguments, results and errors as fdfb_bootstrap, bit for bit.  The
+ * intermediates live in one fixed 32 MiB device array compiled into the
+ * library (every GPU that loads the library holds it until the process
+ * exits); this call performs no cudaMalloc, cudaFree or other allocation.
+ *   - batch may be at most fdfb_noalloc_max_batch(ctx, set_id): 32 MiB /
+ *     ((6N + 2) words), e.g. 1365 ciphertexts at N = 1024, q = 2^32 and 170
+ *     at N = 4096, q = 2^64.  Larger batches return FDFB_EINVAL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls, from any context on the device, share the one array: calls
+ *     that can overlap on the GPU (different streams, no ordering) race and
+ *     corrupt each other's results.  Every intermediate is fully rewritten by
+ *     each call, so nothing left by an earlier call is read.
+ *   - Keys and tables must be installed beforehand (those calls allocate). */
+int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                           int64_t batch, void* ct_out, void* cuda_stream);
+
+/* Largest batch fdfb_bootstrap_noalloc accepts for the parameter set. */
+int fdfb_noalloc_max_batch(fdfb_ctx* ctx, int set_id, int64_t* max_batch);
+
 /* One group of a mixed batch: a parameter set and its ciphertexts. */
 typedef struct {
   int set_id;

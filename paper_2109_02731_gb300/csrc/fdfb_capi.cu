@@ -192,7 +192,7 @@ struct StageTimer {
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   StageTimer(fdfb_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
-    if (ctx->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    if (ctx && ctx->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
   }
   ~StageTimer() {
     if (!a) return;
@@ -209,7 +209,8 @@ struct StageTimer {
 // One bootstrap pipeline on one parameter set (figure "functional-
 // bootstrapping", left), steps 1-14.
 int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
-                 int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s) {
+                 int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
+                 void* fixed_scratch = nullptr) {
   if (batch < 0) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
@@ -218,8 +219,11 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   if (batch > 0x7fffffff) return FDFB_EINVAL;
   const fdfb_params& P = st.prm;
   const size_t N = P.N, wb = st.wbytes();
-  FD_TRY(ensure_scratch(st, batch));
-  unsigned char* base = (unsigned char*)st.scratch.p;
+  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch));
+  unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
+  // The measurement hook creates CUDA events; the fixed-scratch path stays
+  // free of any runtime object creation.
+  fdfb_ctx* tctx = fixed_scratch ? nullptr : ctx;
   void* sgn = base;
   void* cR = base + (size_t)batch * (N + 1) * wb;
   void* accF = (unsigned char*)cR + (size_t)batch * 2 * N * wb;
@@ -250,7 +254,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.smem_r1 = st.br_r1;
   br.smem_exch = st.br_ex;
   {
-    StageTimer tm(ctx, 0, s);
+    StageTimer tm(tctx, 0, s);
     FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
   }
 
@@ -258,7 +262,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   {
     dim3 grid((unsigned)((2 * N + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
     const int rt = trunc_bits(st.w, P.log2Bpk, P.lpk);
-    StageTimer tm(ctx, 1, s);
+    StageTimer tm(tctx, 1, s);
     if (st.w == 32)
       keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
           (const uint32_t*)sgn, batch, (int)N, (const uint32_t*)st.pk.p, P.lpk, P.log2Bpk, rt,
@@ -282,7 +286,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   pm.delta = delta;
   pm.err = ctx->d_err;
   {
-    StageTimer tm(ctx, 2, s);
+    StageTimer tm(tctx, 2, s);
     FD_CUDA(st.ops->pubmux(pm, batch, s));
   }
 
@@ -292,7 +296,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.ctN_out = nullptr;
   br.sign_mode = 0;
   {
-    StageTimer tm(ctx, 3, s);
+    StageTimer tm(tctx, 3, s);
     FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
   }
 
@@ -300,7 +304,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   {
     dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
     const int rt = trunc_bits(st.w, P.log2Bks, P.lks);
-    StageTimer tm(ctx, 4, s);
+    StageTimer tm(tctx, 4, s);
     if (st.w == 32)
       keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
           (const uint32_t*)cQ, batch, (int)N, (const uint32_t*)st.ksk.p, P.lks, P.log2Bks, rt,
@@ -311,6 +315,33 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
           (int)P.n + 1, (uint64_t*)ct_out);
     FD_CUDA(cudaGetLastError());
   }
+  return FDFB_OK;
+}
+
+// Scratch of fdfb_bootstrap_noalloc: a file-scope device array, so that the
+// entry point itself never allocates.  Every GPU that loads the library
+// holds it until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device (the host-side symbol is only
+// a stand-in and must never be handed to a kernel).
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= 64) return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return FDFB_ECUDA;
+    }
+    g_noalloc_addr[device] = ptr;
+  }
+  *out = g_noalloc_addr[device];
   return FDFB_OK;
 }
 
@@ -606,6 +637,29 @@ int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* 
   if (!st) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
   return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, nullptr, as_stream(cuda_stream));
+}
+
+int fdfb_noalloc_max_batch(fdfb_ctx* ctx, int set_id, int64_t* max_batch) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !max_batch) return FDFB_EINVAL;
+  const size_t N = st->prm.N;
+  const size_t per = ((N + 1) + 2 * N + 2 * N + (N + 1)) * st->wbytes();
+  *max_batch = (int64_t)(kNoAllocScratchBytes / per);
+  return FDFB_OK;
+}
+
+int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                           int64_t batch, void* ct_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  int64_t cap = 0;
+  FD_TRY(fdfb_noalloc_max_batch(ctx, set_id, &cap));
+  if (batch > cap) return FDFB_EINVAL;  // beyond the fixed scratch
+  DeviceGuard g(ctx->device);
+  void* scratch = nullptr;
+  FD_TRY(noalloc_scratch(ctx->device, &scratch));
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, nullptr, as_stream(cuda_stream),
+                      scratch);
 }
 
 int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,

@@ -25,6 +25,7 @@ SYMBOLS = [
     "fdfb_create", "fdfb_destroy", "fdfb_params_register", "fdfb_key_words", "fdfb_keys_upload",
     "fdfb_keys_generate", "fdfb_keys_download", "fdfb_lut_setup", "fdfb_lut_polys",
     "fdfb_bootstrap", "fdfb_bootstrap_debug", "fdfb_bootstrap_mixed", "fdfb_keyswitch",
+    "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_profile_enable",
     "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
 ]
@@ -86,6 +87,8 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_bootstrap": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_bootstrap_debug": ([vp, i32, vp, vp, i64, vp, C.POINTER(fdfb_debug_bufs), vp], i32),
                 "fdfb_bootstrap_mixed": ([vp, i32, C.POINTER(fdfb_group), vp], i32),
+                "fdfb_bootstrap_noalloc": ([vp, i32, vp, vp, i64, vp, vp], i32),
+                "fdfb_noalloc_max_batch": ([vp, i32, C.POINTER(i64)], i32),
                 "fdfb_keyswitch": ([vp, i32, vp, i64, vp, vp], i32),
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_decrypt": ([vp, i32, vp, vp, i64, vp, vp], i32),
@@ -246,6 +249,17 @@ class Context:
         b = int(ct_in.shape[0]) if batch is None else batch
         _check(self.L.fdfb_bootstrap(self.h, set_id, _ptr(ct_in), _ptr(lut_ids), b, _ptr(ct_out),
                                      _stream(stream)), "fdfb_bootstrap")
+
+    def bootstrap_noalloc(self, set_id: int, ct_in, lut_ids, ct_out, stream=None):
+        """fdfb_bootstrap on the library's fixed scratch: allocates nothing."""
+        _check(self.L.fdfb_bootstrap_noalloc(self.h, set_id, _ptr(ct_in), _ptr(lut_ids),
+                                             int(ct_in.shape[0]), _ptr(ct_out), _stream(stream)),
+               "fdfb_bootstrap_noalloc")
+
+    def noalloc_max_batch(self, set_id: int) -> int:
+        out = C.c_int64()
+        _check(self.L.fdfb_noalloc_max_batch(self.h, set_id, C.byref(out)), "fdfb_noalloc_max_batch")
+        return int(out.value)
 
     def bootstrap_debug(self, set_id: int, ct_in, lut_ids, ct_out, dbg: dict, stream=None):
         d = fdfb_debug_bufs(*[_ptr(dbg.get(k)) for k in ("ctN", "sgn", "cR", "accF", "cQ")])
