@@ -205,6 +205,141 @@ def cpu_baseline(wl, g, ps, seconds_target=20.0):
                       f"ring products spread over {cores} threads ({dt:.1f} s)"}
 
 
+class Job:
+    """The timed work of one workload on this rank: `step()` queues one step on
+    the current stream; `units` bootstraps per step."""
+
+    def __init__(self, torch, F, ctx, dev, args, rank):
+        self.torch, self.F, self.ctx, self.dev = torch, F, ctx, dev
+        wl = S.WORKLOADS[args.workload]
+        self.wl = wl
+        self.groups = []
+        self.tuned = {}
+        if wl.mlp_layers:
+            self._prepare_mlp(args, rank)
+        else:
+            for gi, g in enumerate(wl.groups):
+                self.groups.append(self._prepare_group(gi, g, args, rank))
+            self.units = sum(x["batch"] for x in self.groups)
+
+    def _prepare_group(self, gi, g, args, rank):
+        torch, F, ctx, dev, wl = self.torch, self.F, self.ctx, self.dev, self.wl
+        ps = S.PARAM_SETS[g.set_name]
+        sid = ctx.register(ps)
+        kr = S.key_randomness(ps, wl.seed)
+        ctx.keys_generate(sid, kr)
+        fs = S.lut_tables(ps, wl.seed, g.n_luts, gi)
+        for f in fs:
+            ctx.lut_setup(sid, f)
+        ids_np = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign, gi)
+        mr = S.message_randomness(ps, wl.seed, g.batch, group=1000 * rank + gi)
+        s_d = torch.tensor(kr.s, device=dev)
+        ct = torch.empty((g.batch, ps.n + 1), dtype=F.word_torch(ps), device=dev)
+        ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a, dev), torch.tensor(mr.e, device=dev),
+                        torch.tensor(mr.m, device=dev), ct)
+        ids = torch.tensor(ids_np, dtype=torch.int32, device=dev)
+        if not args.no_autotune:
+            v, tms = ctx.autotune(sid, g.batch)
+            cur, cnt, cpt = ctx.variant_info(sid)
+            self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
+                                   "trial_blind_rotation_ms": tms}
+        want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
+        return {"sid": sid, "ps": ps, "batch": g.batch, "ct": ct, "ids": ids, "out": torch.empty_like(ct),
+                "s": s_d, "want": want}
+
+    def _prepare_mlp(self, args, rank):
+        from paper_2109_02731_gb300 import mlp
+        torch, F, ctx, dev, wl = self.torch, self.F, self.ctx, self.dev, self.wl
+        ps = S.PARAM_SETS[wl.groups[0].set_name]
+        sid = ctx.register(ps)
+        kr = S.key_randomness(ps, wl.seed)
+        ctx.keys_generate(sid, kr)
+        x, Ws = S.mlp_inputs_and_weights(wl.seed, wl.mlp_layers, wl.mlp_inputs)
+        self.net = mlp.EncryptedMLP(ctx, sid, Ws)
+        mr = S.message_randomness(ps, wl.seed, x.size, group=rank, m=x.reshape(-1))
+        s_d = torch.tensor(kr.s, device=dev)
+        ct = torch.empty((x.size, ps.n + 1), dtype=F.word_torch(ps), device=dev)
+        ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a, dev), torch.tensor(mr.e, device=dev),
+                        torch.tensor(mr.m, device=dev), ct)
+        if not args.no_autotune:
+            v, tms = ctx.autotune(sid, wl.mlp_inputs * wl.mlp_layers[1])
+            cur, cnt, cpt = ctx.variant_info(sid)
+            self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
+                                   "trial_blind_rotation_ms": tms}
+        self.mlp_x = ct.view(x.shape[0], x.shape[1], ps.n + 1)
+        self.mlp_want = mlp.plain_forward(x, Ws, ps.t)
+        self.groups.append({"sid": sid, "ps": ps, "batch": x.size, "ct": ct, "s": s_d})
+        self.units = wl.mlp_inputs * sum(wl.mlp_layers[1:])
+        self.mlp_batches = [wl.mlp_inputs * k for k in wl.mlp_layers[1:]]
+
+    def step(self, groups=None):
+        gs = groups or self.groups
+        if self.wl.mlp_layers:
+            self.mlp_out = self.net.forward(self.mlp_x)
+        elif len(gs) == 1:
+            g = gs[0]
+            self.ctx.bootstrap(g["sid"], g["ct"], g["ids"], g["out"])
+        else:
+            self.ctx.bootstrap_mixed([(g["sid"], g["ct"], g["ids"], g["out"]) for g in gs])
+
+    def decrypt_ok(self):
+        torch, ctx = self.torch, self.ctx
+        if self.wl.mlp_layers:
+            g = self.groups[0]
+            out = self.mlp_out.reshape(-1, g["ps"].n + 1)
+            m = torch.empty(out.shape[0], dtype=torch.int32, device=self.dev)
+            ctx.lwe_decrypt(g["sid"], g["s"], out, m)
+            ctx.sync()
+            return float((m.cpu().numpy().reshape(self.mlp_want.shape) == self.mlp_want).mean())
+        ok = {}
+        for g in self.groups:
+            m = torch.empty(g["batch"], dtype=torch.int32, device=self.dev)
+            ctx.lwe_decrypt(g["sid"], g["s"], g["out"], m)
+            ctx.sync()
+            ok[g["ps"].name] = float((m.cpu().numpy() == g["want"]).mean())
+        return ok if len(ok) > 1 else next(iter(ok.values()))
+
+    def slots_per_step(self):
+        if self.wl.mlp_layers:
+            ps = self.groups[0]["ps"]
+            return 2 * sum(br_algorithmic_slots(ps, b) for b in self.mlp_batches)
+        return 2 * sum(br_algorithmic_slots(g["ps"], g["batch"]) for g in self.groups)
+
+    def io_bytes(self):
+        if self.wl.mlp_layers:
+            g = self.groups[0]
+            return (g["ct"].numel() * g["ct"].element_size(),
+                    self.mlp_want.size * (g["ps"].n + 1) * g["ct"].element_size())
+        h2d = sum(g["ct"].numel() * g["ct"].element_size() + g["ids"].numel() * 4 for g in self.groups)
+        d2h = sum(g["out"].numel() * g["out"].element_size() for g in self.groups)
+        return h2d, d2h
+
+    def launches_per_step(self):
+        if self.wl.mlp_layers:
+            return 6 * (len(self.wl.mlp_layers) - 1)
+        return 5 * len(self.groups)
+
+
+def config_for(job, args):
+    wl = job.wl
+    if wl.mlp_layers:
+        ps = job.groups[0]["ps"]
+        return {"workload": f"{wl.name}: encrypted MLP {'->'.join(map(str, wl.mlp_layers))}, "
+                            f"{wl.mlp_inputs} inputs, FDFB set {ps.name} (n={ps.n} N={ps.N} q=2^{ps.w} "
+                            f"t={ps.t}); unit = bootstraps ({job.units} per step)",
+                "param_set": ps.name, "seed": wl.seed,
+                "l2": "flushed before every timed step (512 MB write, not timed)"}
+    if len(job.groups) == 1:
+        g = wl.groups[0]
+        ps = S.PARAM_SETS[g.set_name]
+        return config_of(args, wl, g, ps)
+    return {"workload": f"{wl.name}: " + ", ".join(
+                f"set {g['ps'].name} (N={g['ps'].N} q=2^{g['ps'].w} t={g['ps'].t}) x {g['batch']}"
+                for g in job.groups) + " in one fdfb_bootstrap_mixed call per step",
+            "batch_per_gpu": job.units, "seed": wl.seed,
+            "l2": "flushed before every timed step (512 MB write, not timed)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +349,7 @@ def main():
     ap.add_argument("--workload", default="tfhe_scale", choices=sorted(S.WORKLOADS))
     ap.add_argument("--ref-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--plain", action="store_true",
                     help="also time the plain path: one ciphertext per bootstrap call")
     args = ap.parse_args()
@@ -230,25 +366,10 @@ def main():
         torch.cuda.set_device(0)
     from paper_2109_02731_gb300 import fdfb as F
 
-    wl, g, ps = workload_desc(args.workload)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     ctx = F.Context(dev.index)
-    sid = ctx.register(ps)
-    kr = S.key_randomness(ps, wl.seed)
-    ctx.keys_generate(sid, kr)
-    fs = S.lut_tables(ps, wl.seed, g.n_luts)
-    for f in fs:
-        ctx.lut_setup(sid, f)
-    batch = g.batch
-    ids_np = S.lut_assignment(wl.seed, batch, g.n_luts, g.lut_assign)
-    mr = S.message_randomness(ps, wl.seed, batch, group=rank)
-    s_d = torch.tensor(kr.s, device=dev)
-    ct = torch.empty((batch, ps.n + 1), dtype=F.word_torch(ps), device=dev)
-    ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a, dev), torch.tensor(mr.e, device=dev),
-                    torch.tensor(mr.m, device=dev), ct)
-    ids = torch.tensor(ids_np, dtype=torch.int32, device=dev)
-    out = torch.empty_like(ct)
+    job = Job(torch, F, ctx, dev, args, rank)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -257,14 +378,9 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        ctx.bootstrap(sid, ct, ids, out)
+        job.step()
     ctx.sync()
-    # correctness of this run: decrypt every output with the secret key
-    m_out = torch.empty(batch, dtype=torch.int32, device=dev)
-    ctx.lwe_decrypt(sid, s_d, out, m_out)
-    ctx.sync()
-    want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
-    decrypt_ok = float((m_out.cpu().numpy() == want).mean())
+    decrypt_ok = job.decrypt_ok()
 
     clk_path = os.path.join(tempfile.gettempdir(), f"fdfb_clocks_{os.getpid()}.csv")
     proc, fh = sample_clocks(clk_path)
@@ -275,31 +391,49 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        ctx.bootstrap(sid, ct, ids, out)
+        job.step()
         ev[k][1].record(stream)
     barrier()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    ms_steps = [a.elapsed_time(b) for a, b in ev]
-    ms_total = float(sum(ms_steps))
+    ms_total = float(sum(a.elapsed_time(b) for a, b in ev))
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # ciphertexts and table ids from pinned memory, bootstrap, D2H of outputs.
-    ct_h = ct.cpu().pin_memory()
-    ids_h = ids.cpu().pin_memory()
-    out_h = torch.empty(out.shape, dtype=out.dtype).pin_memory()
-    ct_e, ids_e, out_e = torch.empty_like(ct), torch.empty_like(ids), torch.empty_like(out)
-    e2e_steps = max(1, args.steps)
+    # End to end through the public API with host buffers: the step's inputs
+    # go host -> device from pinned memory, the outputs come back.
+    host_in = [(g["ct"].cpu().pin_memory(), g["ids"].cpu().pin_memory() if "ids" in g else None)
+               for g in job.groups]
+    dev_in = [(torch.empty_like(g["ct"]), torch.empty_like(g["ids"]) if "ids" in g else None)
+              for g in job.groups]
+    e2e_groups = []
+    for g, (c, i) in zip(job.groups, dev_in):
+        e2 = dict(g)
+        e2["ct"] = c
+        if i is not None:
+            e2["ids"] = i
+        e2["out"] = torch.empty_like(g["ct"]) if "out" in g else None
+        e2e_groups.append(e2)
+    out_host = [torch.empty(g["ct"].shape, dtype=g["ct"].dtype).pin_memory() for g in job.groups]
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
-    for k in range(e2e_steps):
+    for k in range(max(1, args.steps)):
         flush.zero_()
         e0.record(stream)
-        ct_e.copy_(ct_h, non_blocking=True)
-        ids_e.copy_(ids_h, non_blocking=True)
-        ctx.bootstrap(sid, ct_e, ids_e, out_e)
-        out_h.copy_(out_e, non_blocking=True)
+        for (hc, hi), (dc, di) in zip(host_in, dev_in):
+            dc.copy_(hc, non_blocking=True)
+            if hi is not None:
+                di.copy_(hi, non_blocking=True)
+        if job.wl.mlp_layers:
+            saved = job.mlp_x
+            job.mlp_x = dev_in[0][0].view(saved.shape)
+            job.step()
+            job.mlp_x = saved
+            res = job.mlp_out.reshape(-1)
+            out_host[0].view(-1)[: res.numel()].copy_(res, non_blocking=True)
+        else:
+            job.step(e2e_groups)
+            for oh, g in zip(out_host, e2e_groups):
+                oh.copy_(g["out"], non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
@@ -310,57 +444,60 @@ def main():
         fh.close()
     clocks = read_clocks(clk_path, dev.index)
 
-    # slowest rank
     if world > 1:
         t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_total, e2e_ms = float(t[0]), float(t[1])
 
     plain = None
-    if args.plain and rank == 0:
+    if args.plain and rank == 0 and not job.wl.mlp_layers:
         reps = 8
-        one_ct, one_id, one_out = ct[:1].clone(), ids[:1].clone(), out[:1].clone()
-        ctx.bootstrap(sid, one_ct, one_id, one_out)
+        g = job.groups[0]
+        one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()
+        ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
         barrier()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for _ in range(reps):
-            ctx.bootstrap(sid, one_ct, one_id, one_out)
+            ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
         p1.record(stream)
         p1.synchronize()
         plain = {"value": reps / (p0.elapsed_time(p1) / 1e3), "unit": UNIT,
-                 "what": "one ciphertext per bootstrap call, same kernels"}
+                 "what": f"one ciphertext per bootstrap call, set {g['ps'].name}, same kernels"}
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
 
-    units = batch * args.steps * world
+    units = job.units * args.steps * world
     value = units / (ms_total / 1e3)
-    br_ms, br_n = prof["blind_rotate_sign"]
-    br2_ms, br2_n = prof["blind_rotate_func"]
-    br_avg_s = (br_ms + br2_ms) / max(1, br_n + br2_n) / 1e3
-    slots = br_algorithmic_slots(ps, batch)
+    br_ms = prof["blind_rotate_sign"][0] + prof["blind_rotate_func"][0]
+    br_n = prof["blind_rotate_sign"][1] + prof["blind_rotate_func"][1]
+    slots = job.slots_per_step() * args.steps
     peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T slots/s
-    achieved = slots / br_avg_s / 1e12
+    achieved = slots / (br_ms / 1e3) / 1e12
     stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4) for k, v in prof.items()}
+    h2d, d2h = job.io_bytes()
+    ps0 = job.groups[0]["ps"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if ps.w == 32 else "u64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32" if all(g["ps"].w == 32 for g in job.groups) else "u64",
         "data": "synthetic (seeded SplitMix64 keys, messages and tables; keys generated on the GPU)",
-        "config": config_of(args, wl, g, ps),
+        "config": config_for(job, args),
         "decrypt_ok": decrypt_ok,
         "roofline": {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
                      "unit": "T IMAD slots/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
-                     "launch_ms": br_avg_s * 1e3, "slots_per_launch": slots},
+                     "launch_ms": br_ms / max(1, br_n), "launches": br_n,
+                     "slots_per_step": job.slots_per_step()},
         "stage_share": stage_share,
-        "gpu_launches": 5 * args.steps,
-        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": int(ct.numel() * ct.element_size() + ids.numel() * 4),
-                "d2h_bytes_per_step": int(out.numel() * out.element_size())},
+        "autotune": job.tuned,
+        "gpu_launches": job.launches_per_step() * args.steps,
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
     }
     probe = probe_rates(dev.index)
@@ -369,8 +506,9 @@ def main():
     if plain:
         line["plain_path"] = plain
         line["batched_over_plain"] = value / plain["value"]
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, g, ps)
+    if world == 1 and not args.no_cpu_baseline and len(job.groups) == 1 and not job.wl.mlp_layers:
+        g = job.wl.groups[0]
+        line["cpu_baseline"] = cpu_baseline(job.wl, g, S.PARAM_SETS[g.set_name])
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -200,9 +200,12 @@ typedef struct {
   void* ct_out;            /* device [batch][n+1] */
 } fdfb_group;
 
-/* Bootstraps several groups under different parameter sets; each stage is
- * one launch over all groups (the blind rotations of every group share one
- * persistent launch). */
+/* Bootstraps several groups, possibly under different parameter sets, as
+ * fdfb_bootstrap would for each.  Groups of distinct parameter sets run
+ * concurrently on library-owned side streams forked from and joined back to
+ * cuda_stream with events (so the call can be captured into a CUDA graph
+ * once every set's scratch exists); groups of one set run in order.  The
+ * first call may create the side streams and grow scratch. */
 int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, void* cuda_stream);
 
 /* LWE key switching with the installed ksK (figure "Key switching algorithm
@@ -229,6 +232,23 @@ int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct
  *   y device [batch][n_out][len] words; len = n+1 of the set. */
 int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n_out,
                     const void* x, int64_t batch, void* y, void* cuda_stream);
+
+/* Autotuner; the paper has no counterpart.  The blind rotation is compiled
+ * in several register layouts ("variants": coefficients of one transform per
+ * thread, which sets the threads per prime, the shared-memory exchanges per
+ * transform and the resident CTAs per SM).  fdfb_autotune times one blind
+ * rotation of every variant on `batch` trial ciphertexts with the installed
+ * keys and keeps the fastest for the parameter set (*variant_out, its time
+ * in *ms_out; either may be NULL).  Results never depend on the variant:
+ * every variant computes the same exact products.  Needs keys (FDFB_ENOKEYS),
+ * may grow the set's scratch, and synchronises the stream.
+ * fdfb_set_variant selects a variant by index; fdfb_variant_info reports the
+ * current index, the number of variants and the current coefficients per
+ * thread (any output pointer may be NULL). */
+int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
+                  double* ms_out);
+int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant);
+int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* coeffs_per_thread);
 
 /* Measurement hook; the paper has no counterpart.  While enabled, every
  * launch of the bootstrap pipeline is bracketed by a CUDA event pair recorded

@@ -14,19 +14,19 @@
 #include "fdfb_ops.hpp"
 
 namespace fdfb {
-const Ops* ops_n8(int w);
-const Ops* ops_n9(int w);
-const Ops* ops_n10(int w);
-const Ops* ops_n11(int w);
-const Ops* ops_n12(int w);
+const Ops* ops_n8(int w, int variant);
+const Ops* ops_n9(int w, int variant);
+const Ops* ops_n10(int w, int variant);
+const Ops* ops_n11(int w, int variant);
+const Ops* ops_n12(int w, int variant);
 
-const Ops* find_ops(int L, int w) {
+const Ops* find_ops(int L, int w, int variant) {
   switch (L) {
-    case 8: return ops_n8(w);
-    case 9: return ops_n9(w);
-    case 10: return ops_n10(w);
-    case 11: return ops_n11(w);
-    case 12: return ops_n12(w);
+    case 8: return ops_n8(w, variant);
+    case 9: return ops_n9(w, variant);
+    case 10: return ops_n10(w, variant);
+    case 11: return ops_n11(w, variant);
+    case 12: return ops_n12(w, variant);
     default: return nullptr;
   }
 }
@@ -59,13 +59,22 @@ struct DevBuf {
   }
 };
 
-struct SetState {
-  fdfb_params prm{};
-  int w = 0, L = 0, logt = 0;
+// One register-layout variant of the transforms: its twiddle tables and the
+// bootstrapping key transformed for it.
+struct Variant {
   const Ops* ops = nullptr;
   PrimeSet S{};
   DevBuf tw;        // [2][P][N] uint2
   DevBuf bsk_ntt;   // [n][P][2 lg][2][N] uint32
+  size_t br_smem = 0;
+  uint32_t br_r1 = 0, br_ex = 0;
+};
+
+struct SetState {
+  fdfb_params prm{};
+  int w = 0, L = 0, logt = 0;
+  std::vector<std::unique_ptr<Variant>> var;  // var[0] also serves key generation and PubMux
+  int cur = 0;                                // variant used by the blind rotations
   DevBuf bsk;       // canonical [n][2 lg][2][N] words
   DevBuf pk;        // canonical [N][lpk][2][N] words
   DevBuf ksk;       // canonical [N][lks][n+1] words
@@ -75,9 +84,9 @@ struct SetState {
   int n_luts = 0;
   DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
   int64_t scratch_batch = 0;
-  size_t br_smem = 0;
-  uint32_t br_r1 = 0, br_ex = 0;
   size_t wbytes() const { return (size_t)w / 8; }
+  Variant& base() { return *var[0]; }
+  Variant& br() { return *var[cur]; }
 };
 
 }  // namespace
@@ -95,6 +104,9 @@ struct fdfb_ctx {
   std::vector<Mark> marks;
   double prof_ms[kStages] = {0, 0, 0, 0, 0};
   int64_t prof_n[kStages] = {0, 0, 0, 0, 0};
+  // side streams and fork/join events of fdfb_bootstrap_mixed
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> events;
 };
 
 namespace {
@@ -170,9 +182,11 @@ void setup_polynomial(int N, int t, const uint32_t* f, int16_t* p0, int16_t* p1)
 int install_bsk_ntt(SetState& st, cudaStream_t s) {
   const fdfb_params& P = st.prm;
   const size_t N = P.N;
-  FD_TRY(st.bsk_ntt.ensure((size_t)P.n * st.ops->P * 2 * P.lg * 2 * N * 4));
-  FD_CUDA(st.ops->bsk_ntt(st.S, st.bsk.p, (int64_t)P.n * 2 * P.lg, 2 * (int)P.lg,
-                          (uint32_t*)st.bsk_ntt.p, s));
+  for (auto& v : st.var) {
+    FD_TRY(v->bsk_ntt.ensure((size_t)P.n * v->ops->P * 2 * P.lg * 2 * N * 4));
+    FD_CUDA(v->ops->bsk_ntt(v->S, st.bsk.p, (int64_t)P.n * 2 * P.lg, 2 * (int)P.lg,
+                            (uint32_t*)v->bsk_ntt.p, s));
+  }
   return FDFB_OK;
 }
 
@@ -237,9 +251,10 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   const uint64_t delta = (uint64_t)1 << (st.w - st.logt);
 
   // Steps 1-8: ModSwitch, sign accumulator, BlindRotate, SampleExtract + Delta/2.
+  Variant& bv = st.br();
   BRParams br{};
-  br.S = st.S;
-  br.bsk = (const uint32_t*)st.bsk_ntt.p;
+  br.S = bv.S;
+  br.bsk = (const uint32_t*)bv.bsk_ntt.p;
   br.ct = ct_in;
   br.acc0 = nullptr;
   br.lwe_out = sgn;
@@ -251,11 +266,11 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.batch = batch;
   br.delta_half = delta / 2;
   br.sign_mode = 1;
-  br.smem_r1 = st.br_r1;
-  br.smem_exch = st.br_ex;
+  br.smem_r1 = bv.br_r1;
+  br.smem_exch = bv.br_ex;
   {
     StageTimer tm(tctx, 0, s);
-    FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
+    FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
   }
 
   // Steps 9-11, BuildAcc: KeySwitch to RLWE with pK, then PubMux.
@@ -274,7 +289,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
     FD_CUDA(cudaGetLastError());
   }
   PubMuxParams pm{};
-  pm.S = st.S;
+  pm.S = st.base().S;
   pm.cR = cR;
   pm.ct = ct_in;
   pm.lut_ids = lut_ids;
@@ -287,7 +302,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   pm.err = ctx->d_err;
   {
     StageTimer tm(tctx, 2, s);
-    FD_CUDA(st.ops->pubmux(pm, batch, s));
+    FD_CUDA(st.base().ops->pubmux(pm, batch, s));
   }
 
   // Steps 12-13: function BlindRotate, SampleExtract.
@@ -297,7 +312,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.sign_mode = 0;
   {
     StageTimer tm(tctx, 3, s);
-    FD_CUDA(st.ops->br(br, batch, st.br_smem, s));
+    FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
   }
 
   // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q).
@@ -387,6 +402,11 @@ int fdfb_destroy(fdfb_ctx* ctx) {
   if (!ctx) return FDFB_EINVAL;
   {
     DeviceGuard g(ctx->device);
+    for (cudaStream_t st : ctx->side) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     ctx->sets.clear();
     if (ctx->d_err) cudaFree(ctx->d_err);
   }
@@ -417,15 +437,15 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   if (P.lpk < 1 || P.lpk > 64 || P.log2Bpk < 1 || P.log2Bpk > 16) return FDFB_EINVAL;
   if (P.lboot != 1 || P.log2Lboot != (uint32_t)ilog2(P.t)) return FDFB_EINVAL;
   const int w = (int)P.log2q, L = ilog2(P.N);
-  const Ops* ops = find_ops(L, w);
-  if (!ops) return FDFB_EINVAL;
-  // Exactness of the lifted negacyclic products.
+  const Ops* ops0 = find_ops(L, w, 0);
+  if (!ops0) return FDFB_EINVAL;
+  // Exactness of the lifted negacyclic products (every variant has the same primes).
   const long double q = ldexpl(1.0L, w);
   const long double br_max = 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * (q / 2);
   const long double pm_max = (long double)P.N * (P.t - 1) * q;
   const long double enc_max = (long double)P.N * q;
-  if (!host::lift_is_exact(ops->P, br_max) || !host::lift_is_exact(ops->P, pm_max) ||
-      !host::lift_is_exact(ops->P, enc_max))
+  if (!host::lift_is_exact(ops0->P, br_max) || !host::lift_is_exact(ops0->P, pm_max) ||
+      !host::lift_is_exact(ops0->P, enc_max))
     return FDFB_EINVAL;
 
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -435,20 +455,29 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   st->w = w;
   st->L = L;
   st->logt = ilog2(P.t);
-  st->ops = ops;
-  st->br_smem = ops->br_smem((int)P.n, (int)P.lg, &st->br_r1, &st->br_ex);
   int max_smem = 0;
   FD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  if (st->br_smem > (size_t)max_smem) return FDFB_EINVAL;
-  FD_CUDA(ops->br_prepare(st->br_smem));
-  std::vector<uint2> fwd, inv;
-  host::make_prime_set(ops->P, L, ops->EL, st->S, fwd, inv);
-  FD_TRY(st->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
-  FD_CUDA(cudaMemcpy(st->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
-  FD_CUDA(cudaMemcpy((uint2*)st->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),
-                     cudaMemcpyHostToDevice));
-  st->S.tw_fwd = (const uint2*)st->tw.p;
-  st->S.tw_inv = (const uint2*)st->tw.p + fwd.size();
+  for (int vi = 0;; ++vi) {
+    const Ops* ops = find_ops(L, w, vi);
+    if (!ops) break;
+    auto v = std::make_unique<Variant>();
+    v->ops = ops;
+    v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);
+    if (v->br_smem > (size_t)max_smem) {
+      if (vi == 0) return FDFB_EINVAL;
+      continue;
+    }
+    FD_CUDA(ops->br_prepare(v->br_smem));
+    std::vector<uint2> fwd, inv;
+    host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv);
+    FD_TRY(v->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
+    FD_CUDA(cudaMemcpy(v->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+    FD_CUDA(cudaMemcpy((uint2*)v->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),
+                       cudaMemcpyHostToDevice));
+    v->S.tw_fwd = (const uint2*)v->tw.p;
+    v->S.tw_inv = (const uint2*)v->tw.p + fwd.size();
+    st->var.push_back(std::move(v));
+  }
   ctx->sets.push_back(std::move(st));
   *set_id_out = (int)ctx->sets.size() - 1;
   return FDFB_OK;
@@ -522,9 +551,9 @@ int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, 
     FD_CUDA(cudaMemcpyAsync(d_e.p, in->bsk_e, rows * N * 8, cudaMemcpyHostToDevice, s));
     FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
     FD_CUDA(cudaMemcpyAsync(d_comp.p, comp.data(), rows, cudaMemcpyHostToDevice, s));
-    RlweEncParams rp{st->S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
+    RlweEncParams rp{st->base().S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
                      (const uint64_t*)d_mu.p, (const uint8_t*)d_comp.p, st->bsk.p};
-    FD_CUDA(st->ops->rlwe_enc(rp, (int64_t)rows, s));
+    FD_CUDA(st->base().ops->rlwe_enc(rp, (int64_t)rows, s));
     FD_CUDA(cudaStreamSynchronize(s));
   }
   // KeySwitchSetup for pK: RLWE_sk(s_F[i] g_j), constant message polynomial.
@@ -543,9 +572,9 @@ int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, 
     FD_CUDA(cudaMemcpyAsync(d_e.p, in->pk_e, rows * N * 8, cudaMemcpyHostToDevice, s));
     FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
     FD_CUDA(cudaMemcpyAsync(d_comp.p, comp.data(), rows, cudaMemcpyHostToDevice, s));
-    RlweEncParams rp{st->S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
+    RlweEncParams rp{st->base().S, (const uint8_t*)d_sk.p, d_a.p, (const int64_t*)d_e.p,
                      (const uint64_t*)d_mu.p, (const uint8_t*)d_comp.p, st->pk.p};
-    FD_CUDA(st->ops->rlwe_enc(rp, (int64_t)rows, s));
+    FD_CUDA(st->base().ops->rlwe_enc(rp, (int64_t)rows, s));
     FD_CUDA(cudaStreamSynchronize(s));
   }
   // KeySwitchSetup for ksK: LWE_s(s_F[i] g_j).
@@ -672,17 +701,58 @@ int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
 
 int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, void* cuda_stream) {
   if (!ctx || n_groups < 0 || (n_groups > 0 && !groups)) return FDFB_EINVAL;
+  if (n_groups == 0) return FDFB_OK;
   DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  // Groups of the same parameter set share that set's scratch, so they run
+  // one after another on one side stream; distinct sets run concurrently.
+  std::vector<int> sets;
+  std::vector<int> lane(n_groups);
   for (int i = 0; i < n_groups; ++i) {
     SetState* st = get_set(ctx, groups[i].set_id);
-    if (!st) return FDFB_EINVAL;
+    if (!st || groups[i].batch < 0) return FDFB_EINVAL;
+    int k = 0;
+    while (k < (int)sets.size() && sets[k] != groups[i].set_id) ++k;
+    if (k == (int)sets.size()) sets.push_back(groups[i].set_id);
+    lane[i] = k;
   }
-  for (int i = 0; i < n_groups; ++i) {
-    SetState* st = get_set(ctx, groups[i].set_id);
-    FD_TRY(run_pipeline(ctx, *st, groups[i].ct_in, groups[i].lut_ids, groups[i].batch,
-                        groups[i].ct_out, nullptr, as_stream(cuda_stream)));
+  // Grow every set's scratch before forking, so the forked work allocates nothing.
+  for (int k = 0; k < (int)sets.size(); ++k) {
+    int64_t mx = 0;
+    for (int i = 0; i < n_groups; ++i)
+      if (lane[i] == k && groups[i].batch > mx) mx = groups[i].batch;
+    FD_TRY(ensure_scratch(*get_set(ctx, sets[k]), mx));
   }
-  return FDFB_OK;
+  if (sets.size() == 1) {
+    for (int i = 0; i < n_groups; ++i)
+      FD_TRY(run_pipeline(ctx, *get_set(ctx, groups[i].set_id), groups[i].ct_in, groups[i].lut_ids,
+                          groups[i].batch, groups[i].ct_out, nullptr, s));
+    return FDFB_OK;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  while (ctx->side.size() < sets.size()) {
+    cudaStream_t ns;
+    FD_CUDA(cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+    ctx->side.push_back(ns);
+  }
+  while (ctx->events.size() < sets.size() + 1) {
+    cudaEvent_t e;
+    FD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->events.push_back(e);
+  }
+  FD_CUDA(cudaEventRecord(ctx->events[0], s));
+  for (size_t k = 0; k < sets.size(); ++k) FD_CUDA(cudaStreamWaitEvent(ctx->side[k], ctx->events[0], 0));
+  int rc = FDFB_OK;
+  for (int i = 0; i < n_groups && rc == FDFB_OK; ++i)
+    rc = run_pipeline(ctx, *get_set(ctx, groups[i].set_id), groups[i].ct_in, groups[i].lut_ids,
+                      groups[i].batch, groups[i].ct_out, nullptr, ctx->side[lane[i]]);
+  // Join even after an error, so the caller's stream never runs ahead of
+  // work already queued on the side streams.
+  for (size_t k = 0; k < sets.size(); ++k) {
+    FD_CUDA(cudaEventRecord(ctx->events[1 + k], ctx->side[k]));
+    FD_CUDA(cudaStreamWaitEvent(s, ctx->events[1 + k], 0));
+  }
+  return rc;
 }
 
 int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
@@ -763,6 +833,88 @@ int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n
     lwe_affine_kernel<uint64_t><<<grid, AFF_TK, 0, cs>>>(W, n_in, n_out, (const uint64_t*)x, len,
                                                         (uint64_t*)y);
   return cuda_err(cudaGetLastError());
+}
+
+int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* coeffs_per_thread) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  if (current) *current = st->cur;
+  if (count) *count = (int)st->var.size();
+  if (coeffs_per_thread) *coeffs_per_thread = 1 << st->br().ops->EL;
+  return FDFB_OK;
+}
+
+int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || variant < 0 || variant >= (int)st->var.size()) return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  st->cur = variant;
+  return FDFB_OK;
+}
+
+int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
+                  double* ms_out) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || batch < 1 || batch > 0x7fffffff) return FDFB_EINVAL;
+  if (!st->keys) return FDFB_ENOKEYS;
+  if (st->prm.n > st->prm.N) return FDFB_EINVAL;  // the trial ciphertexts live in scratch
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  FD_TRY(ensure_scratch(*st, batch));
+  const size_t N = st->prm.N, wb = st->wbytes();
+  unsigned char* base = (unsigned char*)st->scratch.p;
+  void* trial_ct = base + (size_t)batch * ((N + 1) + 4 * N) * wb;  // the cQ region
+  void* trial_out = base;                                           // the sgn region
+  FD_CUDA(cudaMemsetAsync(trial_ct, 0, (size_t)batch * (st->prm.n + 1) * wb, s));
+  cudaEvent_t a, b;
+  FD_CUDA(cudaEventCreate(&a));
+  FD_CUDA(cudaEventCreate(&b));
+  int best = st->cur;
+  float best_ms = 1e30f;
+  for (int vi = 0; vi < (int)st->var.size(); ++vi) {
+    Variant& v = *st->var[vi];
+    BRParams br{};
+    br.S = v.S;
+    br.bsk = (const uint32_t*)v.bsk_ntt.p;
+    br.ct = trial_ct;
+    br.lwe_out = trial_out;
+    br.n = st->prm.n;
+    br.lg = st->prm.lg;
+    br.log2Bg = st->prm.log2Bg;
+    br.rtrunc = trunc_bits(st->w, st->prm.log2Bg, st->prm.lg);
+    br.batch = batch;
+    br.delta_half = ((uint64_t)1 << (st->w - st->logt)) / 2;
+    br.sign_mode = 1;
+    br.smem_r1 = v.br_r1;
+    br.smem_exch = v.br_ex;
+    float ms_v = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(a, s);
+      cudaError_t e = v.ops->br(br, batch, v.br_smem, s);
+      cudaEventRecord(b, s);
+      if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return cuda_err(e != cudaSuccess ? e : cudaGetLastError());
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms < ms_v) ms_v = ms;  // the first run warms caches
+    }
+    if (ms_v < best_ms) {
+      best_ms = ms_v;
+      best = vi;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    st->cur = best;
+  }
+  if (variant_out) *variant_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return FDFB_OK;
 }
 
 int fdfb_profile_enable(fdfb_ctx* ctx, int enable) {

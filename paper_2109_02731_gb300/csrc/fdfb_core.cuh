@@ -111,6 +111,28 @@ FD_HD uint32_t mod_word<uint32_t>(uint32_t x, const PrimeSet& S, int i) { return
 template <>
 FD_HD uint32_t mod_word<uint64_t>(uint64_t x, const PrimeSet& S, int i) { return mod_u64(x, S, i); }
 
+// Garner reconstruction for a compile-time prime count P.
+template <int P>
+FD_HD uint64_t garner_p(const uint32_t* x, const PrimeSet& S) {
+  uint32_t y[P];
+  y[0] = x[0];
+  uint64_t X = y[0];
+#pragma unroll
+  for (int j = 1; j < P; ++j) {
+    const uint32_t pj = S.p[j];
+    uint32_t v = x[j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      const uint32_t d = v + 2 * pj - y[i];
+      v = csub(mul_shoup(d, S.gc[i][j], S.gcs[i][j], pj), pj);
+    }
+    y[j] = v;
+    X += S.M[j] * (uint64_t)v;
+  }
+  if (y[P - 1] > S.half_top) X -= S.M[P];
+  return X;
+}
+
 // Garner reconstruction of the centred integer with residues x[i] in [0, p_i),
 // reduced mod 2^64 (callers truncate to w bits).
 FD_HD uint64_t garner(const uint32_t* x, const PrimeSet& S) {
@@ -285,5 +307,18 @@ FD_HD uint32_t swz(uint32_t j) {
     if ((j >> b) & 1u) h ^= swz_mask<L, EL>(b);
   return j ^ h;
 }
+
+// Address of element j in a group's exchange buffer.  With 32 coefficients
+// per thread the padded address j + (j >> 5) is bank-conflict free for every
+// pass layout, and since the thread part and the register part of j occupy
+// disjoint bits it splits into base(t) + offset(r), the offset a compile-time
+// constant.  Other shapes use the XOR swizzle above (base(t) ^ offset(r)).
+template <int L, int EL>
+struct Xch {
+  static constexpr bool kAdditive = (EL == 5);
+  static constexpr int kWords = kAdditive ? (1 << L) + ((1 << L) >> 5) : (1 << L);
+  FD_HD static uint32_t addr(uint32_t j) { return kAdditive ? j + (j >> 5) : swz<L, EL>(j); }
+  FD_HD static uint32_t join(uint32_t base, uint32_t off) { return kAdditive ? base + off : base ^ off; }
+};
 
 }  // namespace fdfb

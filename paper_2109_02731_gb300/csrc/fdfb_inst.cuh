@@ -43,7 +43,12 @@ struct Inst {
   static cudaError_t bsk_ntt(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
                              cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
-    constexpr size_t sm = (size_t)P * (1 << L) * 4;
+    constexpr size_t sm = (size_t)P * (((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3) * 4;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(bsk_to_ntt_kernel<L, EL, P, W>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
     bsk_to_ntt_kernel<L, EL, P, W><<<(unsigned)rows, THREADS, sm, st>>>(S, bsk, R, out);
     return cudaGetLastError();
   }

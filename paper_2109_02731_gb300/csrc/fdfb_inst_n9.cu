@@ -1,10 +1,14 @@
-// Kernel instantiations for ring degree N = 2^9.
+// Kernel instantiations for ring degree N = 2^9: one variant per register
+// layout (coefficients per thread 2^EL).
 #include "fdfb_inst.cuh"
 
 namespace fdfb {
-const Ops* ops_n9(int w) {
-  static const Ops o32 = Inst<9, 4, 2, uint32_t>::ops();
-  static const Ops o64 = Inst<9, 4, 3, uint64_t>::ops();
-  return w == 32 ? &o32 : (w == 64 ? &o64 : nullptr);
+const Ops* ops_n9(int w, int variant) {
+  static const Ops a0 = Inst<9, 4, 2, uint32_t>::ops();
+  static const Ops b0 = Inst<9, 4, 3, uint64_t>::ops();
+  switch (variant) {
+    case 0: return w == 32 ? &a0 : (w == 64 ? &b0 : nullptr);
+    default: return nullptr;
+  }
 }
 }  // namespace fdfb

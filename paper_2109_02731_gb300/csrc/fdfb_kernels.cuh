@@ -11,29 +11,57 @@ template <typename W> struct Word;
 template <> struct Word<uint32_t> { static constexpr int bits = 32; };
 template <> struct Word<uint64_t> { static constexpr int bits = 64; };
 
+// 128-bit read-only load that does not allocate in L1: the key rows stream
+// through once per ciphertext and step, and must not evict the twiddles.
+__device__ __forceinline__ uint4 ldg_stream(const uint4* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Synchronises the G threads of one transform: a warp barrier when the group
+// is one warp, else the group's named barrier.
+template <int G>
+__device__ __forceinline__ void group_sync(int bar) {
+  if constexpr (G == 32) {
+    __syncwarp();
+  } else {
+    named_bar(bar, G);
+  }
+}
+
+// Moves the E registers of every thread of a group from the layout of pass
+// FROM to the layout of pass TO through the group's exchange buffer.
+template <int L, int EL, int FROM, int TO>
+__device__ __forceinline__ void exchange(uint32_t (&v)[1 << EL], int t, uint32_t* xb, int bar) {
+  using Y = Layout<L, EL>;
+  using X = Xch<L, EL>;
+  const uint32_t wb = X::addr(Y::j_of(FROM, t, 0));
+#pragma unroll
+  for (int r = 0; r < Y::E; ++r) xb[X::join(wb, X::addr(Y::j_of(FROM, 0, r)))] = v[r];
+  group_sync<Y::G>(bar);
+  const uint32_t rb = X::addr(Y::j_of(TO, t, 0));
+#pragma unroll
+  for (int r = 0; r < Y::E; ++r) v[r] = xb[X::join(rb, X::addr(Y::j_of(TO, 0, r)))];
+  group_sync<Y::G>(bar);
 }
 
 // Forward negacyclic NTT of one polynomial by one thread group: v holds the
 // pass-0 layout (natural order) on entry and the last-pass layout
 // (bit-reversed order, values in [0, 4p)) on exit.  xb is the group's
-// exchange buffer (N words), bar its named barrier.
+// exchange buffer (Xch::kWords words), bar its named barrier.
 template <int L, int EL, int PASS>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
                                         uint32_t* xb, int bar) {
   using Y = Layout<L, EL>;
   if constexpr (PASS < Y::K) {
-    if constexpr (PASS > 0) {
-      const uint32_t wb = swz<L, EL>(Y::j_of(PASS - 1, t, 0));
-#pragma unroll
-      for (int r = 0; r < Y::E; ++r) xb[wb ^ swz<L, EL>(Y::j_of(PASS - 1, 0, r))] = v[r];
-      named_bar(bar, Y::G);
-      const uint32_t rb = swz<L, EL>(Y::j_of(PASS, t, 0));
-#pragma unroll
-      for (int r = 0; r < Y::E; ++r) v[r] = xb[rb ^ swz<L, EL>(Y::j_of(PASS, 0, r))];
-      named_bar(bar, Y::G);
-    }
+    if constexpr (PASS > 0) exchange<L, EL, PASS - 1, PASS>(v, t, xb, bar);
     fwd_pass<L, EL, PASS>(v, t, tw, p);
     ntt_fwd<L, EL, PASS + 1>(v, t, tw, p, xb, bar);
   }
@@ -44,19 +72,9 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&v)[1 << EL], int t, const uin
 template <int L, int EL, int PASS>
 __device__ __forceinline__ void ntt_inv(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
                                         uint32_t* xb, int bar) {
-  using Y = Layout<L, EL>;
   if constexpr (PASS >= 0) {
     inv_pass<L, EL, PASS>(v, t, tw, p);
-    if constexpr (PASS > 0) {
-      const uint32_t wb = swz<L, EL>(Y::j_of(PASS, t, 0));
-#pragma unroll
-      for (int r = 0; r < Y::E; ++r) xb[wb ^ swz<L, EL>(Y::j_of(PASS, 0, r))] = v[r];
-      named_bar(bar, Y::G);
-      const uint32_t rb = swz<L, EL>(Y::j_of(PASS - 1, t, 0));
-#pragma unroll
-      for (int r = 0; r < Y::E; ++r) v[r] = xb[rb ^ swz<L, EL>(Y::j_of(PASS - 1, 0, r))];
-      named_bar(bar, Y::G);
-    }
+    if constexpr (PASS > 0) exchange<L, EL, PASS, PASS - 1>(v, t, xb, bar);
     ntt_inv<L, EL, PASS - 1>(v, t, tw, p, xb, bar);
   }
 }
@@ -118,7 +136,9 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * N * 4;
+    return acc + an + r1 + (size_t)P * xwords() * 4;
+  }
+  static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3;
   }
 };
 
@@ -173,7 +193,7 @@ blind_rotate_kernel(const BRParams prm) {
   const uint32_t pneg = prm.S.pneg[grp];
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
-  uint32_t* xb = exch + grp * N;
+  uint32_t* xb = exch + grp * BRShape<L, EL, P, W>::xwords();
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
@@ -198,7 +218,10 @@ blind_rotate_kernel(const BRParams prm) {
     }
     __syncthreads();
 
-    uint64_t macc[2][E];
+    // Pointwise products summed in the transform domain: each product is
+    // Montgomery-reduced to [0, 2p) as it is formed (the key word carries the
+    // factor 2^32 N^-1), and the running sum is kept in [0, 2p).
+    uint32_t macc[2][E];
 #pragma unroll
     for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
     const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N;
@@ -212,12 +235,12 @@ blind_rotate_kernel(const BRParams prm) {
         const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + c) * N) + t;
 #pragma unroll
         for (int q4 = 0; q4 < E / 4; ++q4) {
-          const uint4 kk = __ldg(kp + q4 * G);
+          const uint4 kk = ldg_stream(kp + q4 * G);
           const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const uint32_t x = csub(csub(v[q4 * 4 + u], 2 * p), p);
-            macc[c][q4 * 4 + u] += (uint64_t)x * kv[u];
+            const uint32_t m = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);  // < 2p
+            macc[c][q4 * 4 + u] = csub(macc[c][q4 * 4 + u] + m, 2 * p);
           }
         }
       }
@@ -227,17 +250,17 @@ blind_rotate_kernel(const BRParams prm) {
     for (int c = 0; c < 2; ++c) {
       uint32_t v[E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) v[k] = csub(redc(macc[c][k], p, pneg), p);
+      for (int k = 0; k < E; ++k) v[k] = macc[c][k];
       ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar);
 #pragma unroll
       for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
     }
     __syncthreads();
     for (int idx = tid; idx < 2 * N; idx += THREADS) {
-      uint32_t x[kMaxPrimes];
+      uint32_t x[P];
 #pragma unroll
-      for (int g = 0; g < kMaxPrimes; ++g) x[g] = g < P ? stage[g * 2 * N + idx] : 0u;
-      acc[idx] = (W)(acc[idx] + (W)garner(x, prm.S));
+      for (int g = 0; g < P; ++g) x[g] = stage[g * 2 * N + idx];
+      acc[idx] = (W)(acc[idx] + (W)garner_p<P>(x, prm.S));
     }
     __syncthreads();
   }
@@ -266,8 +289,9 @@ __device__ __forceinline__ void small_word_product(const PrimeSet& S, int ncols,
                                                    WordF word, OutF out, unsigned char* smem) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  constexpr int XW = (Xch<L, EL>::kWords + 3) & ~3;
   uint32_t* stage = reinterpret_cast<uint32_t*>(smem);          // [P][2][N]
-  uint32_t* exch = stage + P * 2 * N;                           // [P][N]
+  uint32_t* exch = stage + P * 2 * N;                           // [P][XW]
   const int tid = threadIdx.x;
   const int grp = tid / G;
   const int t = tid - grp * G;
@@ -275,7 +299,7 @@ __device__ __forceinline__ void small_word_product(const PrimeSet& S, int ncols,
   const uint32_t pneg = S.pneg[grp];
   const uint2* twf = S.tw_fwd + (size_t)grp * N;
   const uint2* twi = S.tw_inv + (size_t)grp * N;
-  uint32_t* xb = exch + grp * N;
+  uint32_t* xb = exch + grp * XW;
   const int bar = 1 + grp;
 
   uint32_t sv[E];
@@ -301,16 +325,16 @@ __device__ __forceinline__ void small_word_product(const PrimeSet& S, int ncols,
   }
   __syncthreads();
   for (int idx = tid; idx < ncols * N; idx += THREADS) {
-    uint32_t x[kMaxPrimes];
+    uint32_t x[P];
 #pragma unroll
-    for (int g = 0; g < kMaxPrimes; ++g) x[g] = g < P ? stage[g * 2 * N + idx] : 0u;
-    out(idx / N, idx % N, (W)garner(x, S));
+    for (int g = 0; g < P; ++g) x[g] = stage[g * 2 * N + idx];
+    out(idx / N, idx % N, (W)garner_p<P>(x, S));
   }
 }
 
 template <int L, int EL, int P>
 constexpr size_t product_smem_bytes() {
-  return (size_t)P * 3 * (1 << L) * 4;
+  return (size_t)P * 2 * (1 << L) * 4 + (size_t)P * (((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3) * 4;
 }
 
 // PubMux with L_boot = t (one digit): acc_F = [Delta p0, 0] + ((p1 - p0) mod t) * c_R
@@ -412,6 +436,7 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G;
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int XW = (Xch<L, EL>::kWords + 3) & ~3;
   uint32_t* exch = reinterpret_cast<uint32_t*>(smem);
   const int64_t row = blockIdx.x;  // i * R + r
   const int64_t i = row / R;
@@ -423,7 +448,7 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
     uint32_t v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) v[k] = mod_centred<W>(src[c * N + Y::j_of(0, t, k)], S, grp);
-    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * N, 1 + grp);
+    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * XW, 1 + grp);
     uint32_t* dst = out + (((size_t)i * P + grp) * R + r) * 2 * N + (size_t)c * N;
 #pragma unroll
     for (int k = 0; k < E; ++k) {

@@ -19,7 +19,8 @@ struct Ops {
                          cudaStream_t st);
 };
 
-// Returns the launcher table for N = 2^L and word size w, or nullptr.
-const Ops* find_ops(int L, int w);
+// Returns the launcher table of register-layout variant `variant` for
+// N = 2^L and word size w, or nullptr past the last variant.
+const Ops* find_ops(int L, int w, int variant);
 
 }  // namespace fdfb

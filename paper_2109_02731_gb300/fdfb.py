@@ -26,7 +26,8 @@ SYMBOLS = [
     "fdfb_keys_generate", "fdfb_keys_download", "fdfb_lut_setup", "fdfb_lut_polys",
     "fdfb_bootstrap", "fdfb_bootstrap_debug", "fdfb_bootstrap_mixed", "fdfb_keyswitch",
     "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch",
-    "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_profile_enable",
+    "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
+    "fdfb_set_variant", "fdfb_variant_info", "fdfb_profile_enable",
     "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
 ]
 
@@ -93,6 +94,9 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_decrypt": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_affine": ([vp, i32, vp, i32, i32, vp, i64, vp, vp], i32),
+                "fdfb_autotune": ([vp, i32, i64, vp, C.POINTER(i32), C.POINTER(C.c_double)], i32),
+                "fdfb_set_variant": ([vp, i32, i32], i32),
+                "fdfb_variant_info": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
                 "fdfb_profile_enable": ([vp, i32], i32),
                 "fdfb_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], i32),
                 "fdfb_sync": ([vp, vp], i32),
@@ -292,6 +296,23 @@ class Context:
         n_out, n_in = int(W.shape[0]), int(W.shape[1])
         _check(self.L.fdfb_lwe_affine(self.h, set_id, _ptr(W), n_in, n_out, _ptr(x), int(x.shape[0]),
                                       _ptr(y), _stream(stream)), "fdfb_lwe_affine")
+
+    def autotune(self, set_id: int, batch: int, stream=None):
+        """Times every blind-rotation variant; keeps and returns (variant, ms)."""
+        v, ms = C.c_int(), C.c_double()
+        _check(self.L.fdfb_autotune(self.h, set_id, int(batch), _stream(stream), C.byref(v), C.byref(ms)),
+               "fdfb_autotune")
+        return v.value, ms.value
+
+    def set_variant(self, set_id: int, variant: int) -> None:
+        _check(self.L.fdfb_set_variant(self.h, set_id, int(variant)), "fdfb_set_variant")
+
+    def variant_info(self, set_id: int):
+        """(current variant, number of variants, coefficients per thread)."""
+        cur, cnt, cpt = C.c_int(), C.c_int(), C.c_int()
+        _check(self.L.fdfb_variant_info(self.h, set_id, C.byref(cur), C.byref(cnt), C.byref(cpt)),
+               "fdfb_variant_info")
+        return cur.value, cnt.value, cpt.value
 
     STAGES = ("blind_rotate_sign", "keyswitch_pk", "pubmux", "blind_rotate_func", "keyswitch_ksk")
 

@@ -350,3 +350,126 @@ def test_errors_and_edge_cases(F, torch_cuda, ctx, oracle):
         ctx.register(dataclasses.replace(ps, N=128))
     with pytest.raises(F.FDFBError):
         ctx.register(dataclasses.replace(ps, lg=5))
+
+
+# ------------------------------------------------------------ mixed groups --
+
+def test_mixed_groups_match_separate_calls(F, torch_cuda, ctx, oracle):
+    """Three parameter sets (and a repeated set) in one fdfb_bootstrap_mixed
+    call give exactly the outputs of separate fdfb_bootstrap calls; the q = 2^64
+    groups decrypt to f(m)."""
+    spec = [("B", 1, 4, 37), ("D", 3, 4, 64), ("C", 2, 16, 12), ("B", 1, 4, 5)]
+    groups, refs, checks = [], [], []
+    for gi, (name, seed, nl, batch) in enumerate(spec):
+        ps = S.PARAM_SETS[name]
+        K = oracle_keys(name, seed)
+        sid = install(ctx, oracle, name, seed, nl)
+        fs, _ = luts(name, seed, nl)
+        ids = S.lut_assignment(seed, batch, nl, "uniform", group=10 + gi)
+        mr, cts = fresh_cts(name, seed, batch, K, group=10 + gi)
+        ref, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+        ct_d = F.to_device_words(ps, cts)
+        out_d = torch_cuda.empty_like(ct_d)
+        groups.append((sid, ct_d, torch_cuda.tensor(ids, device="cuda"), out_d))
+        refs.append(ref)
+        checks.append((ps, K, fs, ids, mr))
+    ctx.bootstrap_mixed(groups)
+    ctx.sync()
+    for (sid, _, _, out_d), ref, (ps, K, fs, ids, mr) in zip(groups, refs, checks):
+        got = F.to_host_words(ps, out_d).astype(np.uint64)
+        assert np.array_equal(got, ref), ps.name
+        if ps.w == 64:
+            dec = [oracle.lwe_decrypt(ps.w, ps.t, K.s, c) for c in got]
+            assert dec == [int(fs[i][m]) for i, m in zip(ids, mr.m)]
+
+
+# ------------------------------------------------------------- MLP layers --
+
+def test_mlp_small_network_matches_oracle(F, torch_cuda, ctx, oracle):
+    """A small dense network (set A, t = 4) on the GPU -- affine launch, then
+    one batched bootstrap per layer -- against the oracle doing the same
+    affine maps and bootstraps, bit for bit, and against the plaintext
+    network mod t."""
+    from paper_2109_02731_gb300 import mlp
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 7)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    rng = np.random.default_rng(5)
+    layers = [9, 6, 3]
+    Ws = [rng.integers(-1, 2, size=(layers[i + 1], layers[i])) for i in range(len(layers) - 1)]
+    net = mlp.EncryptedMLP(ctx, sid, Ws)
+    n_inputs = 2
+    xs = rng.integers(0, ps.t, size=(n_inputs, layers[0]))
+    mr = S.message_randomness(ps, 7, n_inputs * layers[0], m=xs.reshape(-1))
+    cts = oracle.encrypt_messages(ps, K.s, mr).reshape(n_inputs, layers[0], ps.n + 1)
+    out = F.to_host_words(ps, net.forward(F.to_device_words(ps, cts))).astype(np.uint64)
+    ctx.sync()
+    rot = {lid: np.stack(oracle.setup_polynomial(ps.N, ps.t, f))
+           for lid, f in ((net.relu_id, mlp.relu_table(ps.t)), (net.sign_id, mlp.sign_table(ps.t)))}
+    h = cts
+    for li, W in enumerate(Ws):
+        lid = net.sign_id if li == len(Ws) - 1 else net.relu_id
+        y = np.stack([oracle.lwe_affine(ps.w, W, h[b]) for b in range(n_inputs)])
+        h = np.stack([[oracle.fdfb_bootstrap(ps, K, rot[lid][0], rot[lid][1], y[b, j])
+                       for j in range(W.shape[0])] for b in range(n_inputs)])
+    assert np.array_equal(out, h)
+    dec = np.array([[oracle.lwe_decrypt(ps.w, ps.t, K.s, c) for c in row] for row in out])
+    assert np.array_equal(dec, mlp.plain_forward(xs, Ws, ps.t))
+
+
+@pytest.mark.slow
+def test_mlp_workload_full_size_decrypts(F, torch_cuda, ctx, oracle):
+    """The MLP workload at full size (set D, 784 -> 128 -> 64 -> 10, 64 inputs,
+    weights in [-8, 7], pixels in Z_16): every output decrypts to the
+    plaintext network's value mod t."""
+    from paper_2109_02731_gb300 import mlp
+    wl = S.WORKLOADS["mlp"]
+    ps = S.PARAM_SETS["D"]
+    sid = ctx.register(ps)
+    kr = S.key_randomness(ps, wl.seed)
+    ctx.keys_generate(sid, kr)
+    x, Ws = S.mlp_inputs_and_weights(wl.seed, wl.mlp_layers, wl.mlp_inputs)
+    net = mlp.EncryptedMLP(ctx, sid, Ws)
+    mr = S.message_randomness(ps, wl.seed, x.size, m=x.reshape(-1))
+    d = "cuda"
+    ct = torch_cuda.empty((x.size, ps.n + 1), dtype=torch_cuda.int64, device=d)
+    ctx.lwe_encrypt(sid, torch_cuda.tensor(kr.s, device=d), F.to_device_words(ps, mr.a),
+                    torch_cuda.tensor(mr.e, device=d), torch_cuda.tensor(mr.m, device=d), ct)
+    out = net.forward(ct.view(x.shape[0], x.shape[1], ps.n + 1))
+    m = torch_cuda.empty(out.shape[0] * out.shape[1], dtype=torch_cuda.int32, device=d)
+    ctx.lwe_decrypt(sid, torch_cuda.tensor(kr.s, device=d), out.reshape(-1, ps.n + 1), m)
+    ctx.sync()
+    got = m.cpu().numpy().reshape(out.shape[0], out.shape[1])
+    assert np.array_equal(got, mlp.plain_forward(x, Ws, ps.t))
+
+
+# ---------------------------------------------------- layout variants -----
+
+@pytest.mark.parametrize("name,seed,nl,batch", [("B", 1, 4, 70), ("D", 3, 4, 40), ("C", 2, 16, 9)])
+def test_every_variant_is_bit_exact(F, torch_cuda, ctx, oracle, name, seed, nl, batch):
+    """Every register-layout variant of the blind rotation, and the one the
+    autotuner picks, produce identical ciphertexts (and variant 0 is checked
+    against the oracle on one ciphertext)."""
+    ps = S.PARAM_SETS[name]
+    K = oracle_keys(name, seed)
+    sid = install(ctx, oracle, name, seed, nl)
+    fs, rot = luts(name, seed, nl)
+    ids = S.lut_assignment(seed, batch, nl, "uniform", group=20)
+    mr, cts = fresh_cts(name, seed, batch, K, group=20)
+    cur, count, _ = ctx.variant_info(sid)
+    outs = []
+    for v in range(count):
+        ctx.set_variant(sid, v)
+        out, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+        outs.append(out)
+    for v in range(1, count):
+        assert np.array_equal(outs[v], outs[0]), f"variant {v}"
+    ref = oracle.fdfb_bootstrap(ps, K, rot[ids[0]][0], rot[ids[0]][1], cts[0])
+    assert np.array_equal(outs[0][0], ref)
+    best, ms = ctx.autotune(sid, 64)
+    assert 0 <= best < count and ms > 0
+    assert ctx.variant_info(sid)[0] == best
+    out, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+    assert np.array_equal(out, outs[0])
+    ctx.set_variant(sid, cur)
