@@ -119,6 +119,22 @@ def probe_rates(dev_index: int):
         return {"error": str(e)[:200]}
 
 
+def slowest_rank(values, device):
+    """Element-wise maximum over all ranks of per-rank timings (the job is as
+    fast as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def rank_messages(ps, seed: int, batch: int, rank: int, group: int = 0):
+    """The message randomness of one rank's shard: every rank bootstraps its
+    own batch (weak scaling), drawn from its own sub-stream."""
+    return S.message_randomness(ps, seed, batch, group=1000 * rank + group)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -232,17 +248,21 @@ class Job:
         for f in fs:
             ctx.lut_setup(sid, f)
         ids_np = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign, gi)
-        mr = S.message_randomness(ps, wl.seed, g.batch, group=1000 * rank + gi)
+        mr = rank_messages(ps, wl.seed, g.batch, rank, gi)
         s_d = torch.tensor(kr.s, device=dev)
         ct = torch.empty((g.batch, ps.n + 1), dtype=F.word_torch(ps), device=dev)
         ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a, dev), torch.tensor(mr.e, device=dev),
                         torch.tensor(mr.m, device=dev), ct)
         ids = torch.tensor(ids_np, dtype=torch.int32, device=dev)
-        if not args.no_autotune:
-            v, tms = ctx.autotune(sid, g.batch)
+        if args.variant is not None:
+            ctx.set_variant(sid, args.variant)
+            cur, cnt, cpt = ctx.variant_info(sid)
+            self.tuned[ps.name] = {"variant": cur, "of": cnt, "coeffs_per_thread": cpt, "fixed": True}
+        elif not args.no_autotune:
+            v, tms, each = ctx.autotune(sid, g.batch, each=True)
             cur, cnt, cpt = ctx.variant_info(sid)
             self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
-                                   "trial_blind_rotation_ms": tms}
+                                   "trial_blind_rotation_ms": [round(x, 3) for x in each]}
         want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
         return {"sid": sid, "ps": ps, "batch": g.batch, "ct": ct, "ids": ids, "out": torch.empty_like(ct),
                 "s": s_d, "want": want}
@@ -350,6 +370,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="use this blind-rotation layout variant instead of autotuning")
     ap.add_argument("--plain", action="store_true",
                     help="also time the plain path: one ciphertext per bootstrap call")
     args = ap.parse_args()
@@ -445,9 +467,7 @@ def main():
     clocks = read_clocks(clk_path, dev.index)
 
     if world > 1:
-        t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total, e2e_ms = float(t[0]), float(t[1])
+        ms_total, e2e_ms = slowest_rank([ms_total, e2e_ms], dev)
 
     plain = None
     if args.plain and rank == 0 and not job.wl.mlp_layers:

@@ -239,14 +239,15 @@ int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n
  * transform and the resident CTAs per SM).  fdfb_autotune times one blind
  * rotation of every variant on `batch` trial ciphertexts with the installed
  * keys and keeps the fastest for the parameter set (*variant_out, its time
- * in *ms_out; either may be NULL).  Results never depend on the variant:
+ * in *ms_out, and the time of variant i in ms_each[i] for i < ms_each_len;
+ * any of them may be NULL).  Results never depend on the variant:
  * every variant computes the same exact products.  Needs keys (FDFB_ENOKEYS),
  * may grow the set's scratch, and synchronises the stream.
  * fdfb_set_variant selects a variant by index; fdfb_variant_info reports the
  * current index, the number of variants and the current coefficients per
  * thread (any output pointer may be NULL). */
 int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
-                  double* ms_out);
+                  double* ms_out, double* ms_each, int ms_each_len);
 int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant);
 int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* coeffs_per_thread);
 

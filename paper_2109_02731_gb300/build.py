@@ -81,7 +81,8 @@ PROBE_LIB = os.path.join(BUILD, "libintprobe.so")
 
 def build_probe() -> str:
     """Builds the integer-pipe throughput probe used by bench.py."""
-    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+    deps = [PROBE_SRC] + glob.glob(os.path.join(CSRC, "*.cuh"))
+    if os.path.exists(PROBE_LIB) and all(os.path.getmtime(PROBE_LIB) >= os.path.getmtime(d) for d in deps):
         return PROBE_LIB
     os.makedirs(BUILD, exist_ok=True)
     tmp = PROBE_LIB + f".tmp{os.getpid()}"

@@ -462,9 +462,9 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
     if (!ops) break;
     auto v = std::make_unique<Variant>();
     v->ops = ops;
+    if ((int)P.log2Bg > ops->max_log2B) continue;  // digits too wide for this variant
     v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);
     if (v->br_smem > (size_t)max_smem) {
-      if (vi == 0) return FDFB_EINVAL;
       continue;
     }
     FD_CUDA(ops->br_prepare(v->br_smem));
@@ -478,6 +478,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
     v->S.tw_inv = (const uint2*)v->tw.p + fwd.size();
     st->var.push_back(std::move(v));
   }
+  if (st->var.empty() || st->var[0]->ops != ops0) return FDFB_EINVAL;
   ctx->sets.push_back(std::move(st));
   *set_id_out = (int)ctx->sets.size() - 1;
   return FDFB_OK;
@@ -853,7 +854,7 @@ int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant) {
 }
 
 int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
-                  double* ms_out) {
+                  double* ms_out, double* ms_each, int ms_each_len) {
   SetState* st = get_set(ctx, set_id);
   if (!st || batch < 1 || batch > 0x7fffffff) return FDFB_EINVAL;
   if (!st->keys) return FDFB_ENOKEYS;
@@ -901,6 +902,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
       cudaEventElapsedTime(&ms, a, b);
       if (rep > 0 && ms < ms_v) ms_v = ms;  // the first run warms caches
     }
+    if (ms_each && vi < ms_each_len) ms_each[vi] = ms_v;
     if (ms_v < best_ms) {
       best_ms = ms_v;
       best = vi;

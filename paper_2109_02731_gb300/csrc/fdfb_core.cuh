@@ -73,6 +73,7 @@ struct PrimeSet {
   uint32_t gcs[kMaxPrimes][kMaxPrimes];  // Shoup companions
   uint64_t M[kMaxPrimes + 1];        // prefix products of the primes, mod 2^64
   uint32_t half_top;                 // p_{P-1} / 2: sign threshold of the top digit
+  uint32_t zero;                     // always 0 (see bfly_fwd)
   const uint2* tw_fwd;               // [P][N] (psi^brv(k), Shoup) forward twiddles
   const uint2* tw_inv;               // [P][N] (psi^-brv(k), Shoup) inverse twiddles
 };
@@ -202,17 +203,23 @@ struct Layout {
   }
 };
 
+// The butterflies' additions take a third operand z that is always zero but
+// unknown to the compiler (a kernel argument): as three-input additions they
+// issue on the ALU pipe instead of being turned into multiply-adds, which
+// leaves the multiplier pipe to the Shoup products.
+//
 // Forward Cooley-Tukey butterfly (Harvey's lazy form): X, Y in [0, 4p) ->
 // X + WY, X - WY + 2p, both in [0, 4p).
-FD_HD void bfly_fwd(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p) {
-  uint32_t x = csub(X, 2 * p);
+FD_HD void bfly_fwd(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p, uint32_t z) {
+  uint32_t x = umin32(X, X - 2 * p + z);
   uint32_t t = mul_shoup(Y, w.x, w.y, p);
-  X = x + t;
+  X = x + t + z;
   Y = x - t + 2 * p;
 }
 // Inverse Gentleman-Sande butterfly: X, Y in [0, 2p) -> X + Y, (X - Y) W.
-FD_HD void bfly_inv(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p) {
-  uint32_t s = csub(X + Y, 2 * p);
+FD_HD void bfly_inv(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p, uint32_t z) {
+  uint32_t s = X + Y + z;
+  s = umin32(s, s - 2 * p + z);
   uint32_t d = X - Y + 2 * p;
   X = s;
   Y = mul_shoup(d, w.x, w.y, p);
@@ -243,7 +250,7 @@ FD_HD int tw_index(int s, int t, int r) {
 
 // All stages of forward pass `pass` on the E registers of thread t.
 template <int L, int EL, int PASS>
-FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) {
+FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
   using Y = Layout<L, EL>;
   constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
 #pragma unroll
@@ -254,7 +261,7 @@ FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) 
       if (!(r & (1 << rb))) {
         const int ti = tw_index<L, EL, PASS>(s, t, r);
         const uint2 w = FD_LDG(tw + ti);
-        bfly_fwd(v[r], v[r | (1 << rb)], w, p);
+        bfly_fwd(v[r], v[r | (1 << rb)], w, p, z);
       }
     }
   }
@@ -262,7 +269,7 @@ FD_HD void fwd_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) 
 
 // All stages of inverse pass `pass` (bits ascending) on thread t.
 template <int L, int EL, int PASS>
-FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) {
+FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
   using Y = Layout<L, EL>;
   constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
   // stage s of the forward order touches j-bit L-1-s; run them in reverse
@@ -275,7 +282,7 @@ FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p) 
       if (!(r & (1 << rb))) {
         const int ti = tw_index<L, EL, PASS>(L - 1 - b, t, r);
         const uint2 w = FD_LDG(tw + ti);
-        bfly_inv(v[r], v[r | (1 << rb)], w, p);
+        bfly_inv(v[r], v[r | (1 << rb)], w, p, z);
       }
     }
   }

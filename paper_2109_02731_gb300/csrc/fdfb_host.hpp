@@ -85,6 +85,7 @@ inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>
   S.M[0] = 1;
   for (int i = 0; i < kMaxPrimes; ++i) S.M[i + 1] = S.M[i] * (uint64_t)kPrimes[i];
   S.half_top = kPrimes[P - 1] / 2;
+  S.zero = 0;
   for (int i = 0; i < P; ++i) {
     const uint32_t p = kPrimes[i];
     const uint32_t g = generator(p);

@@ -4,18 +4,19 @@
 
 namespace fdfb {
 
-template <int L, int EL, int P, typename W>
+template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
+          int MINB = br_min_blocks(P * (1 << (L - EL)))>
 struct Inst {
-  using Sh = BRShape<L, EL, P, W>;
+  using Sh = BRShape<L, EL, P, W, DT>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
-    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W>,
+    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    blind_rotate_kernel<L, EL, P, W><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB><<<(unsigned)batch, THREADS, smem, st>>>(prm);
     return cudaGetLastError();
   }
   static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {
@@ -53,7 +54,8 @@ struct Inst {
     return cudaGetLastError();
   }
   static Ops ops() {
-    return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, &br_smem, &br_prepare, &br, &pubmux, &rlwe_enc, &bsk_ntt};
+    return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
+               &pubmux, &rlwe_enc, &bsk_ntt};
   }
 };
 

@@ -1,14 +1,23 @@
 // Kernel instantiations for ring degree N = 2^8: one variant per register
-// layout (coefficients per thread 2^EL).
+// layout (coefficients per thread 2^EL) and digit width.
 #include "fdfb_inst.cuh"
 
 namespace fdfb {
 const Ops* ops_n8(int w, int variant) {
-  static const Ops a0 = Inst<8, 3, 2, uint32_t>::ops();
-  static const Ops b0 = Inst<8, 3, 3, uint64_t>::ops();
-  switch (variant) {
-    case 0: return w == 32 ? &a0 : (w == 64 ? &b0 : nullptr);
-    default: return nullptr;
+  static const Ops a0 = Inst<8, 3, 2, uint32_t, uint16_t>::ops();
+  static const Ops b0 = Inst<8, 3, 3, uint64_t, uint16_t>::ops();
+  if (w == 32) {
+    switch (variant) {
+      case 0: return &a0;
+      default: return nullptr;
+    }
   }
+  if (w == 64) {
+    switch (variant) {
+      case 0: return &b0;
+      default: return nullptr;
+    }
+  }
+  return nullptr;
 }
 }  // namespace fdfb

@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fdfb_core.cuh"
 
 namespace fdfb {
@@ -58,12 +60,12 @@ __device__ __forceinline__ void exchange(uint32_t (&v)[1 << EL], int t, uint32_t
 // exchange buffer (Xch::kWords words), bar its named barrier.
 template <int L, int EL, int PASS>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
-                                        uint32_t* xb, int bar) {
+                                        uint32_t* xb, int bar, uint32_t z) {
   using Y = Layout<L, EL>;
   if constexpr (PASS < Y::K) {
     if constexpr (PASS > 0) exchange<L, EL, PASS - 1, PASS>(v, t, xb, bar);
-    fwd_pass<L, EL, PASS>(v, t, tw, p);
-    ntt_fwd<L, EL, PASS + 1>(v, t, tw, p, xb, bar);
+    fwd_pass<L, EL, PASS>(v, t, tw, p, z);
+    ntt_fwd<L, EL, PASS + 1>(v, t, tw, p, xb, bar, z);
   }
 }
 
@@ -71,11 +73,11 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&v)[1 << EL], int t, const uin
 // (natural order), values in [0, 2p).  The 1/N factor is not applied.
 template <int L, int EL, int PASS>
 __device__ __forceinline__ void ntt_inv(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p,
-                                        uint32_t* xb, int bar) {
+                                        uint32_t* xb, int bar, uint32_t z) {
   if constexpr (PASS >= 0) {
-    inv_pass<L, EL, PASS>(v, t, tw, p);
+    inv_pass<L, EL, PASS>(v, t, tw, p, z);
     if constexpr (PASS > 0) exchange<L, EL, PASS, PASS - 1>(v, t, xb, bar);
-    ntt_inv<L, EL, PASS - 1>(v, t, tw, p, xb, bar);
+    ntt_inv<L, EL, PASS - 1>(v, t, tw, p, xb, bar, z);
   }
 }
 
@@ -124,39 +126,63 @@ struct BRParams {
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
 };
 
-template <int L, int EL, int P, typename W>
+template <int L, int EL, int P, typename W, typename DT>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  // acc | a_N | (digits, or the staged residues) | exchange buffers
   static size_t smem_bytes(int n, int lg, uint32_t* r1_off, uint32_t* exch_off) {
     size_t acc = 2 * (size_t)N * sizeof(W);
     size_t an = ((size_t)n * 2 + 15) & ~(size_t)15;
-    size_t dig = 2 * (size_t)lg * N * 2;
-    size_t stage = (size_t)P * 2 * N * 4;
+    size_t dig = (2 * (size_t)lg * N * sizeof(DT) + 15) & ~(size_t)15;
+    size_t stage = (size_t)2 * (P - 1) * N * 4;
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
     return acc + an + r1 + (size_t)P * xwords() * 4;
   }
-  static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3;
-  }
+  static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3; }
 };
 
 // Resident CTAs per SM the register budget is sized for (512 threads per SM).
 constexpr int br_min_blocks(int threads) { return threads >= 512 ? 1 : 512 / threads; }
 
-template <int L, int EL, int P, typename W>
-__global__ void __launch_bounds__(P * (1 << (L - EL)), br_min_blocks(P * (1 << (L - EL))))
+// Transform-domain sum -> inverse-transform input in [0, 2p): a 64-bit sum
+// (< 8 p^2) is Montgomery-reduced (< 3p) and corrected once.
+template <bool WIDE, typename Acc>
+__device__ __forceinline__ uint32_t acc_to_inv(Acc a, uint32_t p, uint32_t pneg) {
+  if constexpr (WIDE) {
+    const uint32_t r = redc((uint64_t)a, p, pneg);
+    return umin32(r, r - 2 * p);
+  } else {
+    return (uint32_t)a;
+  }
+}
+
+// Staging slot of group g's residues of output column c (g != c): the owner
+// of column c (group c) reads the other P-1 groups' residues there.
+template <int P>
+__device__ __forceinline__ int stage_slot(int g, int c) {
+  return c * (P - 1) + (g < c ? g : g - 1);
+}
+
+// WIDE: sum the pointwise products of all 2l digits in 64 bits and reduce
+// once (fewer instructions, twice the accumulator registers); otherwise each
+// product is Montgomery-reduced as it is formed.  MINB: resident CTAs per SM
+// the register budget is sized for.
+template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
+          int MINB = br_min_blocks(P * (1 << (L - EL)))>
+__global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
-  constexpr int WB = Word<W>::bits;
+  static_assert(P >= 2, "the column owners are groups 0 and 1");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
-  uint16_t* dig = reinterpret_cast<uint16_t*>(smem + prm.smem_r1);          // [2 lg][N]
-  uint32_t* stage = reinterpret_cast<uint32_t*>(smem + prm.smem_r1);        // [P][2][N]
-  uint32_t* exch = reinterpret_cast<uint32_t*>(smem + prm.smem_exch);       // [P][N]
+  DT* dig = reinterpret_cast<DT*>(smem + prm.smem_r1);                      // [2 lg][N]
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem + prm.smem_r1);        // [2 (P-1)][N]
+  uint32_t* exch = reinterpret_cast<uint32_t*>(smem + prm.smem_exch);       // [P][xwords]
 
   const int tid = threadIdx.x;
   const int grp = tid / G;
@@ -191,9 +217,10 @@ blind_rotate_kernel(const BRParams prm) {
 
   const uint32_t p = prm.S.p[grp];
   const uint32_t pneg = prm.S.pneg[grp];
+  const uint32_t z = prm.S.zero;
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
-  uint32_t* xb = exch + grp * BRShape<L, EL, P, W>::xwords();
+  uint32_t* xb = exch + grp * BRShape<L, EL, P, W, DT>::xwords();
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
@@ -214,53 +241,92 @@ blind_rotate_kernel(const BRParams prm) {
       const W d = (W)(rv - acc[c * N + j]);
       const W xt = rt ? (W)((W)(d + half_rt) >> rt) : d;
       for (int l = 0; l < lg; ++l)
-        dig[(c * lg + l) * N + j] = (uint16_t)((uint32_t)(xt >> (l * log2Bg)) & dmask);
+        dig[(c * lg + l) * N + j] = (DT)((uint32_t)(xt >> (l * log2Bg)) & dmask);
     }
     __syncthreads();
 
     // Pointwise products summed in the transform domain: each product is
     // Montgomery-reduced to [0, 2p) as it is formed (the key word carries the
     // factor 2^32 N^-1), and the running sum is kept in [0, 2p).
-    uint32_t macc[2][E];
+    // Group 0 accumulates column 1 in macc[0] and column 0 in macc[1], the
+    // other groups column c in macc[c]: the column a group lifts (its own
+    // index, for groups 0 and 1) always ends up in macc[1].
+    using Acc = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    Acc macc[2][E];
 #pragma unroll
     for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
+    const int swap = (grp == 0) ? 1 : 0;
     const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N;
     for (int r = 0; r < R; ++r) {
       uint32_t v[E];
 #pragma unroll
       for (int k = 0; k < E; ++k) v[k] = dig[r * N + Y::j_of(0, t, k)];
-      ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar);
+      ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar, z);
+      if constexpr (WIDE) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[k] = csub(csub(v[k], 2 * p), p);
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + c) * N) + t;
+        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + (c ^ swap)) * N) + t;
 #pragma unroll
         for (int q4 = 0; q4 < E / 4; ++q4) {
           const uint4 kk = ldg_stream(kp + q4 * G);
           const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const uint32_t m = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);  // < 2p
-            macc[c][q4 * 4 + u] = csub(macc[c][q4 * 4 + u] + m, 2 * p);
+            if constexpr (WIDE) {
+              // v < p and K < p: 2l <= 8 products stay below 2^63
+              macc[c][q4 * 4 + u] += (uint64_t)v[q4 * 4 + u] * kv[u];
+            } else {
+              const uint32_t m = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);  // < 2p
+              uint32_t s2 = (uint32_t)macc[c][q4 * 4 + u] + m + z;
+              macc[c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+            }
           }
         }
       }
     }
     __syncthreads();  // every group is done with the digits: the region becomes `stage`
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
+
+    // Inverse transforms.  Column c is lifted by group c, which keeps its own
+    // residues in registers; every other group stages its residues for it.
+    uint32_t own[E];
+    {
       uint32_t v[E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) v[k] = macc[c][k];
-      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar);
+      for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
+      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+      uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
-      for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
+      for (int k = 0; k < E; ++k) dst[Y::j_of(0, t, k)] = csub(v[k], p);
+    }
+    {
+      uint32_t v[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
+      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+      if (grp < 2) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) own[k] = csub(v[k], p);
+      } else {
+        uint32_t* dst = stage + stage_slot<P>(grp, 1) * N;
+#pragma unroll
+        for (int k = 0; k < E; ++k) dst[Y::j_of(0, t, k)] = csub(v[k], p);
+      }
     }
     __syncthreads();
-    for (int idx = tid; idx < 2 * N; idx += THREADS) {
-      uint32_t x[P];
+    if (grp < 2) {
+      const int c = grp;
 #pragma unroll
-      for (int g = 0; g < P; ++g) x[g] = stage[g * 2 * N + idx];
-      acc[idx] = (W)(acc[idx] + (W)garner_p<P>(x, prm.S));
+      for (int k = 0; k < E; ++k) {
+        const int j = Y::j_of(0, t, k);
+        uint32_t x[P];
+#pragma unroll
+        for (int g = 0; g < P; ++g)
+          x[g] = (g == c) ? own[k] : stage[stage_slot<P>(g, c) * N + j];
+        acc[c * N + j] = (W)(acc[c * N + j] + (W)garner_p<P>(x, prm.S));
+      }
     }
     __syncthreads();
   }
@@ -275,7 +341,6 @@ blind_rotate_kernel(const BRParams prm) {
     else v = (W)(0 - acc[N + (N - (k - 1))]);
     out[k] = v;
   }
-  (void)WB;
 }
 
 // ---------------------------------------------------------------------------
@@ -305,21 +370,21 @@ __device__ __forceinline__ void small_word_product(const PrimeSet& S, int ncols,
   uint32_t sv[E];
 #pragma unroll
   for (int k = 0; k < E; ++k) sv[k] = small(Y::j_of(0, t, k));
-  ntt_fwd<L, EL, 0>(sv, t, twf, p, xb, bar);
+  ntt_fwd<L, EL, 0>(sv, t, twf, p, xb, bar, S.zero);
 #pragma unroll
   for (int k = 0; k < E; ++k) sv[k] = csub(csub(sv[k], 2 * p), p);
   for (int c = 0; c < ncols; ++c) {
     uint32_t v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) v[k] = mod_word<W>(word(c, Y::j_of(0, t, k)), S, grp);
-    ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar);
+    ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar, S.zero);
 #pragma unroll
     for (int k = 0; k < E; ++k) {
       const uint32_t x = csub(csub(v[k], 2 * p), p);
       const uint32_t m = csub(redc((uint64_t)x * sv[k], p, pneg), p);          // x s 2^-32
       v[k] = csub(mul_shoup(m, S.ninv_m[grp], S.ninv_ms[grp], p), p);         // * N^-1 2^32
     }
-    ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar);
+    ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, S.zero);
 #pragma unroll
     for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
   }
@@ -448,7 +513,7 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
     uint32_t v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) v[k] = mod_centred<W>(src[c * N + Y::j_of(0, t, k)], S, grp);
-    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * XW, 1 + grp);
+    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * XW, 1 + grp, S.zero);
     uint32_t* dst = out + (((size_t)i * P + grp) * R + r) * 2 * N + (size_t)c * N;
 #pragma unroll
     for (int k = 0; k < E; ++k) {

@@ -10,6 +10,7 @@ namespace fdfb {
 
 struct Ops {
   int L, EL, P, w, threads;
+  int max_log2B;  // widest digit the blind rotation's digit buffer holds
   size_t (*br_smem)(int n, int lg, uint32_t* r1_off, uint32_t* exch_off);
   cudaError_t (*br_prepare)(size_t smem);
   cudaError_t (*br)(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st);

@@ -94,7 +94,8 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_decrypt": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_affine": ([vp, i32, vp, i32, i32, vp, i64, vp, vp], i32),
-                "fdfb_autotune": ([vp, i32, i64, vp, C.POINTER(i32), C.POINTER(C.c_double)], i32),
+                "fdfb_autotune": ([vp, i32, i64, vp, C.POINTER(i32), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), i32], i32),
                 "fdfb_set_variant": ([vp, i32, i32], i32),
                 "fdfb_variant_info": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
                 "fdfb_profile_enable": ([vp, i32], i32),
@@ -297,11 +298,16 @@ class Context:
         _check(self.L.fdfb_lwe_affine(self.h, set_id, _ptr(W), n_in, n_out, _ptr(x), int(x.shape[0]),
                                       _ptr(y), _stream(stream)), "fdfb_lwe_affine")
 
-    def autotune(self, set_id: int, batch: int, stream=None):
-        """Times every blind-rotation variant; keeps and returns (variant, ms)."""
+    def autotune(self, set_id: int, batch: int, stream=None, each: bool = False):
+        """Times every blind-rotation variant; keeps and returns (variant, ms)
+        (and the list of every variant's ms when `each`)."""
         v, ms = C.c_int(), C.c_double()
-        _check(self.L.fdfb_autotune(self.h, set_id, int(batch), _stream(stream), C.byref(v), C.byref(ms)),
-               "fdfb_autotune")
+        arr = (C.c_double * 16)()
+        _check(self.L.fdfb_autotune(self.h, set_id, int(batch), _stream(stream), C.byref(v), C.byref(ms),
+                                    arr, 16), "fdfb_autotune")
+        if each:
+            n = self.variant_info(set_id)[1]
+            return v.value, ms.value, [arr[i] for i in range(n)]
         return v.value, ms.value
 
     def set_variant(self, set_id: int, variant: int) -> None:

@@ -57,14 +57,14 @@ __global__ void lop_kernel(uint32_t* out, uint32_t x, uint32_t y) {
 }
 
 // Harvey forward butterflies on registers with a fixed twiddle.
-__global__ void bfly_kernel(uint32_t* out, uint32_t w, uint32_t wp, uint32_t p) {
+__global__ void bfly_kernel(uint32_t* out, uint32_t w, uint32_t wp, uint32_t p, uint32_t z) {
   uint32_t v[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = (threadIdx.x * 16 + k) % p;
   const uint2 tw{w, wp};
   for (int i = 0; i < kIter / 8; ++i) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) fdfb::bfly_fwd(v[k], v[k + 8], tw, p);
+    for (int k = 0; k < 8; ++k) fdfb::bfly_fwd(v[k], v[k + 8], tw, p, z);
   }
   uint32_t s = 0;
 #pragma unroll
@@ -93,7 +93,7 @@ extern "C" int probe_int_rates(int device, double* rates) {
       if (kind == 0) imad_kernel<<<blocks, threads>>>(out, 3, 7);
       if (kind == 1) imadhi_kernel<<<blocks, threads>>>(out, 0x9e3779b9u, 7);
       if (kind == 2) lop_kernel<<<blocks, threads>>>(out, 0x9e3779b9u, 7);
-      if (kind == 3) bfly_kernel<<<blocks, threads>>>(out, 123456789u, fdfb::host_shoup(123456789u, 1073692673u), 1073692673u);
+      if (kind == 3) bfly_kernel<<<blocks, threads>>>(out, 123456789u, fdfb::host_shoup(123456789u, 1073692673u), 1073692673u, 0u);
       cudaEventRecord(b);
       cudaEventSynchronize(b);
       float ms = 0;

@@ -112,6 +112,8 @@ WORKLOADS: Dict[str, Workload] = {
     "mixed": Workload("mixed", 3, [Group("B", 37, 4, "uniform"),
                                    Group("D", 1000, 4, "uniform"),
                                    Group("C", 2900, 4, "uniform")]),
+    # the N = 2048 group of the mixed workload on its own
+    "n2048": Workload("n2048", 3, [Group("D", 1000, 4, "uniform")]),
     "mlp": Workload("mlp", 4, [Group("D", 0, 2, "uniform")],
                     mlp_layers=[784, 128, 64, 10], mlp_inputs=64),
 }
