@@ -288,6 +288,48 @@ FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p, 
   }
 }
 
+// The same passes on M polynomials held by the same threads at once: every
+// twiddle is loaded once for the M butterflies that use it, and the M
+// independent butterfly chains give the scheduler M times the parallelism.
+template <int L, int EL, int PASS, int M>
+FD_HD void fwd_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
+  using Y = Layout<L, EL>;
+  constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
+#pragma unroll
+  for (int s = F; s < F + LEN; ++s) {
+    const int rb = Y::rbit(PASS, s);
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      if (!(r & (1 << rb))) {
+        const int ti = tw_index<L, EL, PASS>(s, t, r);
+        const uint2 w = FD_LDG(tw + ti);
+#pragma unroll
+        for (int m = 0; m < M; ++m) bfly_fwd(v[m][r], v[m][r | (1 << rb)], w, p, z);
+      }
+    }
+  }
+}
+
+template <int L, int EL, int PASS, int M>
+FD_HD void inv_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
+  using Y = Layout<L, EL>;
+  constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
+#pragma unroll
+  for (int s = F + LEN - 1; s >= F; --s) {
+    const int b = L - 1 - s;
+    const int rb = Y::rbit(PASS, s);
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      if (!(r & (1 << rb))) {
+        const int ti = tw_index<L, EL, PASS>(L - 1 - b, t, r);
+        const uint2 w = FD_LDG(tw + ti);
+#pragma unroll
+        for (int m = 0; m < M; ++m) bfly_inv(v[m][r], v[m][r | (1 << rb)], w, p, z);
+      }
+    }
+  }
+}
+
 // Shared-memory swizzle for the exchange buffers: XORs the five bank bits of
 // j with a GF(2)-linear function of its higher bits, so that for every pass
 // layout the 32 lanes of a warp hit 32 distinct banks for each register

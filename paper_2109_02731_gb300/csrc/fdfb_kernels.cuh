@@ -54,6 +54,50 @@ __device__ __forceinline__ void exchange(uint32_t (&v)[1 << EL], int t, uint32_t
   group_sync<Y::G>(bar);
 }
 
+// Exchange / transforms of M polynomials at once (buffer m at xb + m * XW).
+template <int L, int EL, int FROM, int TO, int M, int XW>
+__device__ __forceinline__ void exchange_m(uint32_t (&v)[M][1 << EL], int t, uint32_t* xb, int bar) {
+  using Y = Layout<L, EL>;
+  using X = Xch<L, EL>;
+  const uint32_t wb = X::addr(Y::j_of(FROM, t, 0));
+#pragma unroll
+  for (int r = 0; r < Y::E; ++r) {
+    const uint32_t a = X::join(wb, X::addr(Y::j_of(FROM, 0, r)));
+#pragma unroll
+    for (int m = 0; m < M; ++m) xb[m * XW + a] = v[m][r];
+  }
+  group_sync<Y::G>(bar);
+  const uint32_t rb = X::addr(Y::j_of(TO, t, 0));
+#pragma unroll
+  for (int r = 0; r < Y::E; ++r) {
+    const uint32_t a = X::join(rb, X::addr(Y::j_of(TO, 0, r)));
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m][r] = xb[m * XW + a];
+  }
+  group_sync<Y::G>(bar);
+}
+
+template <int L, int EL, int PASS, int M, int XW>
+__device__ __forceinline__ void ntt_fwd_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
+                                          uint32_t* xb, int bar, uint32_t z) {
+  using Y = Layout<L, EL>;
+  if constexpr (PASS < Y::K) {
+    if constexpr (PASS > 0) exchange_m<L, EL, PASS - 1, PASS, M, XW>(v, t, xb, bar);
+    fwd_pass_m<L, EL, PASS, M>(v, t, tw, p, z);
+    ntt_fwd_m<L, EL, PASS + 1, M, XW>(v, t, tw, p, xb, bar, z);
+  }
+}
+
+template <int L, int EL, int PASS, int M, int XW>
+__device__ __forceinline__ void ntt_inv_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
+                                          uint32_t* xb, int bar, uint32_t z) {
+  if constexpr (PASS >= 0) {
+    inv_pass_m<L, EL, PASS, M>(v, t, tw, p, z);
+    if constexpr (PASS > 0) exchange_m<L, EL, PASS, PASS - 1, M, XW>(v, t, xb, bar);
+    ntt_inv_m<L, EL, PASS - 1, M, XW>(v, t, tw, p, xb, bar, z);
+  }
+}
+
 // Forward negacyclic NTT of one polynomial by one thread group: v holds the
 // pass-0 layout (natural order) on entry and the last-pass layout
 // (bit-reversed order, values in [0, 4p)) on exit.  xb is the group's
@@ -126,7 +170,7 @@ struct BRParams {
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
 };
 
-template <int L, int EL, int P, typename W, typename DT>
+template <int L, int EL, int P, typename W, typename DT, int M = 1>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -139,13 +183,17 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * xwords() * 4;
+    return acc + an + r1 + (size_t)P * M * xwords() * 4;
   }
   static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3; }
 };
 
 // Resident CTAs per SM the register budget is sized for (512 threads per SM).
 constexpr int br_min_blocks(int threads) { return threads >= 512 ? 1 : 512 / threads; }
+// Resident CTAs per SM that leave each thread `regs` registers.
+constexpr int br_blocks_for_regs(int threads, int regs) {
+  return 65536 / (threads * regs) > 0 ? 65536 / (threads * regs) : 1;
+}
 
 // Transform-domain sum -> inverse-transform input in [0, 2p): a 64-bit sum
 // (< 8 p^2) is Montgomery-reduced (< 3p) and corrected once.
@@ -170,8 +218,9 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // once (fewer instructions, twice the accumulator registers); otherwise each
 // product is Montgomery-reduced as it is formed.  MINB: resident CTAs per SM
 // the register budget is sized for.
+// M: polynomials transformed together by one thread group (1 or 2).
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL)))>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -220,7 +269,8 @@ blind_rotate_kernel(const BRParams prm) {
   const uint32_t z = prm.S.zero;
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
-  uint32_t* xb = exch + grp * BRShape<L, EL, P, W, DT>::xwords();
+  constexpr int XW = (int)BRShape<L, EL, P, W, DT, M>::xwords();
+  uint32_t* xb = exch + grp * M * XW;
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
@@ -257,31 +307,39 @@ blind_rotate_kernel(const BRParams prm) {
     for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
     const int swap = (grp == 0) ? 1 : 0;
     const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N;
-    for (int r = 0; r < R; ++r) {
-      uint32_t v[E];
+    for (int r0 = 0; r0 < R; r0 += M) {
+      uint32_t v[M][E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) v[k] = dig[r * N + Y::j_of(0, t, k)];
-      ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar, z);
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[m][k] = dig[(r0 + m) * N + Y::j_of(0, t, k)];
+      ntt_fwd_m<L, EL, 0, M, XW>(v, t, twf, p, xb, bar, z);
       if constexpr (WIDE) {
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = csub(csub(v[k], 2 * p), p);
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+          for (int k = 0; k < E; ++k) v[m][k] = csub(csub(v[m][k], 2 * p), p);
       }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const uint4* kp = reinterpret_cast<const uint4*>(krow + ((size_t)r * 2 + (c ^ swap)) * N) + t;
 #pragma unroll
-        for (int q4 = 0; q4 < E / 4; ++q4) {
-          const uint4 kk = ldg_stream(kp + q4 * G);
-          const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+        for (int m = 0; m < M; ++m) {
+          const uint4* kp =
+              reinterpret_cast<const uint4*>(krow + ((size_t)(r0 + m) * 2 + (c ^ swap)) * N) + t;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if constexpr (WIDE) {
-              // v < p and K < p: 2l <= 8 products stay below 2^63
-              macc[c][q4 * 4 + u] += (uint64_t)v[q4 * 4 + u] * kv[u];
-            } else {
-              const uint32_t m = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);  // < 2p
-              uint32_t s2 = (uint32_t)macc[c][q4 * 4 + u] + m + z;
-              macc[c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+          for (int q4 = 0; q4 < E / 4; ++q4) {
+            const uint4 kk = ldg_stream(kp + q4 * G);
+            const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if constexpr (WIDE) {
+                // v < p and K < p: 2l <= 8 products stay below 2^63
+                macc[c][q4 * 4 + u] += (uint64_t)v[m][q4 * 4 + u] * kv[u];
+              } else {
+                const uint32_t mm = redc((uint64_t)v[m][q4 * 4 + u] * kv[u], p, pneg);  // < 2p
+                uint32_t s2 = (uint32_t)macc[c][q4 * 4 + u] + mm + z;
+                macc[c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+              }
             }
           }
         }
@@ -292,27 +350,48 @@ blind_rotate_kernel(const BRParams prm) {
     // Inverse transforms.  Column c is lifted by group c, which keeps its own
     // residues in registers; every other group stages its residues for it.
     uint32_t own[E];
-    {
-      uint32_t v[E];
+    if constexpr (M == 2) {
+      uint32_t v[2][E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
-      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
-      uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
+      for (int k = 0; k < E; ++k) {
+        v[0][k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
+        v[1][k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
+      }
+      ntt_inv_m<L, EL, Y::K - 1, 2, XW>(v, t, twi, p, xb, bar, z);
+      uint32_t* dst0 = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
-      for (int k = 0; k < E; ++k) dst[Y::j_of(0, t, k)] = csub(v[k], p);
-    }
-    {
-      uint32_t v[E];
-#pragma unroll
-      for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
-      ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+      for (int k = 0; k < E; ++k) dst0[Y::j_of(0, t, k)] = csub(v[0][k], p);
       if (grp < 2) {
 #pragma unroll
-        for (int k = 0; k < E; ++k) own[k] = csub(v[k], p);
+        for (int k = 0; k < E; ++k) own[k] = csub(v[1][k], p);
       } else {
-        uint32_t* dst = stage + stage_slot<P>(grp, 1) * N;
+        uint32_t* dst1 = stage + stage_slot<P>(grp, 1) * N;
+#pragma unroll
+        for (int k = 0; k < E; ++k) dst1[Y::j_of(0, t, k)] = csub(v[1][k], p);
+      }
+    } else {
+      {
+        uint32_t v[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
+        ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+        uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
         for (int k = 0; k < E; ++k) dst[Y::j_of(0, t, k)] = csub(v[k], p);
+      }
+      {
+        uint32_t v[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
+        ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+        if (grp < 2) {
+#pragma unroll
+          for (int k = 0; k < E; ++k) own[k] = csub(v[k], p);
+        } else {
+          uint32_t* dst = stage + stage_slot<P>(grp, 1) * N;
+#pragma unroll
+          for (int k = 0; k < E; ++k) dst[Y::j_of(0, t, k)] = csub(v[k], p);
+        }
       }
     }
     __syncthreads();
