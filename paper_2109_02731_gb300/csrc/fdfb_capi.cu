@@ -439,7 +439,9 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   const int w = (int)P.log2q, L = ilog2(P.N);
   const Ops* ops0 = find_ops(L, w, 0);
   if (!ops0) return FDFB_EINVAL;
-  // Exactness of the lifted negacyclic products (every variant has the same primes).
+  // Exactness of the lifted negacyclic products with the 30-bit primes of
+  // variant 0 (which also serves PubMux and key generation); variants of the
+  // lazy prime family are kept below only where the blind rotation stays exact.
   const long double q = ldexpl(1.0L, w);
   const long double br_max = 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * (q / 2);
   const long double pm_max = (long double)P.N * (P.t - 1) * q;
@@ -463,13 +465,14 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
     auto v = std::make_unique<Variant>();
     v->ops = ops;
     if ((int)P.log2Bg > ops->max_log2B) continue;  // digits too wide for this variant
+    if (ops->family && !host::lift_is_exact(ops->P, br_max, ops->family)) continue;
     v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);
     if (v->br_smem > (size_t)max_smem) {
       continue;
     }
     FD_CUDA(ops->br_prepare(v->br_smem));
     std::vector<uint2> fwd, inv;
-    host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv);
+    host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv, ops->family);
     FD_TRY(v->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
     FD_CUDA(cudaMemcpy(v->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
     FD_CUDA(cudaMemcpy((uint2*)v->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),

@@ -27,6 +27,12 @@ namespace fdfb {
 constexpr int kMaxPrimes = 4;
 // Largest primes below 2^30 that are 1 mod 2^14 (so 2N | p - 1 for N <= 8192).
 constexpr uint32_t kPrimes[kMaxPrimes] = {1073692673u, 1073643521u, 1073479681u, 1073430529u};
+// Largest primes below (2^32 - 2^16) / 25 that are 1 mod 2^14 (the "lazy"
+// family): a forward transform of inputs below 2^16 keeps every value below
+// 2^16 + 24 p < 2^32 through 12 stages without reducing (bfly_fwd_lazy).
+constexpr uint32_t kPrimesLazy[kMaxPrimes] = {171737089u, 171687937u, 171491329u, 171048961u};
+// Prime family 0: kPrimes, 1: kPrimesLazy (host side).
+inline uint32_t family_prime(int family, int i) { return family ? kPrimesLazy[i] : kPrimes[i]; }
 
 FD_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
 #ifdef __CUDA_ARCH__
@@ -216,6 +222,15 @@ FD_HD void bfly_fwd(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p, uint32_t z) {
   X = x + t + z;
   Y = x - t + 2 * p;
 }
+// Forward butterfly for the lazy prime family: X is not reduced, so each
+// stage raises the bound on both outputs by less than 2p (X + WY and
+// X - WY + 2p with WY in [0, 2p)).
+FD_HD void bfly_fwd_lazy(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p, uint32_t z) {
+  const uint32_t x = X;
+  const uint32_t t = mul_shoup(Y, w.x, w.y, p);
+  X = x + t + z;
+  Y = x - t + 2 * p;
+}
 // Inverse Gentleman-Sande butterfly: X, Y in [0, 2p) -> X + Y, (X - Y) W.
 FD_HD void bfly_inv(uint32_t& X, uint32_t& Y, uint2 w, uint32_t p, uint32_t z) {
   uint32_t s = X + Y + z;
@@ -291,7 +306,7 @@ FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p, 
 // The same passes on M polynomials held by the same threads at once: every
 // twiddle is loaded once for the M butterflies that use it, and the M
 // independent butterfly chains give the scheduler M times the parallelism.
-template <int L, int EL, int PASS, int M>
+template <int L, int EL, int PASS, int M, bool LZ = false>
 FD_HD void fwd_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
   using Y = Layout<L, EL>;
   constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
@@ -304,7 +319,10 @@ FD_HD void fwd_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_
         const int ti = tw_index<L, EL, PASS>(s, t, r);
         const uint2 w = FD_LDG(tw + ti);
 #pragma unroll
-        for (int m = 0; m < M; ++m) bfly_fwd(v[m][r], v[m][r | (1 << rb)], w, p, z);
+        for (int m = 0; m < M; ++m) {
+          if constexpr (LZ) bfly_fwd_lazy(v[m][r], v[m][r | (1 << rb)], w, p, z);
+          else bfly_fwd(v[m][r], v[m][r | (1 << rb)], w, p, z);
+        }
       }
     }
   }

@@ -54,13 +54,13 @@ inline uint32_t generator(uint32_t p) {
 // keep 2^EL coefficients per thread: the blocks [2^s, 2^(s+1)) read by the
 // last register pass are stored transposed (see tw_index).
 inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>& fwd,
-                           std::vector<uint2>& inv) {
+                           std::vector<uint2>& inv, int family = 0) {
   const uint32_t N = 1u << L;
   S.P = P;
   fwd.assign((size_t)P * N, uint2{0, 0});
   inv.assign((size_t)P * N, uint2{0, 0});
   for (int i = 0; i < kMaxPrimes; ++i) {
-    const uint32_t p = kPrimes[i];
+    const uint32_t p = family_prime(family, i);
     S.p[i] = p;
     uint32_t x = 1;  // Newton iteration for p^-1 mod 2^32
     for (int it = 0; it < 5; ++it) x *= 2u - p * x;
@@ -79,15 +79,15 @@ inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>
   }
   for (int i = 0; i < kMaxPrimes; ++i)
     for (int j = i + 1; j < kMaxPrimes; ++j) {
-      S.gc[i][j] = inv_mod(kPrimes[i] % kPrimes[j], kPrimes[j]);
-      S.gcs[i][j] = shoup(S.gc[i][j], kPrimes[j]);
+      S.gc[i][j] = inv_mod(family_prime(family, i) % family_prime(family, j), family_prime(family, j));
+      S.gcs[i][j] = shoup(S.gc[i][j], family_prime(family, j));
     }
   S.M[0] = 1;
-  for (int i = 0; i < kMaxPrimes; ++i) S.M[i + 1] = S.M[i] * (uint64_t)kPrimes[i];
-  S.half_top = kPrimes[P - 1] / 2;
+  for (int i = 0; i < kMaxPrimes; ++i) S.M[i + 1] = S.M[i] * (uint64_t)family_prime(family, i);
+  S.half_top = family_prime(family, P - 1) / 2;
   S.zero = 0;
   for (int i = 0; i < P; ++i) {
-    const uint32_t p = kPrimes[i];
+    const uint32_t p = family_prime(family, i);
     const uint32_t g = generator(p);
     const uint32_t psi = (uint32_t)powmod(g, (p - 1) / (2 * N), p);  // primitive 2N-th root
     const uint32_t psi_inv = inv_mod(psi, p);
@@ -114,10 +114,10 @@ inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>
 
 // log2 of the largest |centred result| the prime set can lift exactly:
 // the top Garner digit must stay below p_{P-1}/2 - 1 for both signs.
-inline bool lift_is_exact(int P, long double max_abs) {
+inline bool lift_is_exact(int P, long double max_abs, int family = 0) {
   long double m = 1;
-  for (int i = 0; i < P - 1; ++i) m *= (long double)kPrimes[i];
-  return max_abs / m + 2.0L < (long double)(kPrimes[P - 1] / 2);
+  for (int i = 0; i < P - 1; ++i) m *= (long double)family_prime(family, i);
+  return max_abs / m + 2.0L < (long double)(family_prime(family, P - 1) / 2);
 }
 
 }  // namespace host

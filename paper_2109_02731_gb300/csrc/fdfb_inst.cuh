@@ -5,18 +5,18 @@
 namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false>
 struct Inst {
   using Sh = BRShape<L, EL, P, W, DT, M>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
-    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M>,
+    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ><<<(unsigned)batch, THREADS, smem, st>>>(prm);
     return cudaGetLastError();
   }
   static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {
@@ -55,7 +55,7 @@ struct Inst {
   }
   static Ops ops() {
     return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
-               &pubmux, &rlwe_enc, &bsk_ntt};
+               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0};
   }
 };
 

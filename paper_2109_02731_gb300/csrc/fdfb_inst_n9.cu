@@ -5,10 +5,13 @@
 namespace fdfb {
 const Ops* ops_n9(int w, int variant) {
   static const Ops a0 = Inst<9, 4, 2, uint32_t, uint16_t>::ops();
+  // lazy prime family, paired transforms with 64-bit sums
+  static const Ops a1 = Inst<9, 4, 2, uint32_t, uint16_t, true, br_min_blocks(2 << (9 - 4)), 2, true>::ops();
   static const Ops b0 = Inst<9, 4, 3, uint64_t, uint16_t>::ops();
   if (w == 32) {
     switch (variant) {
       case 0: return &a0;
+      case 1: return &a1;
       default: return nullptr;
     }
   }

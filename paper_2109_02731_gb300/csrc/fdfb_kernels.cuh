@@ -77,14 +77,14 @@ __device__ __forceinline__ void exchange_m(uint32_t (&v)[M][1 << EL], int t, uin
   group_sync<Y::G>(bar);
 }
 
-template <int L, int EL, int PASS, int M, int XW>
+template <int L, int EL, int PASS, int M, int XW, bool LZ = false>
 __device__ __forceinline__ void ntt_fwd_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
                                           uint32_t* xb, int bar, uint32_t z) {
   using Y = Layout<L, EL>;
   if constexpr (PASS < Y::K) {
     if constexpr (PASS > 0) exchange_m<L, EL, PASS - 1, PASS, M, XW>(v, t, xb, bar);
-    fwd_pass_m<L, EL, PASS, M>(v, t, tw, p, z);
-    ntt_fwd_m<L, EL, PASS + 1, M, XW>(v, t, tw, p, xb, bar, z);
+    fwd_pass_m<L, EL, PASS, M, LZ>(v, t, tw, p, z);
+    ntt_fwd_m<L, EL, PASS + 1, M, XW, LZ>(v, t, tw, p, xb, bar, z);
   }
 }
 
@@ -195,13 +195,17 @@ constexpr int br_blocks_for_regs(int threads, int regs) {
   return 65536 / (threads * regs) > 0 ? 65536 / (threads * regs) : 1;
 }
 
-// Transform-domain sum -> inverse-transform input in [0, 2p): a 64-bit sum
-// (< 8 p^2) is Montgomery-reduced (< 3p) and corrected once.
-template <bool WIDE, typename Acc>
-__device__ __forceinline__ uint32_t acc_to_inv(Acc a, uint32_t p, uint32_t pneg) {
+// Transform-domain sum -> inverse-transform input in [0, 2p).  A 64-bit sum
+// of at most 8 products is Montgomery-reduced: with transform values below p
+// (< 8 p^2 -> below 3p) it is corrected once; with the lazy family's
+// unreduced transform values (below 2^32: < 2^35 p -> below 9p) it is
+// brought into [0, 2p) by Shoup's product by 1.
+template <bool WIDE, bool LZ, typename Acc>
+__device__ __forceinline__ uint32_t acc_to_inv(Acc a, uint32_t p, uint32_t pneg, uint32_t ones) {
   if constexpr (WIDE) {
     const uint32_t r = redc((uint64_t)a, p, pneg);
-    return umin32(r, r - 2 * p);
+    if constexpr (LZ) return mul_shoup(r, 1u, ones, p);
+    else return umin32(r, r - 2 * p);
   } else {
     return (uint32_t)a;
   }
@@ -219,13 +223,17 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // product is Montgomery-reduced as it is formed.  MINB: resident CTAs per SM
 // the register budget is sized for.
 // M: polynomials transformed together by one thread group (1 or 2).
+// LZ: the prime set is the lazy family; the forward transforms of the digits
+// skip all intermediate reductions and their outputs (below 2^32) enter the
+// pointwise products unreduced.
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
   static_assert(P >= 2, "the column owners are groups 0 and 1");
+  static_assert(!LZ || (L <= 12 && sizeof(DT) <= 2), "lazy bound: 2^16 + 2 L p < 2^32");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
@@ -266,6 +274,7 @@ blind_rotate_kernel(const BRParams prm) {
 
   const uint32_t p = prm.S.p[grp];
   const uint32_t pneg = prm.S.pneg[grp];
+  const uint32_t ones = prm.S.ones[grp];
   const uint32_t z = prm.S.zero;
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
@@ -280,18 +289,21 @@ blind_rotate_kernel(const BRParams prm) {
   for (int i = 0; i < n; ++i) {
     const int a = aN[i];
     // d = acc X^{-a} - acc, rounded and split into digits (component major).
+    // Coefficient j of acc X^{-a} is acc[(j + a) mod 2N], negated when that
+    // index lies in [N, 2N) (X^N = -1).
+#pragma unroll 4
     for (int idx = tid; idx < 2 * N; idx += THREADS) {
       const int c = idx >> L, j = idx & (N - 1);
-      int m = j + a;
-      bool neg = false;
-      if (m >= N) { m -= N; neg = true; }
-      if (m >= N) { m -= N; neg = false; }
-      W rv = acc[c * N + m];
-      if (neg) rv = (W)(0 - rv);
-      const W d = (W)(rv - acc[c * N + j]);
-      const W xt = rt ? (W)((W)(d + half_rt) >> rt) : d;
-      for (int l = 0; l < lg; ++l)
-        dig[(c * lg + l) * N + j] = (DT)((uint32_t)(xt >> (l * log2Bg)) & dmask);
+      const int m = (j + a) & (2 * N - 1);
+      const W neg = (W)0 - (W)(m >> L);  // all ones when negated
+      const W* ac = acc + c * N;
+      const W rv = (W)((ac[m & (N - 1)] ^ neg) - neg);
+      const W d = (W)(rv - ac[j]);
+      const W xt = (W)((W)(d + half_rt) >> rt);
+      DT* dp = dig + c * lg * N + j;
+#pragma unroll
+      for (int l = 0; l < 4; ++l)  // lg <= 4
+        if (l < lg) dp[l * N] = (DT)((uint32_t)(xt >> (l * log2Bg)) & dmask);
     }
     __syncthreads();
 
@@ -313,8 +325,8 @@ blind_rotate_kernel(const BRParams prm) {
       for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int k = 0; k < E; ++k) v[m][k] = dig[(r0 + m) * N + Y::j_of(0, t, k)];
-      ntt_fwd_m<L, EL, 0, M, XW>(v, t, twf, p, xb, bar, z);
-      if constexpr (WIDE) {
+      ntt_fwd_m<L, EL, 0, M, XW, LZ>(v, t, twf, p, xb, bar, z);
+      if constexpr (WIDE && !LZ) {
 #pragma unroll
         for (int m = 0; m < M; ++m)
 #pragma unroll
@@ -333,7 +345,8 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if constexpr (WIDE) {
-                // v < p and K < p: 2l <= 8 products stay below 2^63
+                // K < p, and v < p (or, lazy family, v < 2^32 and p < 2^28):
+                // 2l <= 8 products stay below 2^63
                 macc[c][q4 * 4 + u] += (uint64_t)v[m][q4 * 4 + u] * kv[u];
               } else {
                 const uint32_t mm = redc((uint64_t)v[m][q4 * 4 + u] * kv[u], p, pneg);  // < 2p
@@ -354,8 +367,8 @@ blind_rotate_kernel(const BRParams prm) {
       uint32_t v[2][E];
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        v[0][k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
-        v[1][k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
+        v[0][k] = acc_to_inv<WIDE, LZ>(macc[0][k], p, pneg, ones);
+        v[1][k] = acc_to_inv<WIDE, LZ>(macc[1][k], p, pneg, ones);
       }
       ntt_inv_m<L, EL, Y::K - 1, 2, XW>(v, t, twi, p, xb, bar, z);
       uint32_t* dst0 = stage + stage_slot<P>(grp, swap) * N;
@@ -373,7 +386,7 @@ blind_rotate_kernel(const BRParams prm) {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[0][k], p, pneg);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
@@ -382,7 +395,7 @@ blind_rotate_kernel(const BRParams prm) {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE>(macc[1][k], p, pneg);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[1][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         if (grp < 2) {
 #pragma unroll

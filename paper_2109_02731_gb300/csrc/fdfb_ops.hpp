@@ -18,6 +18,7 @@ struct Ops {
   cudaError_t (*rlwe_enc)(const RlweEncParams& prm, int64_t count, cudaStream_t st);
   cudaError_t (*bsk_ntt)(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
                          cudaStream_t st);
+  int family;  // NTT prime family of the blind rotation (0: 30-bit primes, 1: lazy family)
 };
 
 // Returns the launcher table of register-layout variant `variant` for
