@@ -388,4 +388,26 @@ struct Xch {
   FD_HD static uint32_t join(uint32_t base, uint32_t off) { return kAdditive ? base + off : base ^ off; }
 };
 
+// Exchange buffer of two polynomials transformed together: the two words of
+// position j form one 64-bit word at index addr(j).  A 64-bit shared access
+// is served per half-warp, so the swizzle XORs the low four bits of j (the
+// 8-byte bank) with a GF(2)-linear function of bits 4.. such that, for every
+// pass layout and register index, the 16 lanes of each half-warp hit 16
+// distinct 8-byte banks (masks found by exhaustive search over the layouts).
+template <int L, int EL>
+struct Xch64 {
+  FD_HD static constexpr uint32_t mask(int b) {
+    if (L == 8 && EL == 3) { constexpr uint8_t m[] = {1, 4, 10, 0}; return m[b - 4]; }
+    return b < 8 ? (1u << (b - 4)) : 0u;
+  }
+  FD_HD static uint32_t addr(uint32_t j) {
+    uint32_t h = 0;
+#pragma unroll
+    for (int b = 4; b < L; ++b)
+      if ((j >> b) & 1u) h ^= mask(b);
+    return j ^ h;
+  }
+  FD_HD static uint32_t join(uint32_t base, uint32_t off) { return base ^ off; }
+};
+
 }  // namespace fdfb

@@ -5,18 +5,18 @@
 namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false>
 struct Inst {
-  using Sh = BRShape<L, EL, P, W, DT, M>;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
-    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ>,
+    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP><<<(unsigned)batch, THREADS, smem, st>>>(prm);
     return cudaGetLastError();
   }
   static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {

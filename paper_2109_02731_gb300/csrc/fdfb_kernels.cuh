@@ -54,47 +54,73 @@ __device__ __forceinline__ void exchange(uint32_t (&v)[1 << EL], int t, uint32_t
   group_sync<Y::G>(bar);
 }
 
-// Exchange / transforms of M polynomials at once (buffer m at xb + m * XW).
-template <int L, int EL, int FROM, int TO, int M, int XW>
+// Exchange / transforms of M polynomials at once.  M = 1: one buffer of XW
+// words.  M = 2: the two words of a position travel as one 64-bit word
+// (Xch64), in a buffer of XW 64-bit words; with PP the exchanges between
+// passes 0 and 1 and between passes 1 and 2 use two such buffers, so a
+// buffer is rewritten only after the other buffer's exchange has synchronised
+// the group, and the barrier that protects the reads can be dropped.  That
+// needs three passes per transform and a block-wide barrier between the last
+// forward and the first inverse exchange and between the last inverse and the
+// next forward exchange (the blind rotation has both).
+template <int L, int EL, int FROM, int TO, int M, int XW, bool PP = false>
 __device__ __forceinline__ void exchange_m(uint32_t (&v)[M][1 << EL], int t, uint32_t* xb, int bar) {
   using Y = Layout<L, EL>;
-  using X = Xch<L, EL>;
-  const uint32_t wb = X::addr(Y::j_of(FROM, t, 0));
+  if constexpr (M == 2) {
+    static_assert(!PP || Y::K == 3, "ping-pong exchange buffers need three passes");
+    using X = Xch64<L, EL>;
+    uint2* b = reinterpret_cast<uint2*>(xb) + (PP ? ((FROM < TO ? FROM : TO) & 1) * XW : 0);
+    const uint32_t wb = X::addr(Y::j_of(FROM, t, 0));
 #pragma unroll
-  for (int r = 0; r < Y::E; ++r) {
-    const uint32_t a = X::join(wb, X::addr(Y::j_of(FROM, 0, r)));
+    for (int r = 0; r < Y::E; ++r) b[X::join(wb, X::addr(Y::j_of(FROM, 0, r)))] = make_uint2(v[0][r], v[1][r]);
+    group_sync<Y::G>(bar);
+    const uint32_t rb = X::addr(Y::j_of(TO, t, 0));
 #pragma unroll
-    for (int m = 0; m < M; ++m) xb[m * XW + a] = v[m][r];
+    for (int r = 0; r < Y::E; ++r) {
+      const uint2 x = b[X::join(rb, X::addr(Y::j_of(TO, 0, r)))];
+      v[0][r] = x.x;
+      v[1][r] = x.y;
+    }
+    if constexpr (!PP) group_sync<Y::G>(bar);
+  } else {
+    using X = Xch<L, EL>;
+    const uint32_t wb = X::addr(Y::j_of(FROM, t, 0));
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      const uint32_t a = X::join(wb, X::addr(Y::j_of(FROM, 0, r)));
+#pragma unroll
+      for (int m = 0; m < M; ++m) xb[m * XW + a] = v[m][r];
+    }
+    group_sync<Y::G>(bar);
+    const uint32_t rb = X::addr(Y::j_of(TO, t, 0));
+#pragma unroll
+    for (int r = 0; r < Y::E; ++r) {
+      const uint32_t a = X::join(rb, X::addr(Y::j_of(TO, 0, r)));
+#pragma unroll
+      for (int m = 0; m < M; ++m) v[m][r] = xb[m * XW + a];
+    }
+    group_sync<Y::G>(bar);
   }
-  group_sync<Y::G>(bar);
-  const uint32_t rb = X::addr(Y::j_of(TO, t, 0));
-#pragma unroll
-  for (int r = 0; r < Y::E; ++r) {
-    const uint32_t a = X::join(rb, X::addr(Y::j_of(TO, 0, r)));
-#pragma unroll
-    for (int m = 0; m < M; ++m) v[m][r] = xb[m * XW + a];
-  }
-  group_sync<Y::G>(bar);
 }
 
-template <int L, int EL, int PASS, int M, int XW, bool LZ = false>
+template <int L, int EL, int PASS, int M, int XW, bool LZ = false, bool PP = false>
 __device__ __forceinline__ void ntt_fwd_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
                                           uint32_t* xb, int bar, uint32_t z) {
   using Y = Layout<L, EL>;
   if constexpr (PASS < Y::K) {
-    if constexpr (PASS > 0) exchange_m<L, EL, PASS - 1, PASS, M, XW>(v, t, xb, bar);
+    if constexpr (PASS > 0) exchange_m<L, EL, PASS - 1, PASS, M, XW, PP>(v, t, xb, bar);
     fwd_pass_m<L, EL, PASS, M, LZ>(v, t, tw, p, z);
-    ntt_fwd_m<L, EL, PASS + 1, M, XW, LZ>(v, t, tw, p, xb, bar, z);
+    ntt_fwd_m<L, EL, PASS + 1, M, XW, LZ, PP>(v, t, tw, p, xb, bar, z);
   }
 }
 
-template <int L, int EL, int PASS, int M, int XW>
+template <int L, int EL, int PASS, int M, int XW, bool PP = false>
 __device__ __forceinline__ void ntt_inv_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
                                           uint32_t* xb, int bar, uint32_t z) {
   if constexpr (PASS >= 0) {
     inv_pass_m<L, EL, PASS, M>(v, t, tw, p, z);
-    if constexpr (PASS > 0) exchange_m<L, EL, PASS, PASS - 1, M, XW>(v, t, xb, bar);
-    ntt_inv_m<L, EL, PASS - 1, M, XW>(v, t, tw, p, xb, bar, z);
+    if constexpr (PASS > 0) exchange_m<L, EL, PASS, PASS - 1, M, XW, PP>(v, t, xb, bar);
+    ntt_inv_m<L, EL, PASS - 1, M, XW, PP>(v, t, tw, p, xb, bar, z);
   }
 }
 
@@ -170,7 +196,7 @@ struct BRParams {
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
 };
 
-template <int L, int EL, int P, typename W, typename DT, int M = 1>
+template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -183,7 +209,7 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * M * xwords() * 4;
+    return acc + an + r1 + (size_t)P * M * (PP ? 2 : 1) * xwords() * 4;
   }
   static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3; }
 };
@@ -226,8 +252,10 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // LZ: the prime set is the lazy family; the forward transforms of the digits
 // skip all intermediate reductions and their outputs (below 2^32) enter the
 // pointwise products unreduced.
+// PP: two exchange buffers per group used in turn (M = 2 only), one group
+// barrier per exchange instead of two.
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -278,8 +306,9 @@ blind_rotate_kernel(const BRParams prm) {
   const uint32_t z = prm.S.zero;
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
-  constexpr int XW = (int)BRShape<L, EL, P, W, DT, M>::xwords();
-  uint32_t* xb = exch + grp * M * XW;
+  static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
+  constexpr int XW = (int)BRShape<L, EL, P, W, DT, M, PP>::xwords();
+  uint32_t* xb = exch + grp * M * (PP ? 2 : 1) * XW;
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
@@ -325,7 +354,7 @@ blind_rotate_kernel(const BRParams prm) {
       for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int k = 0; k < E; ++k) v[m][k] = dig[(r0 + m) * N + Y::j_of(0, t, k)];
-      ntt_fwd_m<L, EL, 0, M, XW, LZ>(v, t, twf, p, xb, bar, z);
+      ntt_fwd_m<L, EL, 0, M, XW, LZ, PP>(v, t, twf, p, xb, bar, z);
       if constexpr (WIDE && !LZ) {
 #pragma unroll
         for (int m = 0; m < M; ++m)
@@ -370,7 +399,7 @@ blind_rotate_kernel(const BRParams prm) {
         v[0][k] = acc_to_inv<WIDE, LZ>(macc[0][k], p, pneg, ones);
         v[1][k] = acc_to_inv<WIDE, LZ>(macc[1][k], p, pneg, ones);
       }
-      ntt_inv_m<L, EL, Y::K - 1, 2, XW>(v, t, twi, p, xb, bar, z);
+      ntt_inv_m<L, EL, Y::K - 1, 2, XW, PP>(v, t, twi, p, xb, bar, z);
       uint32_t* dst0 = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
       for (int k = 0; k < E; ++k) dst0[Y::j_of(0, t, k)] = csub(v[0][k], p);

@@ -481,15 +481,15 @@ def test_every_variant_is_bit_exact(F, torch_cuda, ctx, oracle, name, seed, nl, 
 def test_lazy_family_only_where_exact(F, torch_cuda, ctx):
     """Variants on the lazy (28-bit) prime family are offered only for sets
     whose blind-rotation products they lift exactly.  At N = 1024, q = 2^32
-    there are seven variants: 0-4 on the 30-bit primes (1 and 3 with 8-bit
-    digits) and 5-6 on the lazy family (6 with 8-bit digits).  Set B
-    (product bound 2^50.6) gets all seven; a set with B_g = 2^11, l_g = 2
+    there are eight variants: 0-4 on the 30-bit primes (1 and 3 with 8-bit
+    digits) and 5-7 on the lazy family (6 with 8-bit digits).  Set B
+    (product bound 2^50.6) gets all eight; a set with B_g = 2^11, l_g = 2
     (bound 2^54.0: above the lazy family's 2^53.7, within the 30-bit primes'
     2^59) keeps only the 16-bit-digit variants 0, 2 and 4."""
     import dataclasses
     ps = S.PARAM_SETS["B"]
     wide = dataclasses.replace(ps, name="Bwide", log2Bg=11, lg=2)
-    assert ctx.variant_info(ctx.register(ps))[1] == 7
+    assert ctx.variant_info(ctx.register(ps))[1] == 8
     assert ctx.variant_info(ctx.register(wide))[1] == 3
 
 
