@@ -79,6 +79,8 @@ def lib():
                 "or_pubmux": ([i32, i32, i32, vp, vp, vp, vp], None),
                 "or_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
                 "or_fdfb_batch": ([vp, vp, vp, vp, vp, vp, i64, vp, vp], None),
+                "or_fdfb_bootstrap_multi": ([vp, vp, vp, vp, vp, i32, vp, vp], None),
+                "or_fdfb_batch_multi": ([vp, vp, vp, vp, vp, vp, i32, i64, vp, vp], None),
                 "or_lwe_affine": ([i32, i32, i32, i32, vp, vp, vp], None),
             }
             for name, (args, res) in sig.items():
@@ -343,6 +345,33 @@ def fdfb_batch(ps, keys: Keys, rotP, lut_ids, cts, threads: int | None = None) -
         set_threads(threads)
     lib().or_fdfb_batch(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(rotP), _p(ids),
                         len(ids), _p(cts), _p(out))
+    return out
+
+
+def fdfb_bootstrap_multi(ps, keys: Keys, rots, ct) -> np.ndarray:
+    """k functions of one input, sharing the sign part.  rots: int64[k][2][N]
+    (p0, p1 per table); returns [k][n+1]."""
+    P = params(ps)
+    rots, ct = _i64(rots), _u64(ct)
+    k = rots.shape[0]
+    out = np.zeros((k, ps.n + 1), dtype=np.uint64)
+    lib().or_fdfb_bootstrap_multi(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(rots), k,
+                                  _p(ct), _p(out))
+    return out
+
+
+def fdfb_batch_multi(ps, keys: Keys, rotP, lut_ids, cts, threads: int | None = None) -> np.ndarray:
+    """rotP: int64[n_luts][2][N]; lut_ids: int32[count][k]; cts: [count][n+1];
+    returns [count][k][n+1]."""
+    P = params(ps)
+    rotP, cts = _i64(rotP), _u64(cts)
+    ids = np.ascontiguousarray(np.asarray(lut_ids, dtype=np.int32))
+    count, k = ids.shape
+    out = np.zeros((count, k, ps.n + 1), dtype=np.uint64)
+    if threads is not None:
+        set_threads(threads)
+    lib().or_fdfb_batch_multi(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(rotP), _p(ids),
+                              k, count, _p(cts), _p(out))
     return out
 
 

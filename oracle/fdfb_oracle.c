@@ -446,29 +446,30 @@ typedef struct {
     u64 *ctN, *sgn, *cR, *accF, *accBR, *cQ;
 } or_debug;
 
-/* Bootstrap (figure "functional-bootstrapping", left) under readings G1-G4:
- * ct: [n+1]; rotP0, rotP1: signed [N] (SetupPolynomial output);
- * out: [n+1]. */
-void or_fdfb_bootstrap(const or_params* P, const u64* bsk, const u64* pk, const u64* ksk,
-                       const i64* rotP0, const i64* rotP1, const u64* ct, u64* out,
-                       const or_debug* dbg) {
+/* Bootstrap (figure "functional-bootstrapping", left) under readings G1-G4,
+ * in two parts.  The sign part depends on the input only: ModSwitch, the sign
+ * accumulator, BlindRotate, SampleExtract + Delta/2 and the packing
+ * KeySwitch, giving ctN [n+1] and cR [2N].  The function part takes one
+ * table's rotation polynomials: PubMux, BlindRotate, SampleExtract and the
+ * LWE KeySwitch, giving out [n+1].  Several functions of one input share the
+ * sign part (Section "Application of Functional Bootstrapping": the first
+ * bootstrap's accumulators are reused for the next function). */
+static void or_fdfb_sign_part(const or_params* P, const u64* bsk, const u64* pk, const u64* ct,
+                              u64* ctN, u64* cR, const or_debug* dbg) {
     const int n = P->n, N = P->N, w = P->w, t = P->t;
     const u64 m = wmask(w);
     const u64 delta = delta_of(w, t);
     int logN = 0;
     while ((1 << logN) < N) ++logN;
 
-    u64* ctN = (u64*)malloc(sizeof(u64) * (n + 1));
     u64* sgnP = (u64*)malloc(sizeof(u64) * N);
     u64* acc = (u64*)malloc(sizeof(u64) * 2 * N);
     u64* lwe = (u64*)malloc(sizeof(u64) * (N + 1));
-    u64* cR = (u64*)malloc(sizeof(u64) * 2 * N);
-    i64* r0 = (i64*)malloc(sizeof(i64) * N);
-    i64* r1 = (i64*)malloc(sizeof(i64) * N);
 
     /* ct_N = ModSwitch(ct, q, 2N) */
     or_modswitch(w, logN + 1, n, ct, ctN);
     const i64 bN = (i64)ctN[0];
+    if (dbg && dbg->ctN) memcpy(dbg->ctN, ctN, sizeof(u64) * (n + 1));
 
     /* sgnP = 1 - sum_{i=2}^{N} X^{i-1}, scaled by Delta/2, times X^{b_N};
      * acc = [that, 0] (l_boot = 1, L_boot^0 = 1). */
@@ -483,9 +484,25 @@ void or_fdfb_bootstrap(const or_params* P, const u64* bsk, const u64* pk, const 
     lwe[0] = (lwe[0] + delta / 2) & m;
     if (dbg && dbg->sgn) memcpy(dbg->sgn, lwe, sizeof(u64) * (N + 1));
 
-    /* BuildAcc: acc_R = KeySwitch(acc_c, pK); PubMux(acc_R, rotP'_1, rotP'_0) */
+    /* BuildAcc, first half: acc_R = KeySwitch(acc_c, pK) */
     or_keyswitch(w, N, P->log2Bpk, P->lpk, 2 * N, pk, lwe, cR);
     if (dbg && dbg->cR) memcpy(dbg->cR, cR, sizeof(u64) * 2 * N);
+
+    free(lwe); free(acc); free(sgnP);
+}
+
+static void or_fdfb_function_part(const or_params* P, const u64* bsk, const u64* ksk,
+                                  const i64* rotP0, const i64* rotP1, const u64* ctN,
+                                  const u64* cR, u64* out, const or_debug* dbg) {
+    const int n = P->n, N = P->N, w = P->w, t = P->t;
+    const i64 bN = (i64)ctN[0];
+
+    u64* acc = (u64*)malloc(sizeof(u64) * 2 * N);
+    u64* lwe = (u64*)malloc(sizeof(u64) * (N + 1));
+    i64* r0 = (i64*)malloc(sizeof(i64) * N);
+    i64* r1 = (i64*)malloc(sizeof(i64) * N);
+
+    /* BuildAcc, second half: PubMux(acc_R, rotP'_1, rotP'_0), rotP'_j = rotP_j X^{b_N} */
     or_poly_mul_xk_signed(N, rotP0, bN, r0);
     or_poly_mul_xk_signed(N, rotP1, bN, r1);
     or_pubmux(w, N, t, cR, r1, r0, acc);
@@ -499,9 +516,34 @@ void or_fdfb_bootstrap(const or_params* P, const u64* bsk, const u64* pk, const 
 
     /* c_Q,ksK = KeySwitch(c_Q, ksK); q = Q so the final ModSwitch is the identity */
     or_keyswitch(w, N, P->log2Bks, P->lks, n + 1, ksk, lwe, out);
-    if (dbg && dbg->ctN) memcpy(dbg->ctN, ctN, sizeof(u64) * (n + 1));
 
-    free(r1); free(r0); free(cR); free(lwe); free(acc); free(sgnP); free(ctN);
+    free(r1); free(r0); free(lwe); free(acc);
+}
+
+/* ct: [n+1]; rotP0, rotP1: signed [N] (SetupPolynomial output); out: [n+1]. */
+void or_fdfb_bootstrap(const or_params* P, const u64* bsk, const u64* pk, const u64* ksk,
+                       const i64* rotP0, const i64* rotP1, const u64* ct, u64* out,
+                       const or_debug* dbg) {
+    const int n = P->n, N = P->N;
+    u64* ctN = (u64*)malloc(sizeof(u64) * (n + 1));
+    u64* cR = (u64*)malloc(sizeof(u64) * 2 * N);
+    or_fdfb_sign_part(P, bsk, pk, ct, ctN, cR, dbg);
+    or_fdfb_function_part(P, bsk, ksk, rotP0, rotP1, ctN, cR, out, dbg);
+    free(cR); free(ctN);
+}
+
+/* k functions of one input: rotP [k][2][N] signed (p0 then p1 per table);
+ * outs [k][n+1]. */
+void or_fdfb_bootstrap_multi(const or_params* P, const u64* bsk, const u64* pk, const u64* ksk,
+                             const i64* rotP, int k, const u64* ct, u64* outs) {
+    const int n = P->n, N = P->N;
+    u64* ctN = (u64*)malloc(sizeof(u64) * (n + 1));
+    u64* cR = (u64*)malloc(sizeof(u64) * 2 * N);
+    or_fdfb_sign_part(P, bsk, pk, ct, ctN, cR, NULL);
+    for (int j = 0; j < k; ++j)
+        or_fdfb_function_part(P, bsk, ksk, rotP + (size_t)j * 2 * N, rotP + (size_t)j * 2 * N + N,
+                              ctN, cR, outs + (size_t)j * (n + 1), NULL);
+    free(cR); free(ctN);
 }
 
 /* A batch of bootstraps, one thread per ciphertext.  rotP: [n_luts][2][N]
@@ -515,6 +557,23 @@ void or_fdfb_batch(const or_params* P, const u64* bsk, const u64* pk, const u64*
         const i64* rp = rotP + (size_t)lut_ids[c] * 2 * N;
         or_fdfb_bootstrap(P, bsk, pk, ksk, rp, rp + N, cts + (size_t)c * (n + 1),
                           outs + (size_t)c * (n + 1), NULL);
+    }
+}
+
+/* The batch with k tables per input: lut_ids [count][k]; outs [count][k][n+1]. */
+void or_fdfb_batch_multi(const or_params* P, const u64* bsk, const u64* pk, const u64* ksk,
+                         const i64* rotP, const int32_t* lut_ids, int k, int64_t count,
+                         const u64* cts, u64* outs) {
+    const int n = P->n, N = P->N;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) if (g_threads > 1)
+    for (int64_t c = 0; c < count; ++c) {
+        i64* sel = (i64*)malloc(sizeof(i64) * (size_t)k * 2 * N);
+        for (int j = 0; j < k; ++j)
+            memcpy(sel + (size_t)j * 2 * N, rotP + (size_t)lut_ids[c * k + j] * 2 * N,
+                   sizeof(i64) * 2 * N);
+        or_fdfb_bootstrap_multi(P, bsk, pk, ksk, sel, k, cts + (size_t)c * (n + 1),
+                                outs + (size_t)c * k * (n + 1));
+        free(sel);
     }
 }
 

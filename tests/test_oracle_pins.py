@@ -396,6 +396,48 @@ def test_fdfb_noiseless_exhaustive(oracle):
         assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
 
 
+def test_fdfb_multi_noiseless_exhaustive(oracle):
+    """Several functions of one input (Section 'Application of Functional
+    Bootstrapping': the sign accumulators are reused): at sigma = 0 with exact
+    decompositions, one call per message m in Z_4 evaluates all 256 functions
+    f: Z_4 -> Z_4, and every output phase is exactly Delta * f(m)."""
+    ps = S.PARAM_SETS["Z"]
+    k = _tiny_keys(oracle, ps, 0)
+    t = ps.t
+    fs = np.array(list(itertools.product(range(t), repeat=t)), dtype=np.int64)
+    rot = np.zeros((len(fs), 2, ps.N), dtype=np.int64)
+    for i, f in enumerate(fs):
+        rot[i, 0], rot[i, 1] = oracle.setup_polynomial(ps.N, t, f)
+    ms = np.arange(t)
+    ids = np.tile(np.arange(len(fs), dtype=np.int32), (t, 1))     # [4][256]
+    mr = S.message_randomness(ps, 1, t, m=ms)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.fdfb_batch_multi(ps, k, rot, ids, cts)
+    assert outs.shape == (t, len(fs), ps.n + 1)
+    for m in range(t):
+        for i in range(len(fs)):
+            want = (ps.delta * int(fs[i, m])) % (1 << ps.w)
+            assert oracle.lwe_phase(ps.w, k.s, outs[m, i]) == want, (m, i)
+
+
+def test_fdfb_multi_equals_single(oracle):
+    """The sign part of the bootstrap does not depend on the table, so the
+    multi-table form returns, for every (input, table), the bits of the
+    single-table bootstrap (set A with noise, 5 inputs x 3 tables)."""
+    ps = S.PARAM_SETS["A"]
+    k = _tiny_keys(oracle, ps, 4)
+    fs = S.lut_tables(ps, 4, 4)
+    rot = np.stack([np.stack(oracle.setup_polynomial(ps.N, ps.t, f)) for f in fs])
+    ids = np.array([[0, 1, 2], [3, 3, 0], [1, 2, 3], [2, 0, 1], [0, 0, 0]], dtype=np.int32)
+    mr = S.message_randomness(ps, 4, len(ids))
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    multi = oracle.fdfb_batch_multi(ps, k, rot, ids, cts)
+    single = oracle.fdfb_batch(ps, k, rot, ids.reshape(-1), np.repeat(cts, ids.shape[1], axis=0))
+    assert np.array_equal(multi.reshape(-1, ps.n + 1), single)
+    one = oracle.fdfb_bootstrap_multi(ps, k, rot[ids[1]], cts[1])
+    assert np.array_equal(one, multi[1])
+
+
 def test_fdfb_toy_decrypts(oracle):
     """Toy workload (set A, seed 0): every output decrypts to f(m)."""
     wl = S.WORKLOADS["toy"]
