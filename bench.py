@@ -163,7 +163,10 @@ def run_reference(args):
     def step(k):
         sl = slice(k * per_step, (k + 1) * per_step)
         for c in range(sl.start, sl.stop):
-            O.fdfb_bootstrap(ps, K, rot[ids[c % g.batch]][0], rot[ids[c % g.batch]][1], cts[c])
+            if g.tables_per_input > 1:
+                O.fdfb_bootstrap_multi(ps, K, rot[ids[c % g.batch]], cts[c])
+            else:
+                O.fdfb_bootstrap(ps, K, rot[ids[c % g.batch]][0], rot[ids[c % g.batch]][1], cts[c])
 
     for k in range(args.warmup):
         step(k)
@@ -171,7 +174,7 @@ def run_reference(args):
     for k in range(args.warmup, args.warmup + args.steps):
         step(k)
     dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+    value = per_step * g.tables_per_input * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -179,7 +182,8 @@ def run_reference(args):
         "data": "synthetic (seeded SplitMix64 keys, messages and tables)",
         "config": config_of(args, wl, g, ps),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} ciphertexts per step of the {args.workload} workload, "
+                         "sample": f"{per_step} ciphertexts per step of the {args.workload} workload "
+                                   f"({g.tables_per_input} table(s) each), "
                                    f"each bootstrapped by the schoolbook oracle with its ring products "
                                    f"spread over {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -191,7 +195,9 @@ def run_reference(args):
 def config_of(args, wl, g, ps):
     return {"workload": f"{wl.name}: FDFB n={ps.n} N={ps.N} q=2^{ps.w} t={ps.t} B_g=2^{ps.log2Bg} "
                         f"l_g={ps.lg} B_ks=2^{ps.log2Bks} l_ks={ps.lks} B_pk=2^{ps.log2Bpk} l_pk={ps.lpk}, "
-                        f"{g.batch} ciphertexts per GPU, {g.n_luts} tables ({g.lut_assign})",
+                        f"{g.batch} ciphertexts per GPU, {g.n_luts} tables ({g.lut_assign})"
+                        + (f", {g.tables_per_input} tables per input sharing one sign rotation"
+                           if g.tables_per_input > 1 else ""),
             "batch_per_gpu": g.batch, "param_set": ps.name, "seed": wl.seed,
             "l2": "flushed before every timed step (512 MB write, not timed)"}
 
@@ -209,16 +215,20 @@ def cpu_baseline(wl, g, ps, seconds_target=20.0):
     cts = O.encrypt_messages(ps, K.s, mr)
     t0 = time.perf_counter()
     done = 0
+    k = g.tables_per_input
     while done < g.batch:
         c = done
-        O.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
+        if k > 1:
+            O.fdfb_bootstrap_multi(ps, K, rot[ids[c]], cts[c])
+        else:
+            O.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
         done += 1
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {done} ciphertexts of the workload, one after another, each bootstrap's "
-                      f"ring products spread over {cores} threads ({dt:.1f} s)"}
+    return {"value": done * k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} ciphertexts of the workload ({k} table(s) each), one after another, "
+                      f"each bootstrap's ring products spread over {cores} threads ({dt:.1f} s)"}
 
 
 class Job:
@@ -236,7 +246,7 @@ class Job:
         else:
             for gi, g in enumerate(wl.groups):
                 self.groups.append(self._prepare_group(gi, g, args, rank))
-            self.units = sum(x["batch"] for x in self.groups)
+            self.units = sum(x["batch"] * x["k"] for x in self.groups)
 
     def _prepare_group(self, gi, g, args, rank):
         torch, F, ctx, dev, wl = self.torch, self.F, self.ctx, self.dev, self.wl
@@ -263,8 +273,14 @@ class Job:
             cur, cnt, cpt = ctx.variant_info(sid)
             self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
                                    "trial_blind_rotation_ms": [round(x, 3) for x in each]}
-        want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
-        return {"sid": sid, "ps": ps, "batch": g.batch, "ct": ct, "ids": ids, "out": torch.empty_like(ct),
+        k = g.tables_per_input
+        if k > 1:
+            want = np.array([[fs[i][m] for i in row] for row, m in zip(ids_np, mr.m)]).reshape(-1)
+            out = torch.empty((g.batch, k, ps.n + 1), dtype=ct.dtype, device=dev)
+        else:
+            want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
+            out = torch.empty_like(ct)
+        return {"sid": sid, "ps": ps, "batch": g.batch, "k": k, "ct": ct, "ids": ids, "out": out,
                 "s": s_d, "want": want}
 
     def _prepare_mlp(self, args, rank):
@@ -288,7 +304,7 @@ class Job:
                                    "trial_blind_rotation_ms": tms}
         self.mlp_x = ct.view(x.shape[0], x.shape[1], ps.n + 1)
         self.mlp_want = mlp.plain_forward(x, Ws, ps.t)
-        self.groups.append({"sid": sid, "ps": ps, "batch": x.size, "ct": ct, "s": s_d})
+        self.groups.append({"sid": sid, "ps": ps, "batch": x.size, "k": 1, "ct": ct, "s": s_d})
         self.units = wl.mlp_inputs * sum(wl.mlp_layers[1:])
         self.mlp_batches = [wl.mlp_inputs * k for k in wl.mlp_layers[1:]]
 
@@ -298,7 +314,10 @@ class Job:
             self.mlp_out = self.net.forward(self.mlp_x)
         elif len(gs) == 1:
             g = gs[0]
-            self.ctx.bootstrap(g["sid"], g["ct"], g["ids"], g["out"])
+            if g["k"] > 1:
+                self.ctx.bootstrap_multi(g["sid"], g["ct"], g["ids"], g["out"])
+            else:
+                self.ctx.bootstrap(g["sid"], g["ct"], g["ids"], g["out"])
         else:
             self.ctx.bootstrap_mixed([(g["sid"], g["ct"], g["ids"], g["out"]) for g in gs])
 
@@ -313,8 +332,8 @@ class Job:
             return float((m.cpu().numpy().reshape(self.mlp_want.shape) == self.mlp_want).mean())
         ok = {}
         for g in self.groups:
-            m = torch.empty(g["batch"], dtype=torch.int32, device=self.dev)
-            ctx.lwe_decrypt(g["sid"], g["s"], g["out"], m)
+            m = torch.empty(g["batch"] * g["k"], dtype=torch.int32, device=self.dev)
+            ctx.lwe_decrypt(g["sid"], g["s"], g["out"].view(-1, g["ps"].n + 1), m)
             ctx.sync()
             ok[g["ps"].name] = float((m.cpu().numpy() == g["want"]).mean())
         return ok if len(ok) > 1 else next(iter(ok.values()))
@@ -323,7 +342,9 @@ class Job:
         if self.wl.mlp_layers:
             ps = self.groups[0]["ps"]
             return 2 * sum(br_algorithmic_slots(ps, b) for b in self.mlp_batches)
-        return 2 * sum(br_algorithmic_slots(g["ps"], g["batch"]) for g in self.groups)
+        # one sign rotation per input, one function rotation per (input, table)
+        return sum(br_algorithmic_slots(g["ps"], g["batch"]) + br_algorithmic_slots(g["ps"], g["batch"] * g["k"])
+                   for g in self.groups)
 
     def io_bytes(self):
         if self.wl.mlp_layers:
@@ -432,9 +453,10 @@ def main():
         e2["ct"] = c
         if i is not None:
             e2["ids"] = i
-        e2["out"] = torch.empty_like(g["ct"]) if "out" in g else None
+        e2["out"] = torch.empty_like(g["out"]) if "out" in g else None
         e2e_groups.append(e2)
-    out_host = [torch.empty(g["ct"].shape, dtype=g["ct"].dtype).pin_memory() for g in job.groups]
+    out_host = [torch.empty((g["out"] if "out" in g else g["ct"]).shape, dtype=g["ct"].dtype).pin_memory()
+                for g in job.groups]
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
@@ -470,7 +492,7 @@ def main():
         ms_total, e2e_ms = slowest_rank([ms_total, e2e_ms], dev)
 
     plain = None
-    if args.plain and rank == 0 and not job.wl.mlp_layers:
+    if args.plain and rank == 0 and not job.wl.mlp_layers and job.groups[0]["k"] == 1:
         reps = 8
         g = job.groups[0]
         one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()

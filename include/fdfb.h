@@ -146,6 +146,21 @@ int fdfb_lut_polys(fdfb_ctx* ctx, int set_id, int lut_id, int32_t* p0, int32_t* 
 int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
                    int64_t batch, void* ct_out, void* cuda_stream);
 
+/* Several functions of one input (Section "Application of Functional
+ * Bootstrapping", multiple univariate functions with the same input: the
+ * accumulators of the first bootstrap are reused for the next function).
+ * The sign rotation, its SampleExtract and the packing key switch run once
+ * per input; PubMux, the function rotation, SampleExtract and the LWE key
+ * switch run once per (input, table):
+ *   ct_in   device, [batch][n+1] words;
+ *   lut_ids device, int32[batch][k], table ids from fdfb_lut_setup;
+ *   ct_out  device, [batch][k][n+1] words; ct_out[b][j] is bit for bit what
+ *           fdfb_bootstrap returns for ct_in[b] with table lut_ids[b][j].
+ * k >= 1 and batch * k < 2^31, else FDFB_EINVAL.  Scratch grows as for
+ * fdfb_bootstrap (for batch inputs and batch * k outputs). */
+int fdfb_bootstrap_multi(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                         int64_t batch, int k, void* ct_out, void* cuda_stream);
+
 /* Intermediates of fdfb_bootstrap for checking (device pointers, each may
  * be NULL; [batch] x ...):
  *   ctN  uint32 [n+1]  ModSwitch(ct, q, 2N)

@@ -83,7 +83,6 @@ struct SetState {
   DevBuf luts;
   int n_luts = 0;
   DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
-  int64_t scratch_batch = 0;
   size_t wbytes() const { return (size_t)w / 8; }
   Variant& base() { return *var[0]; }
   Variant& br() { return *var[cur]; }
@@ -190,12 +189,16 @@ int install_bsk_ntt(SetState& st, cudaStream_t s) {
   return FDFB_OK;
 }
 
-int ensure_scratch(SetState& st, int64_t batch) {
-  if (batch <= st.scratch_batch) return FDFB_OK;
+// Pipeline intermediates for `batch` inputs with k tables each: per input the
+// sign LWE [N+1] and the packed RLWE [2N], per (input, table) the function
+// accumulator [2N] and the extracted LWE [N+1].
+size_t scratch_bytes(const SetState& st, int64_t batch, int k) {
   const size_t N = st.prm.N;
-  const size_t per = ((N + 1) + 2 * N + 2 * N + (N + 1)) * st.wbytes();
-  FD_TRY(st.scratch.ensure(per * (size_t)batch + 256));
-  st.scratch_batch = batch;
+  return ((size_t)batch * ((N + 1) + 2 * N) + (size_t)batch * k * (2 * N + (N + 1))) * st.wbytes();
+}
+
+int ensure_scratch(SetState& st, int64_t batch, int k = 1) {
+  FD_TRY(st.scratch.ensure(scratch_bytes(st, batch, k) + 256));
   return FDFB_OK;
 }
 
@@ -221,19 +224,25 @@ struct StageTimer {
 };
 
 // One bootstrap pipeline on one parameter set (figure "functional-
-// bootstrapping", left), steps 1-14.
+// bootstrapping", left), steps 1-14, for `batch` inputs and k tables per
+// input: steps 1-10 (sign rotation, packing key switch) once per input, steps
+// 11-14 (PubMux, function rotation, key switch) once per (input, table) --
+// the reuse of the sign accumulators for further functions of one input
+// (Section "Application of Functional Bootstrapping", multiple univariate
+// functions with the same input).  lut_ids and ct_out are [batch][k].
 int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
-                 int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
+                 int64_t batch, int k, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
                  void* fixed_scratch = nullptr) {
-  if (batch < 0) return FDFB_EINVAL;
+  if (batch < 0 || k < 1) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
   if (!st.keys) return FDFB_ENOKEYS;
   if (st.n_luts == 0) return FDFB_EBADLUT;
-  if (batch > 0x7fffffff) return FDFB_EINVAL;
+  if (batch * (int64_t)k > 0x7fffffff) return FDFB_EINVAL;
   const fdfb_params& P = st.prm;
   const size_t N = P.N, wb = st.wbytes();
-  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch));
+  const int64_t items = batch * k;
+  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, k));
   unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
   // The measurement hook creates CUDA events; the fixed-scratch path stays
   // free of any runtime object creation.
@@ -241,7 +250,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   void* sgn = base;
   void* cR = base + (size_t)batch * (N + 1) * wb;
   void* accF = (unsigned char*)cR + (size_t)batch * 2 * N * wb;
-  void* cQ = (unsigned char*)accF + (size_t)batch * 2 * N * wb;
+  void* cQ = (unsigned char*)accF + (size_t)items * 2 * N * wb;
   if (dbg) {
     if (dbg->sgn) sgn = dbg->sgn;
     if (dbg->cR) cR = dbg->cR;
@@ -268,6 +277,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.sign_mode = 1;
   br.smem_r1 = bv.br_r1;
   br.smem_exch = bv.br_ex;
+  br.rep = 1;
   {
     StageTimer tm(tctx, 0, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -292,6 +302,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   pm.S = st.base().S;
   pm.cR = cR;
   pm.ct = ct_in;
+  pm.rep = k;
   pm.lut_ids = lut_ids;
   pm.luts = (const int16_t*)st.luts.p;
   pm.n_luts = st.n_luts;
@@ -302,7 +313,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   pm.err = ctx->d_err;
   {
     StageTimer tm(tctx, 2, s);
-    FD_CUDA(st.base().ops->pubmux(pm, batch, s));
+    FD_CUDA(st.base().ops->pubmux(pm, items, s));
   }
 
   // Steps 12-13: function BlindRotate, SampleExtract.
@@ -310,23 +321,25 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.lwe_out = cQ;
   br.ctN_out = nullptr;
   br.sign_mode = 0;
+  br.batch = items;
+  br.rep = k;
   {
     StageTimer tm(tctx, 3, s);
-    FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
+    FD_CUDA(bv.ops->br(br, items, bv.br_smem, s));
   }
 
   // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q).
   {
-    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
+    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((items + KS_BM - 1) / KS_BM));
     const int rt = trunc_bits(st.w, P.log2Bks, P.lks);
     StageTimer tm(tctx, 4, s);
     if (st.w == 32)
       keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint32_t*)cQ, batch, (int)N, (const uint32_t*)st.ksk.p, P.lks, P.log2Bks, rt,
+          (const uint32_t*)cQ, items, (int)N, (const uint32_t*)st.ksk.p, P.lks, P.log2Bks, rt,
           (int)P.n + 1, (uint32_t*)ct_out);
     else
       keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint64_t*)cQ, batch, (int)N, (const uint64_t*)st.ksk.p, P.lks, P.log2Bks, rt,
+          (const uint64_t*)cQ, items, (int)N, (const uint64_t*)st.ksk.p, P.lks, P.log2Bks, rt,
           (int)P.n + 1, (uint64_t*)ct_out);
     FD_CUDA(cudaGetLastError());
   }
@@ -669,15 +682,21 @@ int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* 
   SetState* st = get_set(ctx, set_id);
   if (!st) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, nullptr, as_stream(cuda_stream));
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, nullptr, as_stream(cuda_stream));
+}
+
+int fdfb_bootstrap_multi(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
+                         int64_t batch, int k, void* ct_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  DeviceGuard g(ctx->device);
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, k, ct_out, nullptr, as_stream(cuda_stream));
 }
 
 int fdfb_noalloc_max_batch(fdfb_ctx* ctx, int set_id, int64_t* max_batch) {
   SetState* st = get_set(ctx, set_id);
   if (!st || !max_batch) return FDFB_EINVAL;
-  const size_t N = st->prm.N;
-  const size_t per = ((N + 1) + 2 * N + 2 * N + (N + 1)) * st->wbytes();
-  *max_batch = (int64_t)(kNoAllocScratchBytes / per);
+  *max_batch = (int64_t)(kNoAllocScratchBytes / scratch_bytes(*st, 1, 1));
   return FDFB_OK;
 }
 
@@ -691,7 +710,7 @@ int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const i
   DeviceGuard g(ctx->device);
   void* scratch = nullptr;
   FD_TRY(noalloc_scratch(ctx->device, &scratch));
-  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, nullptr, as_stream(cuda_stream),
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, nullptr, as_stream(cuda_stream),
                       scratch);
 }
 
@@ -700,7 +719,7 @@ int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
   SetState* st = get_set(ctx, set_id);
   if (!st || !dbg) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, ct_out, dbg, as_stream(cuda_stream));
+  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, dbg, as_stream(cuda_stream));
 }
 
 int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, void* cuda_stream) {
@@ -730,7 +749,7 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
   if (sets.size() == 1) {
     for (int i = 0; i < n_groups; ++i)
       FD_TRY(run_pipeline(ctx, *get_set(ctx, groups[i].set_id), groups[i].ct_in, groups[i].lut_ids,
-                          groups[i].batch, groups[i].ct_out, nullptr, s));
+                          groups[i].batch, 1, groups[i].ct_out, nullptr, s));
     return FDFB_OK;
   }
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -749,7 +768,7 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
   int rc = FDFB_OK;
   for (int i = 0; i < n_groups && rc == FDFB_OK; ++i)
     rc = run_pipeline(ctx, *get_set(ctx, groups[i].set_id), groups[i].ct_in, groups[i].lut_ids,
-                      groups[i].batch, groups[i].ct_out, nullptr, ctx->side[lane[i]]);
+                      groups[i].batch, 1, groups[i].ct_out, nullptr, ctx->side[lane[i]]);
   // Join even after an error, so the caller's stream never runs ahead of
   // work already queued on the side streams.
   for (size_t k = 0; k < sets.size(); ++k) {
@@ -891,6 +910,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.sign_mode = 1;
     br.smem_r1 = v.br_r1;
     br.smem_exch = v.br_ex;
+    br.rep = 1;
     float ms_v = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, s);

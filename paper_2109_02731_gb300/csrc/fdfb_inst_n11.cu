@@ -17,11 +17,14 @@ const Ops* ops_n11(int w, int variant) {
   static const Ops b2 = Inst<11, 4, 3, uint64_t, uint16_t, true>::ops();
   static const Ops b3 = Inst<11, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (11 - 4)), 2>::ops();
   static const Ops b4 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2>::ops();
+  // b3 and b4 with ping-pong exchange buffers
+  static const Ops b5 = Inst<11, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (11 - 4)), 2, false, true>::ops();
+  static const Ops b6 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, true>::ops();
   static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4};
+  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4, &b5, &b6};
   if (variant < 0) return nullptr;
   if (w == 32) return variant < 6 ? v32[variant] : nullptr;
-  if (w == 64) return variant < 5 ? v64[variant] : nullptr;
+  if (w == 64) return variant < 7 ? v64[variant] : nullptr;
   return nullptr;
 }
 }  // namespace fdfb

@@ -185,7 +185,7 @@ __device__ __forceinline__ uint32_t modswitch_2n(W x) {
 struct BRParams {
   PrimeSet S;
   const uint32_t* bsk;    // [n][P][2 lg][2][N]
-  const void* ct;         // [batch][n+1] words (input LWE, modulus q)
+  const void* ct;         // [batch / rep][n+1] words (input LWE, modulus q)
   const void* acc0;       // function mode: [batch][2N] words; sign mode: nullptr
   void* lwe_out;          // [batch][N+1] words: SampleExtract(acc, 0) (+ Delta/2 in sign mode)
   uint32_t* ctN_out;      // optional [batch][n+1]: ModSwitch(ct, q, 2N)
@@ -194,6 +194,7 @@ struct BRParams {
   uint64_t delta_half;
   int sign_mode;
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
+  int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
 };
 
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false>
@@ -274,7 +275,7 @@ blind_rotate_kernel(const BRParams prm) {
   const int t = tid - grp * G;
   const int64_t ci = blockIdx.x;
   const int n = prm.n, lg = prm.lg, log2Bg = prm.log2Bg;
-  const W* ct = reinterpret_cast<const W*>(prm.ct) + ci * (n + 1);
+  const W* ct = reinterpret_cast<const W*>(prm.ct) + (ci / prm.rep) * (n + 1);
 
   // ModSwitch of the mask; b_N for the sign accumulator.
   for (int i = tid; i < n; i += THREADS) {
@@ -527,8 +528,9 @@ constexpr size_t product_smem_bytes() {
 // with (p0, p1) = (rotP'_1, rotP'_0), rotP'_j = rotP_j X^{b_N}.
 struct PubMuxParams {
   PrimeSet S;
-  const void* cR;          // [batch][2N]
-  const void* ct;          // [batch][n+1] input LWE (for b_N)
+  const void* cR;          // [batch / rep][2N]
+  const void* ct;          // [batch / rep][n+1] input LWE (for b_N)
+  int rep;                 // tables per input: item i reads cR and ct of input i / rep
   const int32_t* lut_ids;  // [batch]
   const int16_t* luts;     // [n_luts][2][N]  (rotP_0, rotP_1)
   int n_luts;
@@ -543,7 +545,8 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_kernel(const PubMu
   constexpr int N = 1 << L;
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t ci = blockIdx.x;
-  const W* ct = reinterpret_cast<const W*>(prm.ct) + ci * (prm.n + 1);
+  const int64_t src = ci / prm.rep;
+  const W* ct = reinterpret_cast<const W*>(prm.ct) + src * (prm.n + 1);
   const int bN = (int)modswitch_2n<W, L>(ct[0]);
   int lut = prm.lut_ids[ci];
   if (lut < 0 || lut >= prm.n_luts) {
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_kernel(const PubMu
     int v = poly[m];
     return neg ? -v : v;
   };
-  const W* cR = reinterpret_cast<const W*>(prm.cR) + ci * 2 * N;
+  const W* cR = reinterpret_cast<const W*>(prm.cR) + src * 2 * N;
   W* out = reinterpret_cast<W*>(prm.accF) + ci * 2 * N;
   const W delta = (W)prm.delta;
   small_word_product<L, EL, P, W>(

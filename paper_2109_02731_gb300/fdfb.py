@@ -25,7 +25,7 @@ SYMBOLS = [
     "fdfb_create", "fdfb_destroy", "fdfb_params_register", "fdfb_key_words", "fdfb_keys_upload",
     "fdfb_keys_generate", "fdfb_keys_download", "fdfb_lut_setup", "fdfb_lut_polys",
     "fdfb_bootstrap", "fdfb_bootstrap_debug", "fdfb_bootstrap_mixed", "fdfb_keyswitch",
-    "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch",
+    "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch", "fdfb_bootstrap_multi",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
     "fdfb_set_variant", "fdfb_variant_info", "fdfb_profile_enable",
     "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
@@ -90,6 +90,7 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_bootstrap_mixed": ([vp, i32, C.POINTER(fdfb_group), vp], i32),
                 "fdfb_bootstrap_noalloc": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_noalloc_max_batch": ([vp, i32, C.POINTER(i64)], i32),
+                "fdfb_bootstrap_multi": ([vp, i32, vp, vp, i64, i32, vp, vp], i32),
                 "fdfb_keyswitch": ([vp, i32, vp, i64, vp, vp], i32),
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_decrypt": ([vp, i32, vp, vp, i64, vp, vp], i32),
@@ -254,6 +255,13 @@ class Context:
         b = int(ct_in.shape[0]) if batch is None else batch
         _check(self.L.fdfb_bootstrap(self.h, set_id, _ptr(ct_in), _ptr(lut_ids), b, _ptr(ct_out),
                                      _stream(stream)), "fdfb_bootstrap")
+
+    def bootstrap_multi(self, set_id: int, ct_in, lut_ids, ct_out, stream=None):
+        """k tables per input: ct_in [batch][n+1], lut_ids int32 [batch][k] and
+        ct_out [batch][k][n+1], all on the device."""
+        b, k = int(lut_ids.shape[0]), int(lut_ids.shape[1])
+        _check(self.L.fdfb_bootstrap_multi(self.h, set_id, _ptr(ct_in), _ptr(lut_ids), b, k,
+                                           _ptr(ct_out), _stream(stream)), "fdfb_bootstrap_multi")
 
     def bootstrap_noalloc(self, set_id: int, ct_in, lut_ids, ct_out, stream=None):
         """fdfb_bootstrap on the library's fixed scratch: allocates nothing."""

@@ -92,7 +92,8 @@ class Group:
     set_name: str
     batch: int
     n_luts: int
-    lut_assign: str   # "round_robin" or "uniform"
+    lut_assign: str   # "round_robin", "uniform", or "all" (every input, every table)
+    tables_per_input: int = 1
 
 
 @dataclasses.dataclass(frozen=True)
@@ -114,6 +115,9 @@ WORKLOADS: Dict[str, Workload] = {
                                    Group("C", 2900, 4, "uniform")]),
     # the N = 2048 group of the mixed workload on its own
     "n2048": Workload("n2048", 3, [Group("D", 1000, 4, "uniform")]),
+    # the TFHE-scale inputs, each evaluated under all four tables with one
+    # shared sign rotation (several functions of one input)
+    "multi_lut": Workload("multi_lut", 1, [Group("B", 1024, 4, "all", tables_per_input=4)]),
     "mlp": Workload("mlp", 4, [Group("D", 0, 2, "uniform")],
                     mlp_layers=[784, 128, 64, 10], mlp_inputs=64),
 }
@@ -272,8 +276,12 @@ def lut_tables(ps: ParamSet, seed: int, count: int, group: int = 0) -> np.ndarra
 
 
 def lut_assignment(seed: int, count: int, n_luts: int, how: str, group: int = 0) -> np.ndarray:
+    """Table ids: [count], or [count][n_luts] for "all" (input c gets the
+    tables in the order c, c+1, ... mod n_luts)."""
     if how == "round_robin":
         return (np.arange(count) % n_luts).astype(np.int32)
+    if how == "all":
+        return ((np.arange(count)[:, None] + np.arange(n_luts)[None, :]) % n_luts).astype(np.int32)
     st = Stream(seed, STREAM_LUT_ASSIGN, group)
     return st.below(count, n_luts).astype(np.int32)
 

@@ -446,6 +446,84 @@ def test_mlp_workload_full_size_decrypts(F, torch_cuda, ctx, oracle):
     assert np.array_equal(got, mlp.plain_forward(x, Ws, ps.t))
 
 
+# ------------------------------------------------------------ multi-table --
+
+def run_gpu_multi(F, torch, ctx, sid, ps, cts, ids2):
+    ct_d = F.to_device_words(ps, cts)
+    ids_d = torch.tensor(np.ascontiguousarray(ids2, dtype=np.int32), device="cuda")
+    out_d = torch.empty((len(cts), ids2.shape[1], ps.n + 1), dtype=ct_d.dtype, device="cuda")
+    ctx.bootstrap_multi(sid, ct_d, ids_d, out_d)
+    ctx.sync()
+    return F.to_host_words(ps, out_d).astype(np.uint64)
+
+
+def test_multi_table_toy_matches_oracle(F, torch_cuda, ctx, oracle):
+    """Several tables per input (one sign rotation shared by k function
+    rotations): every (input, table) output equals the oracle's multi-table
+    bootstrap bit for bit (set A, 13 inputs x 3 tables)."""
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 0)
+    sid = install(ctx, oracle, "A", 0, 4)
+    fs, rot = luts("A", 0, 4)
+    rng = np.random.default_rng(5)
+    ids = rng.integers(0, 4, size=(13, 3)).astype(np.int32)
+    mr, cts = fresh_cts("A", 0, 13, K, group=7)
+    got = run_gpu_multi(F, torch_cuda, ctx, sid, ps, cts, ids)
+    want = oracle.fdfb_batch_multi(ps, K, rot, ids, cts)
+    assert np.array_equal(got, want)
+    dec = [[oracle.lwe_decrypt(ps.w, ps.t, K.s, o) for o in row] for row in got]
+    assert dec == [[int(fs[i][m]) for i in row] for row, m in zip(ids, mr.m)]
+
+
+def test_multi_table_tfhe_scale(F, torch_cuda, ctx, oracle):
+    """Set B, 256 inputs x 4 tables in one call, in the autotuned layout:
+    every output equals the single-table bootstrap of its (input, table) on
+    the GPU, and sampled inputs equal the oracle's multi-table bootstrap."""
+    wl = S.WORKLOADS["tfhe_scale"]
+    g = wl.groups[0]
+    ps = S.PARAM_SETS[g.set_name]
+    K = oracle_keys(g.set_name, wl.seed)
+    sid = install(ctx, oracle, g.set_name, wl.seed, g.n_luts)
+    fs, rot = luts(g.set_name, wl.seed, g.n_luts)
+    ids = np.tile(np.arange(4, dtype=np.int32), (256, 1))
+    ids[1::2] = ids[1::2, ::-1]
+    mr, cts = fresh_cts(g.set_name, wl.seed, 256, K, group=3)
+    ctx.autotune(sid, 1024)
+    got = run_gpu_multi(F, torch_cuda, ctx, sid, ps, cts, ids)
+    single, _ = run_gpu(F, torch_cuda, ctx, sid, ps, np.repeat(cts, 4, axis=0), ids.reshape(-1),
+                        debug=False)
+    assert np.array_equal(got.reshape(-1, ps.n + 1), single)
+    for c in (0, 1, 255):
+        assert np.array_equal(got[c], oracle.fdfb_bootstrap_multi(ps, K, rot[ids[c]], cts[c])), c
+
+
+def test_multi_table_edge_cases(F, torch_cuda, ctx, oracle):
+    """k = 1 is the single-table bootstrap; batch 0 is a no-op; k = 0 and a
+    table id out of range are rejected."""
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 0)
+    sid = install(ctx, oracle, "A", 0, 4)
+    mr, cts = fresh_cts("A", 0, 5, K, group=8)
+    ids = np.array([[0], [1], [2], [3], [0]], dtype=np.int32)
+    got = run_gpu_multi(F, torch_cuda, ctx, sid, ps, cts, ids)
+    single, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids[:, 0], debug=False)
+    assert np.array_equal(got[:, 0], single)
+    ct_d = F.to_device_words(ps, cts)
+    empty_ids = torch_cuda.empty((0, 2), dtype=torch_cuda.int32, device="cuda")
+    empty_out = torch_cuda.empty((0, 2, ps.n + 1), dtype=ct_d.dtype, device="cuda")
+    ctx.bootstrap_multi(sid, ct_d[:0], empty_ids, empty_out)
+    zero_k = torch_cuda.empty((5, 0), dtype=torch_cuda.int32, device="cuda")
+    with pytest.raises(F.FDFBError) as e:
+        ctx.bootstrap_multi(sid, ct_d, zero_k, empty_out)
+    assert e.value.code == -1
+    bad = torch_cuda.tensor([[0, 9]] * 5, dtype=torch_cuda.int32, device="cuda")
+    out_d = torch_cuda.empty((5, 2, ps.n + 1), dtype=ct_d.dtype, device="cuda")
+    ctx.bootstrap_multi(sid, ct_d, bad, out_d)
+    with pytest.raises(F.FDFBError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+
+
 # ---------------------------------------------------- layout variants -----
 
 @pytest.mark.parametrize("name,seed,nl,batch", [("A", 0, 2, 50), ("B", 1, 4, 70), ("D", 3, 4, 40),
