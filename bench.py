@@ -272,7 +272,8 @@ class Job:
             v, tms, each = ctx.autotune(sid, g.batch, each=True)
             cur, cnt, cpt = ctx.variant_info(sid)
             self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
-                                   "trial_blind_rotation_ms": [round(x, 3) for x in each]}
+                                   "trial_blind_rotation_ms": [round(x, 3) for x in each],
+                                   "chunks": ctx.get_chunks(sid)}
         k = g.tables_per_input
         if k > 1:
             want = np.array([[fs[i][m] for i in row] for row, m in zip(ids_np, mr.m)]).reshape(-1)
@@ -356,9 +357,16 @@ class Job:
         return h2d, d2h
 
     def launches_per_step(self):
+        """Kernel launches of one step: 5 per pipeline (sign rotation, packing
+        key switch, PubMux, function rotation, LWE key switch), one pipeline per
+        chunk of a single-set call; plus one affine launch per MLP layer."""
+        def pipelines(g, batch):
+            c = self.ctx.get_chunks(g["sid"])
+            return c if (len(self.groups) == 1 and batch >= 2 * c) else 1
         if self.wl.mlp_layers:
-            return 6 * (len(self.wl.mlp_layers) - 1)
-        return 5 * len(self.groups)
+            g = self.groups[0]
+            return sum(1 + 5 * pipelines(g, b) for b in self.mlp_batches)
+        return sum(5 * pipelines(g, g["batch"]) for g in self.groups)
 
 
 def config_for(job, args):
@@ -514,12 +522,15 @@ def main():
 
     units = job.units * args.steps * world
     value = units / (ms_total / 1e3)
-    br_ms = prof["blind_rotate_sign"][0] + prof["blind_rotate_func"][0]
+    # wall time with at least one blind-rotation launch in flight (the
+    # launches of the chunks of one call overlap on different streams)
+    br_ms = prof["blind_rotate_union"][0]
     br_n = prof["blind_rotate_sign"][1] + prof["blind_rotate_func"][1]
     slots = job.slots_per_step() * args.steps
     peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T slots/s
     achieved = slots / (br_ms / 1e3) / 1e12
-    stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4) for k, v in prof.items()}
+    stages = {k: v for k, v in prof.items() if k != "blind_rotate_union"}
+    stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
     h2d, d2h = job.io_bytes()
     ps0 = job.groups[0]["ps"]
     line = {
@@ -533,7 +544,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
                      "unit": "T IMAD slots/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
-                     "launch_ms": br_ms / max(1, br_n), "launches": br_n,
+                     "br_ms_per_step": br_ms / args.steps, "launches": br_n,
                      "slots_per_step": job.slots_per_step()},
         "stage_share": stage_share,
         "autotune": job.tuned,

@@ -256,21 +256,39 @@ int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n
  * keys and keeps the fastest for the parameter set (*variant_out, its time
  * in *ms_out, and the time of variant i in ms_each[i] for i < ms_each_len;
  * any of them may be NULL).  Results never depend on the variant:
- * every variant computes the same exact products.  Needs keys (FDFB_ENOKEYS),
- * may grow the set's scratch, and synchronises the stream.
+ * every variant computes the same exact products.  It then chooses the
+ * set's chunk count (fdfb_set_chunks) by timing whole bootstrap calls.  Needs
+ * keys (FDFB_ENOKEYS), may grow the set's scratch, creates the chunk side
+ * streams, and synchronises the stream.
  * fdfb_set_variant selects a variant by index; fdfb_variant_info reports the
  * current index, the number of variants and the current coefficients per
  * thread (any output pointer may be NULL). */
 int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
                   double* ms_out, double* ms_each, int ms_each_len);
 int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant);
+
+/* How many consecutive slices fdfb_bootstrap and fdfb_bootstrap_multi split
+ * a batch into, each slice's pipeline on a library side stream forked from
+ * and joined back to the caller's stream (the paper has no counterpart: the
+ * launches of the slices overlap on the GPU, filling the last partial wave of
+ * one blind-rotation launch with the next).  Results do not depend on it.
+ * 1 to 4; 1 (one pipeline on the caller's stream) until fdfb_autotune times
+ * the whole pipeline with 1-4 slices for batches below 8 waves of the blind
+ * rotation.  A call with more than one slice creates the side streams on
+ * first use; make it outside any stream capture.  The debug, no-allocation
+ * and mixed entry points always run one pipeline per group. */
+int fdfb_set_chunks(fdfb_ctx* ctx, int set_id, int chunks);
+int fdfb_get_chunks(fdfb_ctx* ctx, int set_id, int* chunks);
 int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* coeffs_per_thread);
 
 /* Measurement hook; the paper has no counterpart.  While enabled, every
  * launch of the bootstrap pipeline is bracketed by a CUDA event pair recorded
  * on the caller's stream, and the device time is accumulated per stage:
  *   0 sign blind rotation, 1 packing key switch, 2 PubMux,
- *   3 function blind rotation, 4 LWE key switch.
+ *   3 function blind rotation, 4 LWE key switch,
+ *   5 all blind rotations: the length of the union of the intervals of the
+ *     stage 0 and 3 launches (launches of the chunks of one call, on
+ *     different streams, overlap; stages 0-4 add their durations up).
  * fdfb_profile_read synchronises on the recorded events and returns the
  * accumulated milliseconds and launch count of `stage` since the last
  * enable.  Disabled by default. */

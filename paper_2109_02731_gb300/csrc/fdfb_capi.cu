@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -83,6 +84,7 @@ struct SetState {
   DevBuf luts;
   int n_luts = 0;
   DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
+  int chunks = 1;  // pieces fdfb_bootstrap splits a large batch into (set by fdfb_autotune)
   size_t wbytes() const { return (size_t)w / 8; }
   Variant& base() { return *var[0]; }
   Variant& br() { return *var[cur]; }
@@ -90,7 +92,7 @@ struct SetState {
 
 }  // namespace
 
-constexpr int kStages = 5;
+constexpr int kStages = 6;  // 5: union of all blind-rotation launches (computed when read)
 
 struct fdfb_ctx {
   int device = 0;
@@ -101,11 +103,14 @@ struct fdfb_ctx {
   bool prof = false;
   struct Mark { int stage; cudaEvent_t a, b; };
   std::vector<Mark> marks;
-  double prof_ms[kStages] = {0, 0, 0, 0, 0};
-  int64_t prof_n[kStages] = {0, 0, 0, 0, 0};
+  double prof_ms[kStages] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_n[kStages] = {0, 0, 0, 0, 0, 0};
   // side streams and fork/join events of fdfb_bootstrap_mixed
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> events;
+  // side streams and fork/join events of the chunked single-set pipeline
+  std::vector<cudaStream_t> chunk_side;
+  std::vector<cudaEvent_t> chunk_events;
 };
 
 namespace {
@@ -232,7 +237,7 @@ struct StageTimer {
 // functions with the same input).  lut_ids and ct_out are [batch][k].
 int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
                  int64_t batch, int k, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
-                 void* fixed_scratch = nullptr) {
+                 void* fixed_scratch = nullptr, bool timed = true) {
   if (batch < 0 || k < 1) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
@@ -244,9 +249,9 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   const int64_t items = batch * k;
   if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, k));
   unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
-  // The measurement hook creates CUDA events; the fixed-scratch path stays
+  // The measurement hook creates CUDA events; the no-allocation path stays
   // free of any runtime object creation.
-  fdfb_ctx* tctx = fixed_scratch ? nullptr : ctx;
+  fdfb_ctx* tctx = timed ? ctx : nullptr;
   void* sgn = base;
   void* cR = base + (size_t)batch * (N + 1) * wb;
   void* accF = (unsigned char*)cR + (size_t)batch * 2 * N * wb;
@@ -346,6 +351,60 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   return FDFB_OK;
 }
 
+constexpr int kMaxChunks = 4;
+
+// Library side streams (and count + 1 fork/join events) for chunked calls.
+int ensure_chunk_streams(fdfb_ctx* ctx, int count) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  while ((int)ctx->chunk_side.size() < count) {
+    cudaStream_t ns;
+    FD_CUDA(cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+    ctx->chunk_side.push_back(ns);
+  }
+  while ((int)ctx->chunk_events.size() < count + 1) {
+    cudaEvent_t e;
+    FD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->chunk_events.push_back(e);
+  }
+  return FDFB_OK;
+}
+
+// The pipeline on `chunks` consecutive slices of the inputs, each on its own
+// library side stream forked from and joined back to s, each slice on its
+// own part of the set's scratch.  The launches of different slices overlap on
+// the GPU, so the last wave of one blind-rotation launch shares the SMs with
+// the next launch instead of leaving them idle.  Results are those of one
+// pipeline over the whole batch (every ciphertext is independent).
+int run_chunked(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
+                int64_t batch, int k, void* ct_out, cudaStream_t s, int chunks) {
+  if (chunks <= 1 || batch < 2 * (int64_t)chunks)
+    return run_pipeline(ctx, st, ct_in, lut_ids, batch, k, ct_out, nullptr, s);
+  if (k < 1 || !ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
+  if (!st.keys) return FDFB_ENOKEYS;
+  if (st.n_luts == 0) return FDFB_EBADLUT;
+  if (batch * (int64_t)k > 0x7fffffff) return FDFB_EINVAL;
+  FD_TRY(ensure_scratch(st, batch, k));
+  FD_TRY(ensure_chunk_streams(ctx, chunks));
+  const size_t wb = st.wbytes(), row = (size_t)(st.prm.n + 1) * wb;
+  unsigned char* base = (unsigned char*)st.scratch.p;
+  FD_CUDA(cudaEventRecord(ctx->chunk_events[0], s));
+  for (int c = 0; c < chunks; ++c) FD_CUDA(cudaStreamWaitEvent(ctx->chunk_side[c], ctx->chunk_events[0], 0));
+  int rc = FDFB_OK;
+  for (int c = 0; c < chunks && rc == FDFB_OK; ++c) {
+    const int64_t b0 = batch * c / chunks, b1 = batch * (c + 1) / chunks;
+    rc = run_pipeline(ctx, st, (const unsigned char*)ct_in + b0 * row, lut_ids + b0 * k, b1 - b0, k,
+                      (unsigned char*)ct_out + b0 * k * row, nullptr, ctx->chunk_side[c],
+                      base + scratch_bytes(st, b0, k));
+  }
+  // Join even after an error, so the caller's stream never runs ahead of
+  // work already queued on the side streams.
+  for (int c = 0; c < chunks; ++c) {
+    FD_CUDA(cudaEventRecord(ctx->chunk_events[1 + c], ctx->chunk_side[c]));
+    FD_CUDA(cudaStreamWaitEvent(s, ctx->chunk_events[1 + c], 0));
+  }
+  return rc;
+}
+
 // Scratch of fdfb_bootstrap_noalloc: a file-scope device array, so that the
 // entry point itself never allocates.  Every GPU that loads the library
 // holds it until the process exits.
@@ -420,6 +479,11 @@ int fdfb_destroy(fdfb_ctx* ctx) {
       cudaStreamDestroy(st);
     }
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    for (cudaStream_t st : ctx->chunk_side) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
     ctx->sets.clear();
     if (ctx->d_err) cudaFree(ctx->d_err);
   }
@@ -682,7 +746,7 @@ int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* 
   SetState* st = get_set(ctx, set_id);
   if (!st) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, nullptr, as_stream(cuda_stream));
+  return run_chunked(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, as_stream(cuda_stream), st->chunks);
 }
 
 int fdfb_bootstrap_multi(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
@@ -690,7 +754,7 @@ int fdfb_bootstrap_multi(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
   SetState* st = get_set(ctx, set_id);
   if (!st) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  return run_pipeline(ctx, *st, ct_in, lut_ids, batch, k, ct_out, nullptr, as_stream(cuda_stream));
+  return run_chunked(ctx, *st, ct_in, lut_ids, batch, k, ct_out, as_stream(cuda_stream), st->chunks);
 }
 
 int fdfb_noalloc_max_batch(fdfb_ctx* ctx, int set_id, int64_t* max_batch) {
@@ -711,7 +775,7 @@ int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const i
   void* scratch = nullptr;
   FD_TRY(noalloc_scratch(ctx->device, &scratch));
   return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, nullptr, as_stream(cuda_stream),
-                      scratch);
+                      scratch, false);
 }
 
 int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
@@ -875,6 +939,58 @@ int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant) {
   return FDFB_OK;
 }
 
+// Chooses how many chunks fdfb_bootstrap splits a batch of `batch` into: the
+// whole pipeline on zero trial ciphertexts (table 0) is timed with 1 to
+// kMaxChunks chunks.  Only batches below 8 waves of the blind rotation are
+// tried (beyond that the last partial wave costs little) and only when a
+// table is installed; otherwise one chunk.
+int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
+  int dev_sms = 0;
+  FD_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int per_sm = st.br().ops->br_blocks_per_sm(st.br().br_smem);
+  const int64_t slots = (int64_t)dev_sms * (per_sm > 0 ? per_sm : 1);
+  int best = 1;
+  if (st.n_luts > 0 && batch >= 2 && batch < 8 * slots) {
+    const size_t row = (size_t)(st.prm.n + 1) * st.wbytes();
+    DevBuf in, out, ids;
+    FD_TRY(in.ensure(batch * row));
+    FD_TRY(out.ensure(batch * row));
+    FD_TRY(ids.ensure(batch * sizeof(int32_t)));
+    FD_CUDA(cudaMemsetAsync(in.p, 0, batch * row, s));
+    FD_CUDA(cudaMemsetAsync(ids.p, 0, batch * sizeof(int32_t), s));
+    FD_TRY(ensure_scratch(st, batch, 1));
+    FD_TRY(ensure_chunk_streams(ctx, kMaxChunks));
+    cudaEvent_t a, b;
+    FD_CUDA(cudaEventCreate(&a));
+    FD_CUDA(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    int rc = FDFB_OK;
+    for (int c = 1; c <= kMaxChunks && rc == FDFB_OK; ++c) {
+      float ms_c = 1e30f;
+      for (int rep = 0; rep < 2 && rc == FDFB_OK; ++rep) {
+        cudaEventRecord(a, s);
+        rc = run_chunked(ctx, st, in.p, (const int32_t*)ids.p, batch, 1, out.p, s, c);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = cuda_err(cudaGetLastError());
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < ms_c) ms_c = ms;  // the first run warms caches
+      }
+      if (ms_c < best_ms) {
+        best_ms = ms_c;
+        best = c;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    FD_CUDA(cudaStreamSynchronize(s));
+    if (rc != FDFB_OK) return rc;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  st.chunks = best;
+  return FDFB_OK;
+}
+
 int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, int* variant_out,
                   double* ms_out, double* ms_each, int ms_each_len) {
   SetState* st = get_set(ctx, set_id);
@@ -939,6 +1055,21 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
   }
   if (variant_out) *variant_out = best;
   if (ms_out) *ms_out = best_ms;
+  return tune_chunks(ctx, *st, batch, s);
+}
+
+int fdfb_set_chunks(fdfb_ctx* ctx, int set_id, int chunks) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || chunks < 1 || chunks > kMaxChunks) return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  st->chunks = chunks;
+  return FDFB_OK;
+}
+
+int fdfb_get_chunks(fdfb_ctx* ctx, int set_id, int* chunks) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !chunks) return FDFB_EINVAL;
+  *chunks = st->chunks;
   return FDFB_OK;
 }
 
@@ -962,12 +1093,34 @@ int fdfb_profile_enable(fdfb_ctx* ctx, int enable) {
 int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launches) {
   if (!ctx || stage < 0 || stage >= kStages || !total_ms || !launches) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
+  // Blind-rotation launches of different chunks overlap: stage 5 is the
+  // length of the union of their [start, end] intervals.
+  std::vector<std::pair<double, double>> br;
   for (auto& m : ctx->marks) {
-    float ms = 0;
+    float ms = 0, t0 = 0;
     FD_CUDA(cudaEventSynchronize(m.b));
     FD_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
     ctx->prof_ms[m.stage] += ms;
     ctx->prof_n[m.stage] += 1;
+    // start relative to the first mark (negative when it ran earlier on
+    // another stream)
+    if ((m.stage == 0 || m.stage == 3) && cudaEventElapsedTime(&t0, ctx->marks[0].a, m.a) == cudaSuccess)
+      br.push_back({(double)t0, (double)t0 + ms});
+  }
+  std::sort(br.begin(), br.end());
+  double lo = 0, hi = -1e300;
+  for (auto& iv : br) {
+    if (iv.first > hi) {
+      if (hi > lo) ctx->prof_ms[5] += hi - lo;
+      lo = iv.first;
+      hi = iv.second;
+    } else if (iv.second > hi) {
+      hi = iv.second;
+    }
+  }
+  if (!br.empty() && hi > lo) ctx->prof_ms[5] += hi - lo;
+  ctx->prof_n[5] += (int64_t)br.size();
+  for (auto& m : ctx->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
   }

@@ -53,9 +53,18 @@ struct Inst {
     bsk_to_ntt_kernel<L, EL, P, W><<<(unsigned)rows, THREADS, sm, st>>>(S, bsk, R, out);
     return cudaGetLastError();
   }
+  static int br_blocks_per_sm(size_t smem) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP>, THREADS, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return b;
+  }
   static Ops ops() {
     return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
-               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0};
+               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm};
   }
 };
 

@@ -19,6 +19,7 @@ struct Ops {
   cudaError_t (*bsk_ntt)(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
                          cudaStream_t st);
   int family;  // NTT prime family of the blind rotation (0: 30-bit primes, 1: lazy family)
+  int (*br_blocks_per_sm)(size_t smem);  // resident blind-rotation CTAs per SM
 };
 
 // Returns the launcher table of register-layout variant `variant` for

@@ -27,7 +27,7 @@ SYMBOLS = [
     "fdfb_bootstrap", "fdfb_bootstrap_debug", "fdfb_bootstrap_mixed", "fdfb_keyswitch",
     "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch", "fdfb_bootstrap_multi",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
-    "fdfb_set_variant", "fdfb_variant_info", "fdfb_profile_enable",
+    "fdfb_set_variant", "fdfb_variant_info", "fdfb_set_chunks", "fdfb_get_chunks", "fdfb_profile_enable",
     "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
 ]
 
@@ -91,6 +91,8 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_bootstrap_noalloc": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_noalloc_max_batch": ([vp, i32, C.POINTER(i64)], i32),
                 "fdfb_bootstrap_multi": ([vp, i32, vp, vp, i64, i32, vp, vp], i32),
+                "fdfb_set_chunks": ([vp, i32, i32], i32),
+                "fdfb_get_chunks": ([vp, i32, C.POINTER(i32)], i32),
                 "fdfb_keyswitch": ([vp, i32, vp, i64, vp, vp], i32),
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
                 "fdfb_lwe_decrypt": ([vp, i32, vp, vp, i64, vp, vp], i32),
@@ -321,6 +323,14 @@ class Context:
     def set_variant(self, set_id: int, variant: int) -> None:
         _check(self.L.fdfb_set_variant(self.h, set_id, int(variant)), "fdfb_set_variant")
 
+    def set_chunks(self, set_id: int, chunks: int) -> None:
+        _check(self.L.fdfb_set_chunks(self.h, set_id, int(chunks)), "fdfb_set_chunks")
+
+    def get_chunks(self, set_id: int) -> int:
+        c = C.c_int()
+        _check(self.L.fdfb_get_chunks(self.h, set_id, C.byref(c)), "fdfb_get_chunks")
+        return c.value
+
     def variant_info(self, set_id: int):
         """(current variant, number of variants, coefficients per thread)."""
         cur, cnt, cpt = C.c_int(), C.c_int(), C.c_int()
@@ -328,7 +338,8 @@ class Context:
                "fdfb_variant_info")
         return cur.value, cnt.value, cpt.value
 
-    STAGES = ("blind_rotate_sign", "keyswitch_pk", "pubmux", "blind_rotate_func", "keyswitch_ksk")
+    STAGES = ("blind_rotate_sign", "keyswitch_pk", "pubmux", "blind_rotate_func", "keyswitch_ksk",
+              "blind_rotate_union")
 
     def profile_enable(self, enable: bool = True) -> None:
         _check(self.L.fdfb_profile_enable(self.h, 1 if enable else 0), "fdfb_profile_enable")

@@ -625,3 +625,62 @@ def test_bootstrap_captured_in_cuda_graph(F, torch_cuda, ctx, oracle):
     torch.cuda.synchronize()
     for (ps, ref), (_, _, _, out) in zip(refs, groups):
         assert np.array_equal(F.to_host_words(ps, out).astype(np.uint64), ref)
+
+
+def test_chunked_calls_are_bit_exact(F, torch_cuda, ctx, oracle):
+    """fdfb_bootstrap and fdfb_bootstrap_multi split a batch into 1-4 slices
+    on side streams: every chunk count returns the same ciphertexts (set B, 300
+    inputs, and 50 inputs x 3 tables); the union of the blind-rotation launch
+    intervals is at most the sum of their durations; a chunked call replays
+    from a CUDA graph bit for bit."""
+    torch = torch_cuda
+    ps = S.PARAM_SETS["B"]
+    K = oracle_keys("B", 1)
+    sid = install(ctx, oracle, "B", 1, 4)
+    fs, rot = luts("B", 1, 4)
+    ids = S.lut_assignment(1, 300, 4, "uniform", group=40)
+    mr, cts = fresh_cts("B", 1, 300, K, group=40)
+    saved = ctx.get_chunks(sid)
+    outs = []
+    for c in (1, 2, 3, 4):
+        ctx.set_chunks(sid, c)
+        assert ctx.get_chunks(sid) == c
+        out, _ = run_gpu(F, torch, ctx, sid, ps, cts, ids, debug=False)
+        outs.append(out)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    assert np.array_equal(outs[0][7], oracle.fdfb_bootstrap(ps, K, rot[ids[7]][0], rot[ids[7]][1], cts[7]))
+    ids2 = np.random.default_rng(9).integers(0, 4, size=(50, 3)).astype(np.int32)
+    ctx.set_chunks(sid, 3)
+    m3 = run_gpu_multi(F, torch, ctx, sid, ps, cts[:50], ids2)
+    ctx.set_chunks(sid, 1)
+    m1 = run_gpu_multi(F, torch, ctx, sid, ps, cts[:50], ids2)
+    assert np.array_equal(m3, m1)
+    # measurement hook: stage 5 is the union of the rotations' intervals
+    ctx.set_chunks(sid, 3)
+    ctx.profile_enable(True)
+    run_gpu(F, torch, ctx, sid, ps, cts, ids, debug=False)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    total = prof["blind_rotate_sign"][0] + prof["blind_rotate_func"][0]
+    assert prof["blind_rotate_sign"][1] == 3 and prof["blind_rotate_func"][1] == 3
+    assert prof["blind_rotate_union"][1] == 6
+    assert 0 < prof["blind_rotate_union"][0] <= total + 1e-3
+    # graph capture of a chunked call (side streams exist from the calls above)
+    ctx.set_chunks(sid, 2)
+    ct_d = F.to_device_words(ps, cts)
+    ids_d = torch.tensor(ids, device="cuda")
+    out_d = torch.full_like(ct_d, -1)
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            ctx.bootstrap(sid, ct_d, ids_d, out_d)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(F.to_host_words(ps, out_d).astype(np.uint64), outs[0])
+    with pytest.raises(F.FDFBError):
+        ctx.set_chunks(sid, 0)
+    with pytest.raises(F.FDFBError):
+        ctx.set_chunks(sid, 5)
+    ctx.set_chunks(sid, saved)
