@@ -272,9 +272,9 @@ int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant);
  * and joined back to the caller's stream (the paper has no counterpart: the
  * launches of the slices overlap on the GPU, filling the last partial wave of
  * one blind-rotation launch with the next).  Results do not depend on it.
- * 1 to 4; 1 (one pipeline on the caller's stream) until fdfb_autotune times
- * the whole pipeline with 1-4 slices for batches below 8 waves of the blind
- * rotation.  A call with more than one slice creates the side streams on
+ * 1 to 8; 1 (one pipeline on the caller's stream) until fdfb_autotune times
+ * the whole pipeline with 1, 2, 3, 4, 6 and 8 slices for batches below 8
+ * waves of the blind rotation.  A call with more than one slice creates the side streams on
  * first use; make it outside any stream capture.  The debug, no-allocation
  * and mixed entry points always run one pipeline per group. */
 int fdfb_set_chunks(fdfb_ctx* ctx, int set_id, int chunks);

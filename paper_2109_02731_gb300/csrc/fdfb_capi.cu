@@ -351,7 +351,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   return FDFB_OK;
 }
 
-constexpr int kMaxChunks = 4;
+constexpr int kMaxChunks = 8;
 
 // Library side streams (and count + 1 fork/join events) for chunked calls.
 int ensure_chunk_streams(fdfb_ctx* ctx, int count) {
@@ -940,8 +940,8 @@ int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant) {
 }
 
 // Chooses how many chunks fdfb_bootstrap splits a batch of `batch` into: the
-// whole pipeline on zero trial ciphertexts (table 0) is timed with 1 to
-// kMaxChunks chunks.  Only batches below 8 waves of the blind rotation are
+// whole pipeline on zero trial ciphertexts (table 0) is timed with 1, 2, 3,
+// 4, 6 and 8 chunks.  Only batches below 8 waves of the blind rotation are
 // tried (beyond that the last partial wave costs little) and only when a
 // table is installed; otherwise one chunk.
 int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
@@ -965,7 +965,8 @@ int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
     FD_CUDA(cudaEventCreate(&b));
     float best_ms = 1e30f;
     int rc = FDFB_OK;
-    for (int c = 1; c <= kMaxChunks && rc == FDFB_OK; ++c) {
+    for (int c : {1, 2, 3, 4, 6, 8}) {
+      if (rc != FDFB_OK || c > kMaxChunks) break;
       float ms_c = 1e30f;
       for (int rep = 0; rep < 2 && rc == FDFB_OK; ++rep) {
         cudaEventRecord(a, s);

@@ -628,7 +628,7 @@ def test_bootstrap_captured_in_cuda_graph(F, torch_cuda, ctx, oracle):
 
 
 def test_chunked_calls_are_bit_exact(F, torch_cuda, ctx, oracle):
-    """fdfb_bootstrap and fdfb_bootstrap_multi split a batch into 1-4 slices
+    """fdfb_bootstrap and fdfb_bootstrap_multi split a batch into 1-8 slices
     on side streams: every chunk count returns the same ciphertexts (set B, 300
     inputs, and 50 inputs x 3 tables); the union of the blind-rotation launch
     intervals is at most the sum of their durations; a chunked call replays
@@ -642,7 +642,7 @@ def test_chunked_calls_are_bit_exact(F, torch_cuda, ctx, oracle):
     mr, cts = fresh_cts("B", 1, 300, K, group=40)
     saved = ctx.get_chunks(sid)
     outs = []
-    for c in (1, 2, 3, 4):
+    for c in (1, 2, 3, 4, 8):
         ctx.set_chunks(sid, c)
         assert ctx.get_chunks(sid) == c
         out, _ = run_gpu(F, torch, ctx, sid, ps, cts, ids, debug=False)
@@ -682,5 +682,5 @@ def test_chunked_calls_are_bit_exact(F, torch_cuda, ctx, oracle):
     with pytest.raises(F.FDFBError):
         ctx.set_chunks(sid, 0)
     with pytest.raises(F.FDFBError):
-        ctx.set_chunks(sid, 5)
+        ctx.set_chunks(sid, 9)
     ctx.set_chunks(sid, saved)
