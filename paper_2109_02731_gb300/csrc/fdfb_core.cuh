@@ -390,24 +390,31 @@ struct Xch {
 
 // Exchange buffer of two polynomials transformed together: the two words of
 // position j form one 64-bit word at index addr(j).  A 64-bit shared access
-// is served per half-warp, so the swizzle XORs the low four bits of j (the
-// 8-byte bank) with a GF(2)-linear function of bits 4.. such that, for every
-// pass layout and register index, the 16 lanes of each half-warp hit 16
-// distinct 8-byte banks (masks found by exhaustive search over the layouts).
+// is served per half-warp, so for every pass layout and register index the
+// 16 lanes of each half-warp must hit 16 distinct 8-byte banks (addr mod 16).
+// With 16 coefficients per thread the padded index j + (j >> 4) does this
+// (checked exhaustively for N = 2^9 .. 2^12); it is additive over the
+// disjoint thread and register bits of j, so each access is a per-thread
+// base plus a compile-time offset.  N = 2^8 with 8 coefficients per thread has
+// no such padding and uses an XOR swizzle of the low four bits instead
+// (masks found by exhaustive search).
 template <int L, int EL>
 struct Xch64 {
+  static constexpr bool kAdditive = (EL == 4);
+  static constexpr int kEntries = kAdditive ? (1 << L) + ((1 << L) >> 4) : (1 << L);
   FD_HD static constexpr uint32_t mask(int b) {
     if (L == 8 && EL == 3) { constexpr uint8_t m[] = {1, 4, 10, 0}; return m[b - 4]; }
-    return b < 8 ? (1u << (b - 4)) : 0u;
+    return 0u;
   }
   FD_HD static uint32_t addr(uint32_t j) {
+    if (kAdditive) return j + (j >> 4);
     uint32_t h = 0;
 #pragma unroll
     for (int b = 4; b < L; ++b)
       if ((j >> b) & 1u) h ^= mask(b);
     return j ^ h;
   }
-  FD_HD static uint32_t join(uint32_t base, uint32_t off) { return base ^ off; }
+  FD_HD static uint32_t join(uint32_t base, uint32_t off) { return kAdditive ? base + off : base ^ off; }
 };
 
 }  // namespace fdfb

@@ -56,7 +56,7 @@ __device__ __forceinline__ void exchange(uint32_t (&v)[1 << EL], int t, uint32_t
 
 // Exchange / transforms of M polynomials at once.  M = 1: one buffer of XW
 // words.  M = 2: the two words of a position travel as one 64-bit word
-// (Xch64), in a buffer of XW 64-bit words; with PP the exchanges between
+// (Xch64), in a buffer of XW 64-bit entries; with PP the exchanges between
 // passes 0 and 1 and between passes 1 and 2 use two such buffers, so a
 // buffer is rewritten only after the other buffer's exchange has synchronised
 // the group, and the barrier that protects the reads can be dropped.  That
@@ -210,9 +210,16 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * M * (PP ? 2 : 1) * xwords() * 4;
+    return acc + an + r1 + (size_t)P * group_words() * 4;
   }
+  // 32-bit words of one polynomial's exchange buffer (M = 1)
   static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3; }
+  // 64-bit entries of one paired exchange buffer (M = 2)
+  static constexpr size_t x64entries() { return ((size_t)Xch64<L, EL>::kEntries + 1) & ~(size_t)1; }
+  // 32-bit words of one group's exchange region
+  static constexpr size_t group_words() {
+    return M == 2 ? (PP ? 2 : 1) * 2 * x64entries() : (size_t)M * xwords();
+  }
 };
 
 // Resident CTAs per SM the register budget is sized for (512 threads per SM).
@@ -308,8 +315,9 @@ blind_rotate_kernel(const BRParams prm) {
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
-  constexpr int XW = (int)BRShape<L, EL, P, W, DT, M, PP>::xwords();
-  uint32_t* xb = exch + grp * M * (PP ? 2 : 1) * XW;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP>;
+  constexpr int XW = (int)(M == 2 ? Sh::x64entries() : Sh::xwords());
+  uint32_t* xb = exch + grp * (int)Sh::group_words();
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
