@@ -187,7 +187,7 @@ int install_bsk_ntt(SetState& st, cudaStream_t s) {
   const fdfb_params& P = st.prm;
   const size_t N = P.N;
   for (auto& v : st.var) {
-    FD_TRY(v->bsk_ntt.ensure((size_t)P.n * v->ops->P * 2 * P.lg * 2 * N * 4));
+    FD_TRY(v->bsk_ntt.ensure((size_t)P.n * v->ops->P * 2 * P.lg * 2 * v->ops->key_halves * N * 4));
     FD_CUDA(v->ops->bsk_ntt(v->S, st.bsk.p, (int64_t)P.n * 2 * P.lg, 2 * (int)P.lg,
                             (uint32_t*)v->bsk_ntt.p, s));
   }
@@ -543,6 +543,10 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
     v->ops = ops;
     if ((int)P.log2Bg > ops->max_log2B) continue;  // digits too wide for this variant
     if (ops->family && !host::lift_is_exact(ops->P, br_max, ops->family)) continue;
+    if (ops->key_halves == 2 &&
+        !host::lift_is_exact(ops->P, 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * ldexpl(1.0L, 31),
+                             ops->family))
+      continue;  // each key half's products must lift exactly
     v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);
     if (v->br_smem > (size_t)max_smem) {
       continue;

@@ -5,18 +5,19 @@
 namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
+          int KH = 1>
 struct Inst {
-  using Sh = BRShape<L, EL, P, W, DT, M, PP>;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
-    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP>,
+    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH><<<(unsigned)batch, THREADS, smem, st>>>(prm);
     return cudaGetLastError();
   }
   static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {
@@ -46,17 +47,17 @@ struct Inst {
     if (rows <= 0) return cudaSuccess;
     constexpr size_t sm = (size_t)P * (((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3) * 4;
     if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(bsk_to_ntt_kernel<L, EL, P, W>,
+      cudaError_t e = cudaFuncSetAttribute(bsk_to_ntt_kernel<L, EL, P, W, KH>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    bsk_to_ntt_kernel<L, EL, P, W><<<(unsigned)rows, THREADS, sm, st>>>(S, bsk, R, out);
+    bsk_to_ntt_kernel<L, EL, P, W, KH><<<(unsigned)rows, THREADS, sm, st>>>(S, bsk, R, out);
     return cudaGetLastError();
   }
   static int br_blocks_per_sm(size_t smem) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP>, THREADS, smem) != cudaSuccess) {
+            &b, blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH>, THREADS, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -64,7 +65,7 @@ struct Inst {
   }
   static Ops ops() {
     return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
-               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm};
+               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm, KH};
   }
 };
 

@@ -184,7 +184,7 @@ __device__ __forceinline__ uint32_t modswitch_2n(W x) {
 // ---------------------------------------------------------------------------
 struct BRParams {
   PrimeSet S;
-  const uint32_t* bsk;    // [n][P][2 lg][2][N]
+  const uint32_t* bsk;    // [n][P][2 lg][2][KH][N]
   const void* ct;         // [batch / rep][n+1] words (input LWE, modulus q)
   const void* acc0;       // function mode: [batch][2N] words; sign mode: nullptr
   void* lwe_out;          // [batch][N+1] words: SampleExtract(acc, 0) (+ Delta/2 in sign mode)
@@ -197,7 +197,7 @@ struct BRParams {
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
 };
 
-template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false>
+template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -206,7 +206,7 @@ struct BRShape {
     size_t acc = 2 * (size_t)N * sizeof(W);
     size_t an = ((size_t)n * 2 + 15) & ~(size_t)15;
     size_t dig = (2 * (size_t)lg * N * sizeof(DT) + 15) & ~(size_t)15;
-    size_t stage = (size_t)2 * (P - 1) * N * 4;
+    size_t stage = (size_t)2 * (P - 1) * KH * N * 4;
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
@@ -262,14 +262,21 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // pointwise products unreduced.
 // PP: two exchange buffers per group used in turn (M = 2 only), one group
 // barrier per exchange instead of two.
+// KH = 2 (q = 2^64, two primes): every key word K is split into centred
+// 32-bit halves, K = K_lo + 2^32 K_hi; both halves share the digits' forward
+// transforms, and each half's product sum (at most 2l N (B-1) 2^31) is lifted
+// exactly from two primes: acc += X_lo + 2^32 X_hi mod 2^64.
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
-          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false>
+          int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
+          int KH = 1>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
   static_assert(P >= 2, "the column owners are groups 0 and 1");
   static_assert(!LZ || (L <= 12 && sizeof(DT) <= 2), "lazy bound: 2^16 + 2 L p < 2^32");
+  static_assert(KH == 1 || (KH == 2 && P == 2 && M == 2 && !WIDE && sizeof(W) == 8),
+                "split keys: q = 2^64, two primes, paired transforms, per-product reduction");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
@@ -315,7 +322,7 @@ blind_rotate_kernel(const BRParams prm) {
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
-  using Sh = BRShape<L, EL, P, W, DT, M, PP>;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
   constexpr int XW = (int)(M == 2 ? Sh::x64entries() : Sh::xwords());
   uint32_t* xb = exch + grp * (int)Sh::group_words();
   const int bar = 1 + grp;
@@ -352,11 +359,13 @@ blind_rotate_kernel(const BRParams prm) {
     // other groups column c in macc[c]: the column a group lifts (its own
     // index, for groups 0 and 1) always ends up in macc[1].
     using Acc = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
-    Acc macc[2][E];
+    Acc macc[KH][2][E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
+    for (int h = 0; h < KH; ++h)
+#pragma unroll
+      for (int k = 0; k < E; ++k) { macc[h][0][k] = 0; macc[h][1][k] = 0; }
     const int swap = (grp == 0) ? 1 : 0;
-    const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * N;
+    const uint32_t* krow = prm.bsk + ((size_t)i * P + grp) * R * 2 * KH * N;
     for (int r0 = 0; r0 < R; r0 += M) {
       uint32_t v[M][E];
 #pragma unroll
@@ -373,23 +382,26 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const uint4* kp =
-              reinterpret_cast<const uint4*>(krow + ((size_t)(r0 + m) * 2 + (c ^ swap)) * N) + t;
+        for (int h = 0; h < KH; ++h) {
 #pragma unroll
-          for (int q4 = 0; q4 < E / 4; ++q4) {
-            const uint4 kk = ldg_stream(kp + q4 * G);
-            const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+          for (int m = 0; m < M; ++m) {
+            const uint4* kp =
+                reinterpret_cast<const uint4*>(krow + (((size_t)(r0 + m) * 2 + (c ^ swap)) * KH + h) * N) + t;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if constexpr (WIDE) {
-                // K < p, and v < p (or, lazy family, v < 2^32 and p < 2^28):
-                // 2l <= 8 products stay below 2^63
-                macc[c][q4 * 4 + u] += (uint64_t)v[m][q4 * 4 + u] * kv[u];
-              } else {
-                const uint32_t mm = redc((uint64_t)v[m][q4 * 4 + u] * kv[u], p, pneg);  // < 2p
-                uint32_t s2 = (uint32_t)macc[c][q4 * 4 + u] + mm + z;
-                macc[c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+            for (int q4 = 0; q4 < E / 4; ++q4) {
+              const uint4 kk = ldg_stream(kp + q4 * G);
+              const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if constexpr (WIDE) {
+                  // K < p, and v < p (or, lazy family, v < 2^32 and p < 2^28):
+                  // 2l <= 8 products stay below 2^63
+                  macc[h][c][q4 * 4 + u] += (uint64_t)v[m][q4 * 4 + u] * kv[u];
+                } else {
+                  const uint32_t mm = redc((uint64_t)v[m][q4 * 4 + u] * kv[u], p, pneg);  // < 2p
+                  uint32_t s2 = (uint32_t)macc[h][c][q4 * 4 + u] + mm + z;
+                  macc[h][c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+                }
               }
             }
           }
@@ -400,31 +412,35 @@ blind_rotate_kernel(const BRParams prm) {
 
     // Inverse transforms.  Column c is lifted by group c, which keeps its own
     // residues in registers; every other group stages its residues for it.
-    uint32_t own[E];
+    // (staging slot s of key half h at stage + (s KH + h) N)
+    uint32_t own[KH][E];
     if constexpr (M == 2) {
-      uint32_t v[2][E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) {
-        v[0][k] = acc_to_inv<WIDE, LZ>(macc[0][k], p, pneg, ones);
-        v[1][k] = acc_to_inv<WIDE, LZ>(macc[1][k], p, pneg, ones);
-      }
-      ntt_inv_m<L, EL, Y::K - 1, 2, XW, PP>(v, t, twi, p, xb, bar, z);
-      uint32_t* dst0 = stage + stage_slot<P>(grp, swap) * N;
+      for (int h = 0; h < KH; ++h) {
+        uint32_t v[2][E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) dst0[Y::j_of(0, t, k)] = csub(v[0][k], p);
-      if (grp < 2) {
+        for (int k = 0; k < E; ++k) {
+          v[0][k] = acc_to_inv<WIDE, LZ>(macc[h][0][k], p, pneg, ones);
+          v[1][k] = acc_to_inv<WIDE, LZ>(macc[h][1][k], p, pneg, ones);
+        }
+        ntt_inv_m<L, EL, Y::K - 1, 2, XW, PP>(v, t, twi, p, xb, bar, z);
+        uint32_t* dst0 = stage + (stage_slot<P>(grp, swap) * KH + h) * N;
 #pragma unroll
-        for (int k = 0; k < E; ++k) own[k] = csub(v[1][k], p);
-      } else {
-        uint32_t* dst1 = stage + stage_slot<P>(grp, 1) * N;
+        for (int k = 0; k < E; ++k) dst0[Y::j_of(0, t, k)] = csub(v[0][k], p);
+        if (grp < 2) {
 #pragma unroll
-        for (int k = 0; k < E; ++k) dst1[Y::j_of(0, t, k)] = csub(v[1][k], p);
+          for (int k = 0; k < E; ++k) own[h][k] = csub(v[1][k], p);
+        } else {
+          uint32_t* dst1 = stage + (stage_slot<P>(grp, 1) * KH + h) * N;
+#pragma unroll
+          for (int k = 0; k < E; ++k) dst1[Y::j_of(0, t, k)] = csub(v[1][k], p);
+        }
       }
     } else {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][k], p, pneg, ones);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][0][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
@@ -433,11 +449,11 @@ blind_rotate_kernel(const BRParams prm) {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[1][k], p, pneg, ones);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][1][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         if (grp < 2) {
 #pragma unroll
-          for (int k = 0; k < E; ++k) own[k] = csub(v[k], p);
+          for (int k = 0; k < E; ++k) own[0][k] = csub(v[k], p);
         } else {
           uint32_t* dst = stage + stage_slot<P>(grp, 1) * N;
 #pragma unroll
@@ -451,11 +467,17 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const int j = Y::j_of(0, t, k);
-        uint32_t x[P];
+        W add = 0;
 #pragma unroll
-        for (int g = 0; g < P; ++g)
-          x[g] = (g == c) ? own[k] : stage[stage_slot<P>(g, c) * N + j];
-        acc[c * N + j] = (W)(acc[c * N + j] + (W)garner_p<P>(x, prm.S));
+        for (int h = 0; h < KH; ++h) {
+          uint32_t x[P];
+#pragma unroll
+          for (int g = 0; g < P; ++g)
+            x[g] = (g == c) ? own[h][k] : stage[(stage_slot<P>(g, c) * KH + h) * N + j];
+          const W X = (W)garner_p<P>(x, prm.S);
+          add = (W)(add + (h == 0 ? X : (W)((uint64_t)X << 32)));
+        }
+        acc[c * N + j] = (W)(acc[c * N + j] + add);
       }
     }
     __syncthreads();
@@ -623,13 +645,17 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_kernel(const
 }
 
 // Converts canonical GGSW rows [n][2 lg][2][N] into the transform domain:
-// out[i][g][r][c][.] = NTT(centred(bsk[i][r][c]) mod p_g) * N^-1 * 2^32 mod p_g.
+// out[i][g][r][c][h][.] = NTT(centred(half h of bsk[i][r][c]) mod p_g) * N^-1 * 2^32
+// mod p_g, with KH = 1 (the whole word) or KH = 2 (q = 2^64: the centred
+// halves K_lo = (int32) K and K_hi = (K >> 32) + [K_lo < 0], arithmetic
+// shift, so that K = K_lo + 2^32 K_hi with |K_lo|, |K_hi| <= 2^31).
 // Transform output j = t E + k (thread t of the last pass, register k) is
 // stored at (k / 4) 4G + 4t + k % 4, so that the blind rotation's 128-bit
 // key loads are contiguous across a warp.
-template <int L, int EL, int P, typename W>
+template <int L, int EL, int P, typename W, int KH = 1>
 __global__ void __launch_bounds__(P * (1 << (L - EL)))
 bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
+  static_assert(KH == 1 || sizeof(W) == 8, "key halves are for 64-bit words");
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -642,15 +668,30 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
   const uint32_t p = S.p[grp];
   const W* src = reinterpret_cast<const W*>(bsk) + row * 2 * N;
   for (int c = 0; c < 2; ++c) {
-    uint32_t v[E];
+    for (int h = 0; h < KH; ++h) {
+      uint32_t v[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) v[k] = mod_centred<W>(src[c * N + Y::j_of(0, t, k)], S, grp);
-    ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * XW, 1 + grp, S.zero);
-    uint32_t* dst = out + (((size_t)i * P + grp) * R + r) * 2 * N + (size_t)c * N;
+      for (int k = 0; k < E; ++k) {
+        const W x = src[c * N + Y::j_of(0, t, k)];
+        if (KH == 1) {
+          v[k] = mod_centred<W>(x, S, grp);
+        } else {
+          const uint64_t u = (uint64_t)x;
+          if (h == 0) {
+            v[k] = mod_centred<uint32_t>((uint32_t)u, S, grp);  // K_lo = (int32) K
+          } else {
+            const int64_t hi = ((int64_t)u >> 32) + (((uint32_t)u >> 31) ? 1 : 0);
+            v[k] = mod_centred<uint64_t>((uint64_t)hi, S, grp);
+          }
+        }
+      }
+      ntt_fwd<L, EL, 0>(v, t, S.tw_fwd + (size_t)grp * N, p, exch + grp * XW, 1 + grp, S.zero);
+      uint32_t* dst = out + ((((size_t)i * P + grp) * R + r) * 2 + c) * KH * N + (size_t)h * N;
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const uint32_t x = csub(csub(v[k], 2 * p), p);
-      dst[(k >> 2) * 4 * G + t * 4 + (k & 3)] = csub(mul_shoup(x, S.ninv_m[grp], S.ninv_ms[grp], p), p);
+      for (int k = 0; k < E; ++k) {
+        const uint32_t y = csub(csub(v[k], 2 * p), p);
+        dst[(k >> 2) * 4 * G + t * 4 + (k & 3)] = csub(mul_shoup(y, S.ninv_m[grp], S.ninv_ms[grp], p), p);
+      }
     }
   }
 }

@@ -20,6 +20,7 @@ struct Ops {
                          cudaStream_t st);
   int family;  // NTT prime family of the blind rotation (0: 30-bit primes, 1: lazy family)
   int (*br_blocks_per_sm)(size_t smem);  // resident blind-rotation CTAs per SM
+  int key_halves;  // 2: 64-bit key words split into 32-bit halves over two primes
 };
 
 // Returns the launcher table of register-layout variant `variant` for
