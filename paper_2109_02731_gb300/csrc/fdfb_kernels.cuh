@@ -23,6 +23,12 @@ __device__ __forceinline__ uint4 ldg_stream(const uint4* p) {
   return v;
 }
 
+// Asks the bulk-copy engine to bring `bytes` (a multiple of 16, 16-byte
+// aligned) into L2; no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -331,8 +337,15 @@ blind_rotate_kernel(const BRParams prm) {
   const uint32_t dmask = (1u << log2Bg) - 1;
   const int R = 2 * lg;
 
+  // Each group's key block of a step is contiguous (R rows x 2 columns x KH
+  // halves x N words); one thread per group prefetches the next step's block
+  // into L2 while this step computes (the keys of the q = 2^64 sets do not fit
+  // in L2).
+  const uint32_t kblock = (uint32_t)(R * 2 * KH * N * 4);
+  if (t == 0) prefetch_l2_bulk(prm.bsk + (size_t)grp * R * 2 * KH * N, kblock);
   for (int i = 0; i < n; ++i) {
     const int a = aN[i];
+    if (t == 0 && i + 1 < n) prefetch_l2_bulk(prm.bsk + ((size_t)(i + 1) * P + grp) * R * 2 * KH * N, kblock);
     // d = acc X^{-a} - acc, rounded and split into digits (component major).
     // Coefficient j of acc X^{-a} is acc[(j + a) mod 2N], negated when that
     // index lies in [N, 2N) (X^N = -1).
