@@ -80,6 +80,8 @@ def lib():
                 "or_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
                 "or_fdfb_batch": ([vp, vp, vp, vp, vp, vp, i64, vp, vp], None),
                 "or_fdfb_bootstrap_multi": ([vp, vp, vp, vp, vp, i32, vp, vp], None),
+                "or_tfhe_bootstrap": ([vp, vp, vp, vp, vp, vp], None),
+                "or_tfhe_batch": ([vp, vp, vp, vp, vp, i64, vp, vp], None),
                 "or_fdfb_batch_multi": ([vp, vp, vp, vp, vp, vp, i32, i64, vp, vp], None),
                 "or_lwe_affine": ([i32, i32, i32, i32, vp, vp, vp], None),
             }
@@ -373,6 +375,50 @@ def fdfb_batch_multi(ps, keys: Keys, rotP, lut_ids, cts, threads: int | None = N
     lib().or_fdfb_batch_multi(C.byref(P), _p(keys.bsk), _p(keys.pk), _p(keys.ksk), _p(rotP), _p(ids),
                               k, count, _p(cts), _p(out))
     return out
+
+
+def tfhe_bootstrap(ps, keys: Keys, poly, ct) -> np.ndarray:
+    """TFHE bootstrap of one ciphertext with the pre-rotation polynomial poly
+    (N words mod q)."""
+    P = params(ps)
+    poly, ct = _u64(poly), _u64(ct)
+    out = np.zeros(ps.n + 1, dtype=np.uint64)
+    lib().or_tfhe_bootstrap(C.byref(P), _p(keys.bsk), _p(keys.ksk), _p(poly), _p(ct), _p(out))
+    return out
+
+
+def tfhe_batch(ps, keys: Keys, polys, poly_ids, cts, threads: int | None = None) -> np.ndarray:
+    """polys: [n_polys][N] words; poly_ids: int32[count]; cts: [count][n+1]."""
+    P = params(ps)
+    polys, cts = _u64(polys), _u64(cts)
+    ids = np.ascontiguousarray(np.asarray(poly_ids, dtype=np.int32))
+    out = np.zeros_like(cts)
+    if threads is not None:
+        set_threads(threads)
+    lib().or_tfhe_batch(C.byref(P), _p(keys.bsk), _p(keys.ksk), _p(polys), _p(ids), len(ids), _p(cts),
+                        _p(out))
+    return out
+
+
+def tfhe_test_polynomial(ps, f_half) -> np.ndarray:
+    """A pre-rotation polynomial for the TFHE bootstrap that maps m in
+    [0, t/2) to Delta f_half[m] (and m + t/2 to -Delta f_half[m], the
+    negacyclic half): coefficient 0 of poly X^y must be Delta f(m) for every
+    y within N/t of the ModSwitched phase 2N m / t, y in [0, N), and y rounding
+    to t/2 must give -Delta f(0).  Coefficient 0 of poly X^y is poly[0] for
+    y = 0 and -poly[N - y] for 0 < y < N (and minus that for y in [N, 2N))."""
+    N, t = ps.N, ps.t
+    mask = (1 << ps.w) - 1
+    poly = np.zeros(N, dtype=np.uint64)
+    step = 2 * N // t
+    for y in range(N):
+        m = (y + step // 2) // step               # nearest message, 0 .. t/2
+        v = ps.delta * int(f_half[m]) if m < t // 2 else -ps.delta * int(f_half[0])
+        if y == 0:
+            poly[0] = v & mask
+        else:
+            poly[N - y] = (-v) & mask
+    return poly
 
 
 def lwe_affine(w: int, W, x) -> np.ndarray:

@@ -577,6 +577,39 @@ void or_fdfb_batch_multi(const or_params* P, const u64* bsk, const u64* pk, cons
     }
 }
 
+/* TFHE bootstrap (figure "TFHE Bootstrapping"): ct [n+1] under s, the
+ * pre-rotation polynomial poly [N] (words mod q), out [n+1] under s.
+ * ct_N = ModSwitch(ct, q, 2N); acc_F = [poly X^{b_N}, 0];
+ * acc_BR = BlindRotate(brK, acc_F, ct_N); c_Q = SampleExtract(acc_BR, 1);
+ * out = KeySwitch(c_Q, ksK) (ModSwitch Q -> q is the identity, q = Q). */
+void or_tfhe_bootstrap(const or_params* P, const u64* bsk, const u64* ksk, const u64* poly,
+                       const u64* ct, u64* out) {
+    const int n = P->n, N = P->N, w = P->w;
+    int logN = 0;
+    while ((1 << logN) < N) ++logN;
+    u64* ctN = (u64*)malloc(sizeof(u64) * (n + 1));
+    u64* acc = (u64*)malloc(sizeof(u64) * 2 * N);
+    u64* lwe = (u64*)malloc(sizeof(u64) * (N + 1));
+    or_modswitch(w, logN + 1, n, ct, ctN);
+    or_poly_mul_xk(w, N, poly, (i64)ctN[0], acc);
+    memset(acc + N, 0, sizeof(u64) * N);
+    or_blind_rotate(P, bsk, acc, ctN);
+    or_sample_extract(w, N, acc, 0, lwe);
+    or_keyswitch(w, N, P->log2Bks, P->lks, n + 1, ksk, lwe, out);
+    free(lwe); free(acc); free(ctN);
+}
+
+/* A batch of TFHE bootstraps, one thread per ciphertext: polys [n_polys][N],
+ * poly_ids [count], cts and outs [count][n+1]. */
+void or_tfhe_batch(const or_params* P, const u64* bsk, const u64* ksk, const u64* polys,
+                   const int32_t* poly_ids, int64_t count, const u64* cts, u64* outs) {
+    const int n = P->n, N = P->N;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) if (g_threads > 1)
+    for (int64_t c = 0; c < count; ++c)
+        or_tfhe_bootstrap(P, bsk, ksk, polys + (size_t)poly_ids[c] * N, cts + (size_t)c * (n + 1),
+                          outs + (size_t)c * (n + 1));
+}
+
 /* LWE linear homomorphism (Lemma "Linear Homomorphism of GLWE samples"):
  * y_j = sum_i W[j][i] * x_i over LWE samples, integer weights.
  * W: [n_out][n_in] signed; x: [n_in][len]; y: [n_out][len]. */

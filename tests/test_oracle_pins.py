@@ -438,6 +438,47 @@ def test_fdfb_multi_equals_single(oracle):
     assert np.array_equal(one, multi[1])
 
 
+def test_tfhe_bootstrap_noiseless_closed_form(oracle):
+    """TFHE bootstrap (figure 'TFHE Bootstrapping') with noiseless keys and
+    exact decompositions: BlindRotate multiplies by X^{-<a_N, s>} exactly, so
+    the output phase is coefficient 0 of poly X^{b_N - <a_N, s>}, computed
+    here from the definition of the negacyclic ring (X^N = -1) for arbitrary
+    input words and a random polynomial."""
+    ps = S.PARAM_SETS["Z"]
+    k = _tiny_keys(oracle, ps, 2)
+    rng = np.random.default_rng(21)
+    N, w = ps.N, ps.w
+    logN = N.bit_length() - 1
+    for trial in range(6):
+        poly = rng.integers(0, 1 << w, size=N, dtype=np.uint64)
+        ct = rng.integers(0, 1 << w, size=ps.n + 1, dtype=np.uint64)
+        out = oracle.tfhe_bootstrap(ps, k, poly, ct)
+        # ModSwitch to 2N with rounding half up, then the rotation exponent
+        msw = [((int(x) + (1 << (w - logN - 2))) >> (w - logN - 1)) % (2 * N) for x in ct]
+        e = (msw[0] - sum(msw[1 + i] * int(k.s[i]) for i in range(ps.n))) % (2 * N)
+        # the coefficient of X^0 in poly X^e comes from poly[j], j + e = 0 mod 2N,
+        # negated when j lies in [N, 2N) (X^N = -1)
+        j = (2 * N - e) % (2 * N)
+        want = int(poly[j]) if j < N else (-int(poly[j - N])) % (1 << w)
+        assert oracle.lwe_phase(w, k.s, out) == want, trial
+
+
+def test_tfhe_bootstrap_toy_decrypts(oracle):
+    """Set A: the TFHE bootstrap with a test polynomial for a random f on the
+    first half of Z_t maps every m < t/2 to f(m) and m >= t/2 to -f(m - t/2)
+    (negacyclic), after decryption."""
+    ps = S.PARAM_SETS["A"]
+    k = _tiny_keys(oracle, ps, 3)
+    f_half = np.random.default_rng(22).integers(0, ps.t, size=ps.t // 2)
+    poly = oracle.tfhe_test_polynomial(ps, f_half)
+    mr = S.message_randomness(ps, 3, 24)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.tfhe_batch(ps, k, poly[None, :], np.zeros(len(cts), np.int32), cts)
+    got = [oracle.lwe_decrypt(ps.w, ps.t, k.s, o) for o in outs]
+    want = [int(f_half[m]) if m < ps.t // 2 else (-int(f_half[m - ps.t // 2])) % ps.t for m in mr.m]
+    assert got == want
+
+
 def test_fdfb_toy_decrypts(oracle):
     """Toy workload (set A, seed 0): every output decrypts to f(m)."""
     wl = S.WORKLOADS["toy"]
