@@ -156,6 +156,7 @@ def run_reference(args):
     fs = S.lut_tables(ps, wl.seed, g.n_luts)
     rot = np.stack([np.stack(O.setup_polynomial(ps.N, ps.t, f)) for f in fs])
     ids = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign)
+    polys = S.tfhe_polynomials(ps, wl.seed, g.n_luts) if g.mode == "tfhe" else None
     per_step = args.ref_sample
     mr = S.message_randomness(ps, wl.seed, per_step * (args.steps + args.warmup))
     cts = O.encrypt_messages(ps, K.s, mr)
@@ -163,7 +164,9 @@ def run_reference(args):
     def step(k):
         sl = slice(k * per_step, (k + 1) * per_step)
         for c in range(sl.start, sl.stop):
-            if g.tables_per_input > 1:
+            if g.mode == "tfhe":
+                O.tfhe_bootstrap(ps, K, polys[ids[c % g.batch]], cts[c])
+            elif g.tables_per_input > 1:
                 O.fdfb_bootstrap_multi(ps, K, rot[ids[c % g.batch]], cts[c])
             else:
                 O.fdfb_bootstrap(ps, K, rot[ids[c % g.batch]][0], rot[ids[c % g.batch]][1], cts[c])
@@ -193,7 +196,8 @@ def run_reference(args):
 
 
 def config_of(args, wl, g, ps):
-    return {"workload": f"{wl.name}: FDFB n={ps.n} N={ps.N} q=2^{ps.w} t={ps.t} B_g=2^{ps.log2Bg} "
+    kind = "TFHE bootstrap (one blind rotation of a test polynomial)" if g.mode == "tfhe" else "FDFB"
+    return {"workload": f"{wl.name}: {kind} n={ps.n} N={ps.N} q=2^{ps.w} t={ps.t} B_g=2^{ps.log2Bg} "
                         f"l_g={ps.lg} B_ks=2^{ps.log2Bks} l_ks={ps.lks} B_pk=2^{ps.log2Bpk} l_pk={ps.lpk}, "
                         f"{g.batch} ciphertexts per GPU, {g.n_luts} tables ({g.lut_assign})"
                         + (f", {g.tables_per_input} tables per input sharing one sign rotation"
@@ -216,9 +220,12 @@ def cpu_baseline(wl, g, ps, seconds_target=20.0):
     t0 = time.perf_counter()
     done = 0
     k = g.tables_per_input
+    polys = S.tfhe_polynomials(ps, wl.seed, g.n_luts) if g.mode == "tfhe" else None
     while done < g.batch:
         c = done
-        if k > 1:
+        if polys is not None:
+            O.tfhe_bootstrap(ps, K, polys[ids[c]], cts[c])
+        elif k > 1:
             O.fdfb_bootstrap_multi(ps, K, rot[ids[c]], cts[c])
         else:
             O.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
@@ -257,6 +264,9 @@ class Job:
         fs = S.lut_tables(ps, wl.seed, g.n_luts, gi)
         for f in fs:
             ctx.lut_setup(sid, f)
+        if g.mode == "tfhe":
+            for poly in S.tfhe_polynomials(ps, wl.seed, g.n_luts):
+                ctx.tfhe_poly_setup(sid, poly)
         ids_np = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign, gi)
         mr = rank_messages(ps, wl.seed, g.batch, rank, gi)
         s_d = torch.tensor(kr.s, device=dev)
@@ -282,7 +292,7 @@ class Job:
             want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
             out = torch.empty_like(ct)
         return {"sid": sid, "ps": ps, "batch": g.batch, "k": k, "ct": ct, "ids": ids, "out": out,
-                "s": s_d, "want": want}
+                "s": s_d, "want": want, "mode": g.mode}
 
     def _prepare_mlp(self, args, rank):
         from paper_2109_02731_gb300 import mlp
@@ -315,7 +325,9 @@ class Job:
             self.mlp_out = self.net.forward(self.mlp_x)
         elif len(gs) == 1:
             g = gs[0]
-            if g["k"] > 1:
+            if g.get("mode") == "tfhe":
+                self.ctx.tfhe_bootstrap(g["sid"], g["ct"], g["ids"], g["out"])
+            elif g["k"] > 1:
                 self.ctx.bootstrap_multi(g["sid"], g["ct"], g["ids"], g["out"])
             else:
                 self.ctx.bootstrap(g["sid"], g["ct"], g["ids"], g["out"])
@@ -332,6 +344,8 @@ class Job:
             ctx.sync()
             return float((m.cpu().numpy().reshape(self.mlp_want.shape) == self.mlp_want).mean())
         ok = {}
+        if any(g.get("mode") == "tfhe" for g in self.groups):
+            return None  # uniform test polynomials: no function to check against
         for g in self.groups:
             m = torch.empty(g["batch"] * g["k"], dtype=torch.int32, device=self.dev)
             ctx.lwe_decrypt(g["sid"], g["s"], g["out"].view(-1, g["ps"].n + 1), m)
@@ -343,9 +357,10 @@ class Job:
         if self.wl.mlp_layers:
             ps = self.groups[0]["ps"]
             return 2 * sum(br_algorithmic_slots(ps, b) for b in self.mlp_batches)
-        # one sign rotation per input, one function rotation per (input, table)
-        return sum(br_algorithmic_slots(g["ps"], g["batch"]) + br_algorithmic_slots(g["ps"], g["batch"] * g["k"])
-                   for g in self.groups)
+        # one sign rotation per input, one function rotation per (input, table);
+        # the TFHE bootstrap has the function rotation only
+        return sum((0 if g.get("mode") == "tfhe" else br_algorithmic_slots(g["ps"], g["batch"]))
+                   + br_algorithmic_slots(g["ps"], g["batch"] * g["k"]) for g in self.groups)
 
     def io_bytes(self):
         if self.wl.mlp_layers:
@@ -366,6 +381,8 @@ class Job:
         if self.wl.mlp_layers:
             g = self.groups[0]
             return sum(1 + 5 * pipelines(g, b) for b in self.mlp_batches)
+        if any(g.get("mode") == "tfhe" for g in self.groups):
+            return 3 * len(self.groups)  # accumulator, blind rotation, key switch
         return sum(5 * pipelines(g, g["batch"]) for g in self.groups)
 
 
@@ -500,7 +517,8 @@ def main():
         ms_total, e2e_ms = slowest_rank([ms_total, e2e_ms], dev)
 
     plain = None
-    if args.plain and rank == 0 and not job.wl.mlp_layers and job.groups[0]["k"] == 1:
+    if (args.plain and rank == 0 and not job.wl.mlp_layers and job.groups[0]["k"] == 1
+            and job.groups[0].get("mode") != "tfhe"):
         reps = 8
         g = job.groups[0]
         one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()

@@ -146,6 +146,22 @@ int fdfb_lut_polys(fdfb_ctx* ctx, int set_id, int lut_id, int32_t* p0, int32_t* 
 int fdfb_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
                    int64_t batch, void* ct_out, void* cuda_stream);
 
+/* TFHE bootstrap (figure "TFHE Bootstrapping"): one blind rotation of a
+ * caller-given pre-rotation polynomial, for negacyclic functions (f(m + t/2)
+ * = -f(m)); the paper's comparison point for the full-domain bootstrap.
+ *   ct_N = ModSwitch(ct, q, 2N); acc = [poly X^{b_N}, 0];
+ *   acc = BlindRotate(brK, acc, ct_N); c = SampleExtract(acc, 1);
+ *   ct_out = KeySwitch(c, ksK) (the final ModSwitch Q -> q is the identity).
+ * fdfb_tfhe_poly_setup installs a polynomial (host, N words mod q) and
+ * returns its id, dense from 0 per parameter set.  fdfb_tfhe_bootstrap:
+ * ct_in device [batch][n+1] words; poly_ids device int32[batch]; ct_out
+ * device [batch][n+1].  FDFB_ENOKEYS without keys, FDFB_EBADLUT without a
+ * polynomial; an id out of range is latched as FDFB_EBADLUT (reported by
+ * fdfb_sync) and polynomial 0 used. */
+int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_id_out);
+int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* poly_ids,
+                        int64_t batch, void* ct_out, void* cuda_stream);
+
 /* Several functions of one input (Section "Application of Functional
  * Bootstrapping", multiple univariate functions with the same input: the
  * accumulators of the first bootstrap are reused for the next function).
@@ -284,7 +300,8 @@ int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* 
 /* Measurement hook; the paper has no counterpart.  While enabled, every
  * launch of the bootstrap pipeline is bracketed by a CUDA event pair recorded
  * on the caller's stream, and the device time is accumulated per stage:
- *   0 sign blind rotation, 1 packing key switch, 2 PubMux,
+ *   0 sign blind rotation, 1 packing key switch, 2 PubMux (or the TFHE
+ *   bootstrap's accumulator),
  *   3 function blind rotation, 4 LWE key switch,
  *   5 all blind rotations: the length of the union of the intervals of the
  *     stage 0 and 3 launches (launches of the chunks of one call, on

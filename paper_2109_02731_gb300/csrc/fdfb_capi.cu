@@ -83,6 +83,9 @@ struct SetState {
   std::vector<int16_t> luts_host;  // [n_luts][2][N]
   DevBuf luts;
   int n_luts = 0;
+  std::vector<uint64_t> tpolys_host;  // [n_tpolys][N] words (TFHE bootstrap polynomials)
+  DevBuf tpolys;
+  int n_tpolys = 0;
   DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
   int chunks = 1;  // pieces fdfb_bootstrap splits a large batch into (set by fdfb_autotune)
   size_t wbytes() const { return (size_t)w / 8; }
@@ -432,6 +435,20 @@ int noalloc_scratch(int device, void** out) {
   return FDFB_OK;
 }
 
+// The TFHE bootstrap's accumulator kernel for ring degree 2^L.
+template <typename W>
+cudaError_t launch_tfhe_acc(int L, int64_t batch, cudaStream_t s, const W* ct, int n, const int32_t* ids,
+                            const W* polys, int n_polys, W* acc, int* err) {
+  switch (L) {
+    case 8: tfhe_acc_kernel<W, 8><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    case 9: tfhe_acc_kernel<W, 9><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    case 10: tfhe_acc_kernel<W, 10><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    case 11: tfhe_acc_kernel<W, 11><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    case 12: tfhe_acc_kernel<W, 12><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 }  // namespace
 
 extern "C" {
@@ -729,6 +746,94 @@ int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out
   FD_CUDA(cudaMemcpy(st->luts.p, st->luts_host.data(), st->luts_host.size() * sizeof(int16_t),
                      cudaMemcpyHostToDevice));
   *lut_id_out = st->n_luts++;
+  return FDFB_OK;
+}
+
+int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_id_out) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || !poly || !poly_id_out) return FDFB_EINVAL;
+  const size_t N = st->prm.N;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const size_t off = st->tpolys_host.size();
+  st->tpolys_host.resize(off + N);
+  for (size_t j = 0; j < N; ++j)
+    st->tpolys_host[off + j] = st->w == 32 ? ((const uint32_t*)poly)[j] : ((const uint64_t*)poly)[j];
+  // re-upload all polynomials after a device sync (no launch still reads the old buffer)
+  FD_CUDA(cudaDeviceSynchronize());
+  const size_t wb = st->wbytes(), count = st->tpolys_host.size();
+  FD_TRY(st->tpolys.ensure(count * wb));
+  if (st->w == 32) {
+    std::vector<uint32_t> narrow(st->tpolys_host.begin(), st->tpolys_host.end());
+    FD_CUDA(cudaMemcpy(st->tpolys.p, narrow.data(), count * wb, cudaMemcpyHostToDevice));
+  } else {
+    FD_CUDA(cudaMemcpy(st->tpolys.p, st->tpolys_host.data(), count * wb, cudaMemcpyHostToDevice));
+  }
+  *poly_id_out = st->n_tpolys++;
+  return FDFB_OK;
+}
+
+int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* poly_ids,
+                        int64_t batch, void* ct_out, void* cuda_stream) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st || batch < 0 || batch > 0x7fffffff) return FDFB_EINVAL;
+  if (batch == 0) return FDFB_OK;
+  if (!ct_in || !poly_ids || !ct_out) return FDFB_EINVAL;
+  if (!st->keys) return FDFB_ENOKEYS;
+  if (st->n_tpolys == 0) return FDFB_EBADLUT;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = as_stream(cuda_stream);
+  const fdfb_params& P = st->prm;
+  const size_t N = P.N, wb = st->wbytes();
+  FD_TRY(ensure_scratch(*st, batch, 1));
+  unsigned char* base = (unsigned char*)st->scratch.p;
+  void* accF = base + (size_t)batch * ((N + 1) + 2 * N) * wb;
+  void* cQ = (unsigned char*)accF + (size_t)batch * 2 * N * wb;
+  {
+    StageTimer tm(ctx, 2, s);
+    if (st->w == 32)
+      FD_CUDA(launch_tfhe_acc<uint32_t>(st->L, batch, s, (const uint32_t*)ct_in, (int)P.n, poly_ids,
+                                        (const uint32_t*)st->tpolys.p, st->n_tpolys, (uint32_t*)accF,
+                                        ctx->d_err));
+    else
+      FD_CUDA(launch_tfhe_acc<uint64_t>(st->L, batch, s, (const uint64_t*)ct_in, (int)P.n, poly_ids,
+                                        (const uint64_t*)st->tpolys.p, st->n_tpolys, (uint64_t*)accF,
+                                        ctx->d_err));
+  }
+  Variant& bv = st->br();
+  BRParams br{};
+  br.S = bv.S;
+  br.bsk = (const uint32_t*)bv.bsk_ntt.p;
+  br.ct = ct_in;
+  br.acc0 = accF;
+  br.lwe_out = cQ;
+  br.n = P.n;
+  br.lg = P.lg;
+  br.log2Bg = P.log2Bg;
+  br.rtrunc = trunc_bits(st->w, P.log2Bg, P.lg);
+  br.batch = batch;
+  br.sign_mode = 0;
+  br.smem_r1 = bv.br_r1;
+  br.smem_exch = bv.br_ex;
+  br.rep = 1;
+  {
+    StageTimer tm(ctx, 3, s);
+    FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
+  }
+  {
+    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
+    const int rt = trunc_bits(st->w, P.log2Bks, P.lks);
+    StageTimer tm(ctx, 4, s);
+    if (st->w == 32)
+      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>((const uint32_t*)cQ, batch, (int)N,
+                                                            (const uint32_t*)st->ksk.p, P.lks, P.log2Bks,
+                                                            rt, (int)P.n + 1, (uint32_t*)ct_out);
+    else
+      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>((const uint64_t*)cQ, batch, (int)N,
+                                                            (const uint64_t*)st->ksk.p, P.lks, P.log2Bks,
+                                                            rt, (int)P.n + 1, (uint64_t*)ct_out);
+    FD_CUDA(cudaGetLastError());
+  }
   return FDFB_OK;
 }
 

@@ -619,6 +619,33 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_kernel(const PubMu
       smem);
 }
 
+// Accumulator of the TFHE bootstrap (figure "TFHE Bootstrapping", lines
+// 1-3): b_N = ModSwitch(b, q, 2N) and acc = [poly X^{b_N}, 0] for ciphertext
+// blockIdx.x, poly = polys[ids[blockIdx.x]] ([N] words mod q).  An id out of
+// range latches FDFB_EBADLUT and uses polynomial 0.
+template <typename W, int L>
+__global__ void __launch_bounds__(256)
+tfhe_acc_kernel(const W* __restrict__ ct, int n, const int32_t* __restrict__ ids,
+                const W* __restrict__ polys, int n_polys, W* __restrict__ acc, int* err) {
+  constexpr int N = 1 << L;
+  const int64_t ci = blockIdx.x;
+  const int bN = (int)modswitch_2n<W, L>(ct[ci * (n + 1)]);
+  int id = ids[ci];
+  if (id < 0 || id >= n_polys) {
+    if (threadIdx.x == 0) atomicExch(err, -6);
+    id = 0;
+  }
+  const W* poly = polys + (size_t)id * N;
+  W* out = acc + ci * 2 * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    bool neg;
+    const int m = rot_src<L>(j, bN, neg);
+    const W v = poly[m];
+    out[j] = neg ? (W)(0 - v) : v;
+    out[N + j] = 0;
+  }
+}
+
 // RLWE encryption: out[item] = [a sk + e, a], then mu[item] added to the
 // constant coefficient of component comp[item] (GGSW rows and packing-key
 // samples).  sk is binary.

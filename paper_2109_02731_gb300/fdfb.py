@@ -26,6 +26,7 @@ SYMBOLS = [
     "fdfb_keys_generate", "fdfb_keys_download", "fdfb_lut_setup", "fdfb_lut_polys",
     "fdfb_bootstrap", "fdfb_bootstrap_debug", "fdfb_bootstrap_mixed", "fdfb_keyswitch",
     "fdfb_bootstrap_noalloc", "fdfb_noalloc_max_batch", "fdfb_bootstrap_multi",
+    "fdfb_tfhe_poly_setup", "fdfb_tfhe_bootstrap",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
     "fdfb_set_variant", "fdfb_variant_info", "fdfb_set_chunks", "fdfb_get_chunks", "fdfb_profile_enable",
     "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
@@ -92,6 +93,8 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_noalloc_max_batch": ([vp, i32, C.POINTER(i64)], i32),
                 "fdfb_bootstrap_multi": ([vp, i32, vp, vp, i64, i32, vp, vp], i32),
                 "fdfb_set_chunks": ([vp, i32, i32], i32),
+                "fdfb_tfhe_poly_setup": ([vp, i32, vp, C.POINTER(i32)], i32),
+                "fdfb_tfhe_bootstrap": ([vp, i32, vp, vp, i64, vp, vp], i32),
                 "fdfb_get_chunks": ([vp, i32, C.POINTER(i32)], i32),
                 "fdfb_keyswitch": ([vp, i32, vp, i64, vp, vp], i32),
                 "fdfb_lwe_encrypt": ([vp, i32, vp, vp, vp, vp, i64, vp, vp], i32),
@@ -264,6 +267,20 @@ class Context:
         b, k = int(lut_ids.shape[0]), int(lut_ids.shape[1])
         _check(self.L.fdfb_bootstrap_multi(self.h, set_id, _ptr(ct_in), _ptr(lut_ids), b, k,
                                            _ptr(ct_out), _stream(stream)), "fdfb_bootstrap_multi")
+
+    def tfhe_poly_setup(self, set_id: int, poly) -> int:
+        """Installs a TFHE pre-rotation polynomial (N words mod q); returns its id."""
+        ps = self.sets[set_id]
+        arr = np.ascontiguousarray(np.asarray(poly).astype(word_np(ps)))
+        assert arr.shape == (ps.N,)
+        out = C.c_int()
+        _check(self.L.fdfb_tfhe_poly_setup(self.h, set_id, arr.ctypes.data, C.byref(out)),
+               "fdfb_tfhe_poly_setup")
+        return out.value
+
+    def tfhe_bootstrap(self, set_id: int, ct_in, poly_ids, ct_out, stream=None):
+        _check(self.L.fdfb_tfhe_bootstrap(self.h, set_id, _ptr(ct_in), _ptr(poly_ids), int(ct_in.shape[0]),
+                                          _ptr(ct_out), _stream(stream)), "fdfb_tfhe_bootstrap")
 
     def bootstrap_noalloc(self, set_id: int, ct_in, lut_ids, ct_out, stream=None):
         """fdfb_bootstrap on the library's fixed scratch: allocates nothing."""

@@ -94,6 +94,7 @@ class Group:
     n_luts: int
     lut_assign: str   # "round_robin", "uniform", or "all" (every input, every table)
     tables_per_input: int = 1
+    mode: str = "fdfb"   # "fdfb", or "tfhe" (plain TFHE bootstrap of a test polynomial)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -118,6 +119,9 @@ WORKLOADS: Dict[str, Workload] = {
     # the TFHE-scale inputs, each evaluated under all four tables with one
     # shared sign rotation (several functions of one input)
     "multi_lut": Workload("multi_lut", 1, [Group("B", 1024, 4, "all", tables_per_input=4)]),
+    # the TFHE-scale ciphertexts through the plain TFHE bootstrap (one blind
+    # rotation of a test polynomial per ciphertext; negacyclic functions)
+    "tfhe_plain": Workload("tfhe_plain", 1, [Group("B", 1024, 4, "round_robin", mode="tfhe")]),
     "mlp": Workload("mlp", 4, [Group("D", 0, 2, "uniform")],
                     mlp_layers=[784, 128, 64, 10], mlp_inputs=64),
 }
@@ -284,6 +288,13 @@ def lut_assignment(seed: int, count: int, n_luts: int, how: str, group: int = 0)
         return ((np.arange(count)[:, None] + np.arange(n_luts)[None, :]) % n_luts).astype(np.int32)
     st = Stream(seed, STREAM_LUT_ASSIGN, group)
     return st.below(count, n_luts).astype(np.int32)
+
+
+def tfhe_polynomials(ps: ParamSet, seed: int, count: int) -> np.ndarray:
+    """Pre-rotation polynomials for timing the TFHE bootstrap: [count][N]
+    words uniform mod q (the bootstrap's cost does not depend on them)."""
+    st = Stream(seed, STREAM_LUTS, 100)
+    return np.stack([st.sub(i).words(ps.N, ps.w) for i in range(count)])
 
 
 def mlp_inputs_and_weights(seed: int, layers: List[int], n_inputs: int):

@@ -684,3 +684,63 @@ def test_chunked_calls_are_bit_exact(F, torch_cuda, ctx, oracle):
     with pytest.raises(F.FDFBError):
         ctx.set_chunks(sid, 9)
     ctx.set_chunks(sid, saved)
+
+
+# ---------------------------------------------------------- TFHE bootstrap --
+
+def test_tfhe_bootstrap_matches_oracle(F, torch_cuda, ctx, oracle):
+    """TFHE bootstrap (one blind rotation of a pre-rotation polynomial): set A
+    (20 ciphertexts, two polynomials) and set B (sampled from 300, autotuned
+    layout) bit for bit against the oracle; set A decrypts to the negacyclic
+    function."""
+    torch = torch_cuda
+    for name, seed, batch, sample in (("A", 0, 20, range(20)), ("B", 1, 300, (0, 1, 299))):
+        ps = S.PARAM_SETS[name]
+        K = oracle_keys(name, seed)
+        sid = install(ctx, oracle, name, seed, 1)
+        rng = np.random.default_rng(31)
+        f_halves = [rng.integers(0, ps.t, size=ps.t // 2) for _ in range(2)]
+        polys = np.stack([oracle.tfhe_test_polynomial(ps, f) for f in f_halves])
+        pids = [ctx.tfhe_poly_setup(sid, p) for p in polys]
+        ids = rng.integers(0, 2, size=batch).astype(np.int32)
+        mr, cts = fresh_cts(name, seed, batch, K, group=50)
+        if name == "B":
+            ctx.autotune(sid, batch)
+        ct_d = F.to_device_words(ps, cts)
+        out_d = torch.empty_like(ct_d)
+        ctx.tfhe_bootstrap(sid, ct_d, torch.tensor(np.asarray(pids)[ids], dtype=torch.int32, device="cuda"),
+                           out_d)
+        ctx.sync()
+        got = F.to_host_words(ps, out_d).astype(np.uint64)
+        for c in sample:
+            want = oracle.tfhe_bootstrap(ps, K, polys[ids[c]], cts[c])
+            assert np.array_equal(got[c], want), (name, c)
+        if name == "A":
+            dec = [oracle.lwe_decrypt(ps.w, ps.t, K.s, o) for o in got]
+            h = ps.t // 2
+            exp = [int(f_halves[i][m]) if m < h else (-int(f_halves[i][m - h])) % ps.t for i, m in zip(ids, mr.m)]
+            assert dec == exp
+
+
+def test_tfhe_bootstrap_errors(F, torch_cuda, ctx, oracle):
+    """No polynomial installed -> FDFB_EBADLUT; an id out of range is latched
+    and reported by fdfb_sync; batch 0 is a no-op."""
+    torch = torch_cuda
+    ps = S.PARAM_SETS["A"]
+    K = oracle_keys("A", 0)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    ct = torch.zeros((3, ps.n + 1), dtype=torch.int32, device="cuda")
+    out = torch.zeros_like(ct)
+    ids = torch.zeros(3, dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FDFBError) as e:
+        ctx.tfhe_bootstrap(sid, ct, ids, out)
+    assert e.value.code == -6
+    ctx.tfhe_poly_setup(sid, np.zeros(ps.N, dtype=np.uint32))
+    ctx.tfhe_bootstrap(sid, ct[:0], ids[:0], out[:0])
+    ctx.tfhe_bootstrap(sid, ct, torch.tensor([0, 5, 0], dtype=torch.int32, device="cuda"), out)
+    with pytest.raises(F.FDFBError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+    ctx.sync()
+
