@@ -25,7 +25,7 @@ _lock = threading.Lock()
 
 class or_params(C.Structure):
     _fields_ = [(k, C.c_int32) for k in
-                ("n", "N", "w", "t", "log2Bg", "lg", "log2Bks", "lks", "log2Bpk", "lpk")]
+                ("n", "N", "w", "t", "log2Bg", "lg", "log2Bks", "lks", "log2Bpk", "lpk", "signed_digits")]
 
 
 class or_debug(C.Structure):
@@ -58,6 +58,7 @@ def lib():
                 "or_poly_mul_xk_signed": ([i32, vp, i64, vp], None),
                 "or_decomp_round": ([i32, i32, i32, C.c_uint64], C.c_uint64),
                 "or_decomp": ([i32, i32, i32, C.c_uint64, vp], None),
+                "or_decomp_signed": ([i32, i32, i32, C.c_uint64, vp], None),
                 "or_gadget": ([i32, i32, i32, i32], C.c_uint64),
                 "or_lwe_encrypt": ([i32, i32, vp, vp, i64, C.c_uint64, vp], None),
                 "or_lwe_phase": ([i32, i32, vp, vp], C.c_uint64),
@@ -119,7 +120,7 @@ def max_threads() -> int:
 
 def params(ps) -> or_params:
     return or_params(ps.n, ps.N, ps.w, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks,
-                     ps.log2Bpk, ps.lpk)
+                     ps.log2Bpk, ps.lpk, 1 if ps.signed_digits else 0)
 
 
 # --------------------------------------------------------------------------
@@ -151,6 +152,12 @@ def poly_mul_xk_signed(p, k: int) -> np.ndarray:
 def decomp(w: int, log2B: int, ell: int, x: int) -> np.ndarray:
     out = np.zeros(ell, dtype=np.uint64)
     lib().or_decomp(w, log2B, ell, int(x), _p(out))
+    return out
+
+
+def decomp_signed(w: int, log2B: int, ell: int, x: int) -> np.ndarray:
+    out = np.zeros(ell, dtype=np.int64)
+    lib().or_decomp_signed(w, log2B, ell, int(x), _p(out))
     return out
 
 

@@ -48,6 +48,7 @@ typedef uint8_t u8;
 typedef struct {
     int32_t n, N, w, t;
     int32_t log2Bg, lg, log2Bks, lks, log2Bpk, lpk;
+    int32_t signed_digits;  /* blind rotation decomposes into balanced digits (G21) */
 } or_params;
 
 static inline u64 wmask(int w) { return w >= 64 ? ~(u64)0 : (((u64)1 << w) - 1); }
@@ -146,6 +147,24 @@ void or_decomp(int w, int log2B, int ell, u64 x, u64* out) {
     for (int j = 0; j < ell; ++j) {
         int sh = log2B * j;
         out[j] = sh < 64 ? ((xt >> sh) & bm) : 0;
+    }
+}
+
+/* Balanced digits (reading G21) of x: the same rounded value x~, written as
+ * sum_j d_j B^{j-1} with every d_j in [-B/2, B/2): take the base-B digits
+ * from the least significant up, and whenever a digit plus the incoming carry
+ * reaches B/2, subtract B and carry 1 into the next digit.  The carry out of
+ * the top digit is dropped: B^l 2^r = 2^w vanishes mod 2^w, so
+ * sum_j d_j g_j = x~ 2^r (mod 2^w) still holds. */
+void or_decomp_signed(int w, int log2B, int ell, u64 x, i64* out) {
+    u64 xt = or_decomp_round(w, log2B, ell, x);
+    const i64 B = (i64)1 << log2B;
+    i64 carry = 0;
+    for (int j = 0; j < ell; ++j) {
+        int sh = log2B * j;
+        i64 d = (sh < 64 ? (i64)((xt >> sh) & (u64)(B - 1)) : 0) + carry;
+        carry = d >= B / 2 ? 1 : 0;
+        out[j] = d - carry * B;
     }
 }
 
@@ -299,9 +318,16 @@ void or_extprod(const or_params* P, const u64* C, const u64* d, u64* out) {
     u64* dig = (u64*)malloc(sizeof(u64) * 2 * l * N);
     u64* tmp = (u64*)malloc(sizeof(u64) * N);
     u64 digits[64];
+    i64 sdigits[64];
     for (int c = 0; c < 2; ++c)
         for (int k = 0; k < N; ++k) {
-            or_decomp(w, P->log2Bg, l, d[(size_t)c * N + k], digits);
+            if (P->signed_digits) {
+                /* a negative digit enters the ring product as its value mod 2^w */
+                or_decomp_signed(w, P->log2Bg, l, d[(size_t)c * N + k], sdigits);
+                for (int j = 0; j < l; ++j) digits[j] = (u64)sdigits[j] & m;
+            } else {
+                or_decomp(w, P->log2Bg, l, d[(size_t)c * N + k], digits);
+            }
             for (int j = 0; j < l; ++j) dig[((size_t)c * l + j) * N + k] = digits[j];
         }
     memset(out, 0, sizeof(u64) * 2 * N);

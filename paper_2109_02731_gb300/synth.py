@@ -54,6 +54,7 @@ class ParamSet:
     lpk: int
     sigma_lwe: float   # fresh LWE ciphertexts and the key-switching key
     sigma_glwe: float  # bootstrapping key and packing key
+    signed_digits: bool = False  # balanced blind-rotation digits in [-B/2, B/2)
 
     @property
     def logN(self) -> int:

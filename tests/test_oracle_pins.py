@@ -315,6 +315,85 @@ def test_blind_rotate_noise_within_lemma(oracle):
     assert var >= bound / 64
 
 
+@pytest.mark.parametrize("log2B,ell", [(2, 3), (3, 4), (4, 3), (3, 2), (6, 2)])
+def test_decomp_signed_recomposition_exhaustive_w12(oracle, log2B, ell):
+    """Balanced digits (reading G21): every digit in [-B/2, B/2), and for all
+    x in Z_{2^12} the digits recompose (mod 2^12) to the same rounded value
+    x~ 2^r as the unsigned decomposition, within 2^{r-1} of x."""
+    w = 12
+    B = 1 << log2B
+    r = max(0, w - ell * log2B)
+    g = [oracle.gadget(w, log2B, ell, j) for j in range(ell)]
+    for x in range(1 << w):
+        d = oracle.decomp_signed(w, log2B, ell, x)
+        assert all(-B // 2 <= int(v) < B // 2 for v in d), (x, d)
+        rec = sum(int(v) * gj for v, gj in zip(d, g)) % (1 << w)
+        assert rec == (oracle.decomp_round(w, log2B, ell, x) << r) % (1 << w)
+        err = (x - rec) % (1 << w)
+        err = err - (1 << w) if err >= (1 << (w - 1)) else err
+        assert abs(err) <= (1 << (r - 1) if r else 0)
+
+
+def test_decomp_signed_is_the_unique_balanced_form(oracle):
+    """Brute force at w = 6, B = 4, l = 3 (exact): the 64 digit vectors in
+    [-2, 2)^3 hit every residue of Z_64 once, and the oracle returns that
+    vector for each x."""
+    w, log2B, ell = 6, 2, 3
+    table = {}
+    for d in itertools.product(range(-2, 2), repeat=ell):
+        table[sum(v * 4 ** j for j, v in enumerate(d)) % 64] = d
+    assert len(table) == 64
+    for x in range(64):
+        assert tuple(int(v) for v in oracle.decomp_signed(w, log2B, ell, x)) == table[x]
+
+
+def test_blind_rotate_signed_noiseless_is_monomial_rotation(oracle):
+    """With balanced digits the noiseless BR still multiplies by X^{-<a, s>}
+    exactly (the digits recompose to the same value)."""
+    import dataclasses
+    ps = dataclasses.replace(S.PARAM_SETS["Z"], signed_digits=True)
+    k = _tiny_keys(oracle, ps, 3)
+    r = rng(17)
+    N = ps.N
+    for _ in range(2):
+        v = rand_words(r, ps.w, N)
+        acc = np.concatenate([v, np.zeros(N, np.uint64)])
+        ctN = r.integers(0, 2 * N, ps.n + 1).astype(np.uint64)
+        out = oracle.blind_rotate(ps, k.bsk, acc, ctN)
+        rot = -int(np.dot(ctN[1:].astype(np.int64), k.s.astype(np.int64)))
+        assert np.array_equal(oracle.rlwe_phase(ps.w, k.sk, out), oracle.poly_mul_xk(ps.w, v, rot))
+
+
+def test_blind_rotate_signed_digits_quarter_noise(oracle):
+    """Balanced digits have E[d^2] = B^2/12 against B^2/3 for digits uniform in
+    [0, B): on set A, where the key noise dominates, the BR error variance
+    drops about fourfold, and stays within a quarter of the lemma's bound."""
+    import dataclasses
+    base = S.PARAM_SETS["A"]
+    k = _tiny_keys(oracle, base, 4)
+    N = base.N
+    var = {}
+    for sgn in (False, True):
+        ps = dataclasses.replace(base, signed_digits=sgn)
+        r = rng(8)
+        errs = []
+        for _ in range(4):
+            v = rand_words(r, ps.w, N)
+            acc = np.concatenate([v, np.zeros(N, np.uint64)])
+            ctN = r.integers(0, 2 * N, ps.n + 1).astype(np.uint64)
+            out = oracle.blind_rotate(ps, k.bsk, acc, ctN)
+            rot = -int(np.dot(ctN[1:].astype(np.int64), k.s.astype(np.int64)))
+            e = (oracle.rlwe_phase(ps.w, k.sk, out) - oracle.poly_mul_xk(ps.w, v, rot)).astype(np.int64)
+            errs.append(e.astype(np.int32).astype(np.float64))
+        var[sgn] = float(np.mean(np.concatenate(errs) ** 2))
+    assert 2.5 < var[False] / var[True] < 6.0
+    B2 = (1 << base.log2Bg) ** 2
+    rb = base.w - base.lg * base.log2Bg
+    bound = (2 / 3) * base.n * N * base.lg * B2 * base.sigma_glwe ** 2 / 4 \
+        + base.n * (N * 0.5 + 1) * (4.0 ** rb) / 12 * 2
+    assert var[True] <= 1.5 * bound
+
+
 # ------------------------------------------------------------- mod switch ---
 
 def test_modswitch_rounding_and_error(oracle):
@@ -383,6 +462,28 @@ def test_fdfb_noiseless_exhaustive(oracle):
     k = _tiny_keys(oracle, ps, 0)
     t = ps.t
     fs = np.array(list(itertools.product(range(t), repeat=t)), dtype=np.int64)   # 256 x 4
+    rot = np.zeros((len(fs), 2, ps.N), dtype=np.int64)
+    for i, f in enumerate(fs):
+        rot[i, 0], rot[i, 1] = oracle.setup_polynomial(ps.N, t, f)
+    ms = np.tile(np.arange(t), len(fs))
+    ids = np.repeat(np.arange(len(fs)), t).astype(np.int32)
+    mr = S.message_randomness(ps, 0, len(ms), m=ms)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
+    for c in range(len(ms)):
+        want = (ps.delta * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
+
+
+def test_fdfb_signed_digits_noiseless(oracle):
+    """The whole FDFB with balanced blind-rotation digits, sigma = 0 and
+    exact decompositions: for all m in Z_4 and 32 functions f: Z_4 -> Z_4
+    the output phase is exactly Delta f(m)."""
+    import dataclasses
+    ps = dataclasses.replace(S.PARAM_SETS["Z"], signed_digits=True)
+    k = _tiny_keys(oracle, ps, 0)
+    t = ps.t
+    fs = np.array(list(itertools.product(range(t), repeat=t)), dtype=np.int64)[::8]
     rot = np.zeros((len(fs), 2, ps.N), dtype=np.int64)
     for i, f in enumerate(fs):
         rot[i, 0], rot[i, 1] = oracle.setup_polynomial(ps.N, t, f)
