@@ -68,6 +68,11 @@ typedef struct {
   uint32_t log2Bks, lks;   /* LWE->LWE key-switching gadget */
   uint32_t log2Bpk, lpk;   /* LWE->RLWE packing-key gadget */
   uint32_t log2Lboot, lboot;
+  /* 1: the blind rotation decomposes into balanced digits in [-B/2, B/2)
+   * (the same rounded value, carried upward; the carry out of the top digit
+   * vanishes mod q), a quarter of the digit variance of [0, B); 0: digits
+   * in [0, B).  The key switches always use [0, B). */
+  uint32_t signed_digits;
 } fdfb_params;
 
 /* Creates a context on CUDA device `device`.  *out receives the handle. */

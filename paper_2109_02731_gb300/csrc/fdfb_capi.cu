@@ -286,6 +286,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.smem_r1 = bv.br_r1;
   br.smem_exch = bv.br_ex;
   br.rep = 1;
+  br.signed_digits = (int)P.signed_digits;
   {
     StageTimer tm(tctx, 0, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -530,6 +531,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   if (P.lks < 1 || P.lks > 64 || P.log2Bks < 1 || P.log2Bks > 16) return FDFB_EINVAL;
   if (P.lpk < 1 || P.lpk > 64 || P.log2Bpk < 1 || P.log2Bpk > 16) return FDFB_EINVAL;
   if (P.lboot != 1 || P.log2Lboot != (uint32_t)ilog2(P.t)) return FDFB_EINVAL;
+  if (P.signed_digits > 1) return FDFB_EINVAL;
   const int w = (int)P.log2q, L = ilog2(P.N);
   const Ops* ops0 = find_ops(L, w, 0);
   if (!ops0) return FDFB_EINVAL;
@@ -559,6 +561,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
     auto v = std::make_unique<Variant>();
     v->ops = ops;
     if ((int)P.log2Bg > ops->max_log2B) continue;  // digits too wide for this variant
+    if (P.signed_digits && !ops->has_signed) continue;  // not built with balanced digits
     if (ops->family && !host::lift_is_exact(ops->P, br_max, ops->family)) continue;
     if (ops->key_halves == 2 &&
         !host::lift_is_exact(ops->P, 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * ldexpl(1.0L, 31),
@@ -816,6 +819,7 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
   br.smem_r1 = bv.br_r1;
   br.smem_exch = bv.br_ex;
   br.rep = 1;
+  br.signed_digits = (int)P.signed_digits;
   {
     StageTimer tm(ctx, 3, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -1137,6 +1141,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.smem_r1 = v.br_r1;
     br.smem_exch = v.br_ex;
     br.rep = 1;
+    br.signed_digits = (int)st->prm.signed_digits;
     float ms_v = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, s);

@@ -6,18 +6,28 @@ namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1>
+          int KH = 1, bool SGV = false>
 struct Inst {
+  // SGV: also build the blind rotation with balanced digits (parameter sets
+  // with signed_digits only use variants that have it)
+  template <bool SG>
+  static constexpr auto kernel() { return blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH, SG>; }
   using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
-    return cudaFuncSetAttribute(blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || !SGV) return e;
+    return cudaFuncSetAttribute(kernel<SGV>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static cudaError_t br(const BRParams& prm, int64_t batch, size_t smem, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
-    blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH><<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    if (prm.signed_digits) {
+      if (!SGV) return cudaErrorInvalidValue;
+      kernel<SGV>()<<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    } else {
+      kernel<false>()<<<(unsigned)batch, THREADS, smem, st>>>(prm);
+    }
     return cudaGetLastError();
   }
   static cudaError_t pubmux(const PubMuxParams& prm, int64_t batch, cudaStream_t st) {
@@ -56,8 +66,7 @@ struct Inst {
   }
   static int br_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH>, THREADS, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel<false>(), THREADS, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -65,7 +74,7 @@ struct Inst {
   }
   static Ops ops() {
     return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
-               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm, KH};
+               &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm, KH, SGV ? 1 : 0};
   }
 };
 

@@ -4,18 +4,20 @@
 #include "fdfb_inst.cuh"
 
 namespace fdfb {
+// Variants whose last template argument is true are also built with balanced
+// blind-rotation digits (the only ones a set with signed_digits uses).
 const Ops* ops_n10(int w, int variant) {
-  static const Ops a0 = Inst<10, 4, 2, uint32_t, uint16_t>::ops();
+  static const Ops a0 = Inst<10, 4, 2, uint32_t, uint16_t, false, br_min_blocks(2 << (10 - 4)), 1, false, false, 1, true>::ops();
   static const Ops a1 = Inst<10, 5, 2, uint32_t, uint8_t>::ops();
   static const Ops a2 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168)>::ops();
   static const Ops a3 = Inst<10, 4, 2, uint32_t, uint8_t, false, br_blocks_for_regs(2 << (10 - 4), 128), 2>::ops();
   static const Ops a4 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2>::ops();
   // lazy prime family (variants 5-7): a4 and a3 with unreduced forward transforms,
   // and a5 with ping-pong exchange buffers
-  static const Ops a5 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true>::ops();
+  static const Ops a5 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, false, 1, true>::ops();
   static const Ops a6 = Inst<10, 4, 2, uint32_t, uint8_t, false, br_blocks_for_regs(2 << (10 - 4), 128), 2, true>::ops();
-  static const Ops a7 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, true>::ops();
-  static const Ops b0 = Inst<10, 4, 3, uint64_t, uint16_t>::ops();
+  static const Ops a7 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, true, 1, true>::ops();
+  static const Ops b0 = Inst<10, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (10 - 4)), 1, false, false, 1, true>::ops();
   static const Ops b1 = Inst<10, 5, 3, uint64_t, uint16_t>::ops();
   static const Ops b2 = Inst<10, 4, 3, uint64_t, uint16_t, true>::ops();
   static const Ops b3 = Inst<10, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (10 - 4)), 2>::ops();

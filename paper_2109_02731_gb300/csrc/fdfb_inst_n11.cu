@@ -4,22 +4,24 @@
 #include "fdfb_inst.cuh"
 
 namespace fdfb {
+// Variants whose last template argument is true are also built with balanced
+// blind-rotation digits (the only ones a set with signed_digits uses).
 const Ops* ops_n11(int w, int variant) {
-  static const Ops a0 = Inst<11, 4, 2, uint32_t, uint16_t>::ops();
+  static const Ops a0 = Inst<11, 4, 2, uint32_t, uint16_t, false, br_min_blocks(2 << (11 - 4)), 1, false, false, 1, true>::ops();
   static const Ops a1 = Inst<11, 5, 2, uint32_t, uint8_t>::ops();
   static const Ops a2 = Inst<11, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (11 - 4), 168)>::ops();
   static const Ops a3 = Inst<11, 4, 2, uint32_t, uint8_t, false, br_blocks_for_regs(2 << (11 - 4), 128), 2>::ops();
   static const Ops a4 = Inst<11, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (11 - 4), 168), 2>::ops();
   // lazy prime family (variant 5): a4 with unreduced forward transforms
   static const Ops a5 = Inst<11, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (11 - 4), 168), 2, true>::ops();
-  static const Ops b0 = Inst<11, 4, 3, uint64_t, uint16_t>::ops();
+  static const Ops b0 = Inst<11, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (11 - 4)), 1, false, false, 1, true>::ops();
   static const Ops b1 = Inst<11, 5, 3, uint64_t, uint16_t>::ops();
   static const Ops b2 = Inst<11, 4, 3, uint64_t, uint16_t, true>::ops();
   static const Ops b3 = Inst<11, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (11 - 4)), 2>::ops();
   static const Ops b4 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2>::ops();
   // b3 and b4 with ping-pong exchange buffers
   static const Ops b5 = Inst<11, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (11 - 4)), 2, false, true>::ops();
-  static const Ops b6 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, true>::ops();
+  static const Ops b6 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, true, 1, true>::ops();
   // 64-bit key words split into 32-bit halves over two primes (two groups of threads)
   static const Ops b7 = Inst<11, 4, 2, uint64_t, uint16_t, false, 1, 2, false, true, 2>::ops();
   static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5};

@@ -3,11 +3,13 @@
 #include "fdfb_inst.cuh"
 
 namespace fdfb {
+// Variants whose last template argument is true are also built with balanced
+// blind-rotation digits (the only ones a set with signed_digits uses).
 const Ops* ops_n9(int w, int variant) {
-  static const Ops a0 = Inst<9, 4, 2, uint32_t, uint16_t>::ops();
+  static const Ops a0 = Inst<9, 4, 2, uint32_t, uint16_t, false, br_min_blocks(2 << (9 - 4)), 1, false, false, 1, true>::ops();
   // lazy prime family, paired transforms with 64-bit sums
-  static const Ops a1 = Inst<9, 4, 2, uint32_t, uint16_t, true, br_min_blocks(2 << (9 - 4)), 2, true>::ops();
-  static const Ops b0 = Inst<9, 4, 3, uint64_t, uint16_t>::ops();
+  static const Ops a1 = Inst<9, 4, 2, uint32_t, uint16_t, true, br_min_blocks(2 << (9 - 4)), 2, true, false, 1, true>::ops();
+  static const Ops b0 = Inst<9, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (9 - 4)), 1, false, false, 1, true>::ops();
   if (w == 32) {
     switch (variant) {
       case 0: return &a0;

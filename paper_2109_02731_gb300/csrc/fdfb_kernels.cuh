@@ -201,6 +201,7 @@ struct BRParams {
   int sign_mode;
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
+  int signed_digits;            // balanced digits (checked against the kernel's SG)
 };
 
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1>
@@ -272,9 +273,10 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // 32-bit halves, K = K_lo + 2^32 K_hi; both halves share the digits' forward
 // transforms, and each half's product sum (at most 2l N (B-1) 2^31) is lifted
 // exactly from two primes: acc += X_lo + 2^32 X_hi mod 2^64.
+// SG: balanced digits in [-B/2, B/2) (a parameter set's signed_digits).
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1>
+          int KH = 1, bool SG = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -335,6 +337,7 @@ blind_rotate_kernel(const BRParams prm) {
   const int rt = prm.rtrunc;
   const W half_rt = rt ? ((W)1 << (rt - 1)) : (W)0;
   const uint32_t dmask = (1u << log2Bg) - 1;
+  const uint32_t halfB = 1u << (log2Bg - 1);
   const int R = 2 * lg;
 
   // Each group's key block of a step is contiguous (R rows x 2 columns x KH
@@ -359,9 +362,22 @@ blind_rotate_kernel(const BRParams prm) {
       const W d = (W)(rv - ac[j]);
       const W xt = (W)((W)(d + half_rt) >> rt);
       DT* dp = dig + c * lg * N + j;
+      if constexpr (SG) {
+        // balanced digits: a digit (plus the carry) of at least B/2 becomes
+        // digit - B with a carry into the next one; stored as two's complement
+        uint32_t carry = 0;
 #pragma unroll
-      for (int l = 0; l < 4; ++l)  // lg <= 4
-        if (l < lg) dp[l * N] = (DT)((uint32_t)(xt >> (l * log2Bg)) & dmask);
+        for (int l = 0; l < 4; ++l)  // lg <= 4
+          if (l < lg) {
+            const uint32_t dv = ((uint32_t)(xt >> (l * log2Bg)) & dmask) + carry;
+            carry = dv >= halfB ? 1u : 0u;
+            dp[l * N] = (DT)(dv - (carry << log2Bg));
+          }
+      } else {
+#pragma unroll
+        for (int l = 0; l < 4; ++l)  // lg <= 4
+          if (l < lg) dp[l * N] = (DT)((uint32_t)(xt >> (l * log2Bg)) & dmask);
+      }
     }
     __syncthreads();
 
@@ -384,7 +400,17 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
       for (int m = 0; m < M; ++m)
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[m][k] = dig[(r0 + m) * N + Y::j_of(0, t, k)];
+        for (int k = 0; k < E; ++k) {
+          const uint32_t dv = dig[(r0 + m) * N + Y::j_of(0, t, k)];
+          if constexpr (SG) {
+            // a negative balanced digit enters the transform as d + p
+            using SDT = typename std::make_signed<DT>::type;
+            const int sd = (int)(SDT)dv;
+            v[m][k] = sd < 0 ? (uint32_t)(sd + (int)p) : (uint32_t)sd;
+          } else {
+            v[m][k] = dv;
+          }
+        }
       ntt_fwd_m<L, EL, 0, M, XW, LZ, PP>(v, t, twf, p, xb, bar, z);
       if constexpr (WIDE && !LZ) {
 #pragma unroll

@@ -21,6 +21,7 @@ struct Ops {
   int family;  // NTT prime family of the blind rotation (0: 30-bit primes, 1: lazy family)
   int (*br_blocks_per_sm)(size_t smem);  // resident blind-rotation CTAs per SM
   int key_halves;  // 2: 64-bit key words split into 32-bit halves over two primes
+  int has_signed;  // also built with balanced blind-rotation digits
 };
 
 // Returns the launcher table of register-layout variant `variant` for

@@ -744,3 +744,32 @@ def test_tfhe_bootstrap_errors(F, torch_cuda, ctx, oracle):
     assert e.value.code == -6
     ctx.sync()
 
+
+# ---------------------------------------------------------- balanced digits --
+
+def test_signed_digits_match_oracle(F, torch_cuda, ctx, oracle):
+    """Balanced blind-rotation digits (signed_digits = 1): sets A and B, every
+    layout variant bit for bit equal, and equal to the oracle (A: all 30
+    ciphertexts; B: 3 of 40)."""
+    import dataclasses
+    for name, seed, batch, sample in (("A", 0, 30, range(30)), ("B", 1, 40, (0, 1, 39))):
+        ps = dataclasses.replace(S.PARAM_SETS[name], name=name + "s", signed_digits=True)
+        K = oracle_keys(name, seed)  # the keys do not depend on the digit form
+        sid = ctx.register(ps)
+        ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+        fs, rot = luts(name, seed, 2)
+        for f in fs:
+            ctx.lut_setup(sid, f)
+        ids = S.lut_assignment(seed, batch, 2, "uniform", group=60)
+        mr, cts = fresh_cts(name, seed, batch, K, group=60)
+        outs = []
+        for v in range(ctx.variant_info(sid)[1]):
+            ctx.set_variant(sid, v)
+            out, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+            outs.append(out)
+        for v in range(1, len(outs)):
+            assert np.array_equal(outs[v], outs[0]), (name, v)
+        for c in sample:
+            want = oracle.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
+            assert np.array_equal(outs[0][c], want), (name, c)
+
