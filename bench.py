@@ -53,6 +53,15 @@ def workload_desc(name: str):
     return wl, g, ps
 
 
+# DRAM bytes (read + write) of one blind-rotation launch over the whole batch,
+# from the ncu captures summarised under profiles/ (set, variant, batch); the
+# bench reports them only for that configuration of the current kernel.
+KERNEL_TRAFFIC = {
+    ("B", 7, 1024): 86.26e6,    # profiles/blind_rotate_tfhe_scale.md
+    ("D", 6, 1000): 3.19754e9,  # profiles/blind_rotate_n2048.md
+}
+
+
 def br_algorithmic_slots(ps, batch: int) -> float:
     """Integer-multiplier issue slots the blind rotation needs per launch (one
     BR over `batch` ciphertexts), counting only the method's modular products:
@@ -551,6 +560,14 @@ def main():
     stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
     h2d, d2h = job.io_bytes()
     ps0 = job.groups[0]["ps"]
+    traffic, traffic_src = None, None
+    if len(job.groups) == 1 and not job.wl.mlp_layers and job.groups[0]["k"] == 1:
+        g0 = job.groups[0]
+        key = (ps0.name, ctx.variant_info(g0["sid"])[0], g0["batch"])
+        if key in KERNEL_TRAFFIC:
+            traffic = KERNEL_TRAFFIC[key]
+            traffic_src = ("dram bytes per unchunked blind-rotation launch over the batch, "
+                           f"ncu capture of set {key[0]} variant {key[1]}, {key[2]} ciphertexts")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -561,7 +578,8 @@ def main():
         "decrypt_ok": decrypt_ok,
         "roofline": {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
                      "unit": "T IMAD slots/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
                      "br_ms_per_step": br_ms / args.steps, "launches": br_n,
                      "slots_per_step": job.slots_per_step()},
         "stage_share": stage_share,
