@@ -84,8 +84,14 @@ int fdfb_destroy(fdfb_ctx* ctx);
 
 /* Registers a parameter set; *set_id_out receives its id.  Fails with
  * FDFB_EINVAL for unsupported shapes: N not in {256, 512, 1024, 2048, 4096},
- * n > 4096, lg > 4, or a negacyclic product whose exact value could exceed
- * what the library's primes lift exactly. */
+ * n > 4096, lg > 4, signed_digits > 1, or a negacyclic product whose exact
+ * value could exceed what the 30-bit primes lift exactly (2l N (B-1) q/2 for
+ * the blind rotation, N (t-1) q for PubMux).  Registration also builds the
+ * set's blind-rotation variants (fdfb_autotune): the layouts whose shared
+ * memory fits the device, whose digit width holds B, that are built with
+ * balanced digits if the set asks for them, and -- for the lazy 28-bit prime
+ * family and the split-key layouts of q = 2^64 -- whose own primes lift the
+ * products exactly. */
 int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out);
 
 /* Size in words of each key in its canonical layout (what keys_upload reads):

@@ -179,8 +179,9 @@ __device__ __forceinline__ uint32_t modswitch_2n(W x) {
 
 // ---------------------------------------------------------------------------
 // Blind rotation (appendix figure "Blind Rotation and its setup", u = {1}):
-// one CTA per ciphertext, P thread groups of G threads, group g computing
-// every product modulo prime g.  For i = 1..n:
+// one CTA per item (a ciphertext, or an (input, table) pair when rep > 1), P
+// thread groups of G threads, group g computing every product modulo prime g.
+// For i = 1..n:
 //   d = acc * X^{-a_i} - acc;  D = Decomp(d) (2 lg digit polynomials);
 //   acc += sum_r D_r * bsk[i][r]    (CMux = extProd(C, g - h) + h)
 // The digits are transformed on the fly; the key rows are pre-transformed
@@ -194,14 +195,14 @@ struct BRParams {
   const void* ct;         // [batch / rep][n+1] words (input LWE, modulus q)
   const void* acc0;       // function mode: [batch][2N] words; sign mode: nullptr
   void* lwe_out;          // [batch][N+1] words: SampleExtract(acc, 0) (+ Delta/2 in sign mode)
-  uint32_t* ctN_out;      // optional [batch][n+1]: ModSwitch(ct, q, 2N)
+  uint32_t* ctN_out;      // optional [batch][n+1]: ModSwitch(ct, q, 2N) (rep = 1 only)
   int n, lg, log2Bg, rtrunc;
   int64_t batch;
   uint64_t delta_half;
   int sign_mode;
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
-  int signed_digits;            // balanced digits (checked against the kernel's SG)
+  int signed_digits;            // balanced digits: the launcher picks the kernel built with SG
 };
 
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1>
