@@ -226,8 +226,12 @@ def _big_workload(F, torch_cuda, ctx, oracle, name, batch, n_luts, seed, sample)
     fs, rot = luts(name, seed, n_luts)
     ids = S.lut_assignment(seed, batch, n_luts, "uniform")
     mr, cts = fresh_cts(name, seed, batch, K)
-    out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
-    check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, sample)
+    # the configuration the benchmark times: autotuned layout and chunk count
+    ctx.autotune(sid, batch)
+    out_dbg, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
+    check_against_oracle(oracle, ps, K, rot, cts, ids, out_dbg, dbg, sample)
+    out, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+    assert np.array_equal(out, out_dbg)
     # every output decrypts to f(m): decryption on the GPU, checked on the host
     dev_s = torch_cuda.tensor(K.s, device="cuda")
     out_d = F.to_device_words(ps, out)
@@ -242,7 +246,9 @@ def _big_workload(F, torch_cuda, ctx, oracle, name, batch, n_luts, seed, sample)
 @pytest.mark.slow
 def test_fdfb_set_D_full_batch(F, torch_cuda, ctx, oracle):
     """Set D (N = 2048, q = 2^64, t = 32) at the mixed workload's batch of
-    1000: sampled bit-exact parity, every output decrypts correctly."""
+    1000, in the autotuned layout and chunking the benchmark times: sampled
+    bit-exact parity of every stage, chunked call = single pipeline, every
+    output decrypts correctly."""
     _big_workload(F, torch_cuda, ctx, oracle, "D", 1000, 4, 3, [0, 999])
 
 
@@ -433,6 +439,7 @@ def test_mlp_workload_full_size_decrypts(F, torch_cuda, ctx, oracle):
     ctx.keys_generate(sid, kr)
     x, Ws = S.mlp_inputs_and_weights(wl.seed, wl.mlp_layers, wl.mlp_inputs)
     net = mlp.EncryptedMLP(ctx, sid, Ws)
+    ctx.autotune(sid, wl.mlp_inputs * wl.mlp_layers[1])  # as the benchmark does
     mr = S.message_randomness(ps, wl.seed, x.size, m=x.reshape(-1))
     d = "cuda"
     ct = torch_cuda.empty((x.size, ps.n + 1), dtype=torch_cuda.int64, device=d)
