@@ -427,8 +427,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
                     help="use this blind-rotation layout variant instead of autotuning")
-    ap.add_argument("--plain", action="store_true",
-                    help="also time the plain path: one ciphertext per bootstrap call")
+    ap.add_argument("--no-plain", dest="plain", action="store_false",
+                    help="skip timing the plain path (one ciphertext per bootstrap call, rank 0)")
+    ap.add_argument("--plain", dest="plain", action="store_true", help=argparse.SUPPRESS)
+    ap.set_defaults(plain=True)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -532,7 +534,7 @@ def main():
         g = job.groups[0]
         one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()
         ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
-        barrier()
+        torch.cuda.synchronize()  # rank 0 only: no collective here
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for _ in range(reps):
