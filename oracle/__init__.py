@@ -25,7 +25,8 @@ _lock = threading.Lock()
 
 class or_params(C.Structure):
     _fields_ = [(k, C.c_int32) for k in
-                ("n", "N", "w", "t", "log2Bg", "lg", "log2Bks", "lks", "log2Bpk", "lpk", "signed_digits")]
+                ("n", "N", "w", "t", "log2Bg", "lg", "log2Bks", "lks", "log2Bpk", "lpk", "signed_digits",
+                 "t_out")]
 
 
 class or_debug(C.Structure):
@@ -120,7 +121,7 @@ def max_threads() -> int:
 
 def params(ps) -> or_params:
     return or_params(ps.n, ps.N, ps.w, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks,
-                     ps.log2Bpk, ps.lpk, 1 if ps.signed_digits else 0)
+                     ps.log2Bpk, ps.lpk, 1 if ps.signed_digits else 0, ps.t_out)
 
 
 # --------------------------------------------------------------------------

@@ -49,7 +49,12 @@ typedef struct {
     int32_t n, N, w, t;
     int32_t log2Bg, lg, log2Bks, lks, log2Bpk, lpk;
     int32_t signed_digits;  /* blind rotation decomposes into balanced digits (G21) */
+    int32_t t_out;          /* output plaintext modulus t' (0: t' = t), G13 */
 } or_params;
+
+/* The output space Z_t' of f: Z_t -> Z_t' (footnote of Section 1.1: the
+ * same method with a different message scaling). */
+static int out_mod(const or_params* P) { return P->t_out > 0 ? P->t_out : P->t; }
 
 static inline u64 wmask(int w) { return w >= 64 ? ~(u64)0 : (((u64)1 << w) - 1); }
 
@@ -482,9 +487,9 @@ typedef struct {
  * bootstrap's accumulators are reused for the next function). */
 static void or_fdfb_sign_part(const or_params* P, const u64* bsk, const u64* pk, const u64* ct,
                               u64* ctN, u64* cR, const or_debug* dbg) {
-    const int n = P->n, N = P->N, w = P->w, t = P->t;
+    const int n = P->n, N = P->N, w = P->w;
     const u64 m = wmask(w);
-    const u64 delta = delta_of(w, t);
+    const u64 delta = delta_of(w, out_mod(P));  /* Delta' = q / t' scales the sign LWE */
     int logN = 0;
     while ((1 << logN) < N) ++logN;
 
@@ -520,7 +525,7 @@ static void or_fdfb_sign_part(const or_params* P, const u64* bsk, const u64* pk,
 static void or_fdfb_function_part(const or_params* P, const u64* bsk, const u64* ksk,
                                   const i64* rotP0, const i64* rotP1, const u64* ctN,
                                   const u64* cR, u64* out, const or_debug* dbg) {
-    const int n = P->n, N = P->N, w = P->w, t = P->t;
+    const int n = P->n, N = P->N, w = P->w, t = out_mod(P);
     const i64 bN = (i64)ctN[0];
 
     u64* acc = (u64*)malloc(sizeof(u64) * 2 * N);

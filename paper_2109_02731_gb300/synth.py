@@ -55,6 +55,7 @@ class ParamSet:
     sigma_lwe: float   # fresh LWE ciphertexts and the key-switching key
     sigma_glwe: float  # bootstrapping key and packing key
     signed_digits: bool = False  # balanced blind-rotation digits in [-B/2, B/2)
+    t_out: int = 0               # output plaintext modulus t' of f: Z_t -> Z_t' (0: t' = t)
 
     @property
     def logN(self) -> int:
@@ -67,6 +68,15 @@ class ParamSet:
     @property
     def delta(self) -> int:
         return (1 << self.w) // self.t
+
+    @property
+    def tout(self) -> int:
+        """Output plaintext modulus t' (f: Z_t -> Z_t')."""
+        return self.t_out or self.t
+
+    @property
+    def delta_out(self) -> int:
+        return (1 << self.w) // self.tout
 
 
 # Sets A-C come straight from the workload list; D and the bold choices of

@@ -497,6 +497,33 @@ def test_fdfb_signed_digits_noiseless(oracle):
         assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
 
 
+@pytest.mark.parametrize("t_out", [2, 8, 16])
+def test_fdfb_other_output_modulus_noiseless(oracle, t_out):
+    """f: Z_t -> Z_t' with t' != t (Section 1.1, footnote: a different message
+    scaling): sigma = 0, exact decompositions, t = 4; for all m in Z_4 and
+    every function (t' = 2: all 16) or 48 seeded ones (t' = 8, 16), the output
+    phase is exactly Delta' f(m) with Delta' = q / t'."""
+    import dataclasses
+    ps = dataclasses.replace(S.PARAM_SETS["Z"], t_out=t_out)
+    k = _tiny_keys(oracle, ps, 0)
+    t = ps.t
+    if t_out ** t <= 64:
+        fs = np.array(list(itertools.product(range(t_out), repeat=t)), dtype=np.int64)
+    else:
+        fs = np.random.default_rng(t_out).integers(0, t_out, size=(48, t))
+    rot = np.zeros((len(fs), 2, ps.N), dtype=np.int64)
+    for i, f in enumerate(fs):
+        rot[i, 0], rot[i, 1] = oracle.setup_polynomial(ps.N, t, f)
+    ms = np.tile(np.arange(t), len(fs))
+    ids = np.repeat(np.arange(len(fs)), t).astype(np.int32)
+    mr = S.message_randomness(ps, 0, len(ms), m=ms)
+    cts = oracle.encrypt_messages(ps, k.s, mr)
+    outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
+    for c in range(len(ms)):
+        want = (ps.delta_out * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
+
+
 def test_fdfb_multi_noiseless_exhaustive(oracle):
     """Several functions of one input (Section 'Application of Functional
     Bootstrapping': the sign accumulators are reused): at sigma = 0 with exact
