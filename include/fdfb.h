@@ -73,6 +73,12 @@ typedef struct {
    * vanishes mod q), a quarter of the digit variance of [0, B); 0: digits
    * in [0, B).  The key switches always use [0, B). */
   uint32_t signed_digits;
+  /* Output plaintext modulus t' of f: Z_t -> Z_t' (Section 1.1, footnote:
+   * the same method with a different message scaling); 0 means t' = t.  A
+   * power of two, 2 <= t' <= 2^15.  The sign LWE is scaled by Delta'/2 and
+   * PubMux by Delta' = q / t', table entries lie in Z_t', and the bootstrap's
+   * outputs encrypt Delta' f(m). */
+  uint32_t t_out;
 } fdfb_params;
 
 /* Creates a context on CUDA device `device`.  *out receives the handle. */
@@ -141,7 +147,7 @@ int fdfb_keys_download(fdfb_ctx* ctx, int set_id, void* bsk, void* pk, void* ksk
  * f(m), unscaled) and builds its rotation polynomials with SetupPolynomial
  * (figure "functional-bootstrapping", right: m ascending, e ascending, later
  * writes win).  *lut_id_out receives the id, dense from 0 per parameter set.
- * FDFB_EBADLUT if an entry is >= t. */
+ * FDFB_EBADLUT if an entry is >= t' (the output modulus, = t by default). */
 int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out);
 
 /* Reads back the rotation polynomials of a table: p0, p1 host int32[N]. */
@@ -262,8 +268,10 @@ int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, 
 int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,
                      const int64_t* m, int64_t count, void* ct_out, void* cuda_stream);
 
-/* LWE decryption round(t * (b - <a, s>) / q) mod t, round half up
- * (device pointers): s uint8[n]; ct [count][n+1]; m_out int32[count]. */
+/* LWE decryption round(t' * (b - <a, s>) / q) mod t', round half up, in the
+ * bootstrap's output space Z_t' (t' = t unless the set's t_out says
+ * otherwise) (device pointers): s uint8[n]; ct [count][n+1]; m_out
+ * int32[count]. */
 int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct, int64_t count,
                      int32_t* m_out, void* cuda_stream);
 

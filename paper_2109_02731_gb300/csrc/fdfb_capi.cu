@@ -73,7 +73,7 @@ struct Variant {
 
 struct SetState {
   fdfb_params prm{};
-  int w = 0, L = 0, logt = 0;
+  int w = 0, L = 0, logt = 0, tout = 0, logtout = 0;  // tout: output plaintext modulus t'
   std::vector<std::unique_ptr<Variant>> var;  // var[0] also serves key generation and PubMux
   int cur = 0;                                // variant used by the blind rotations
   DevBuf bsk;       // canonical [n][2 lg][2][N] words
@@ -265,7 +265,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
     if (dbg->accF) accF = dbg->accF;
     if (dbg->cQ) cQ = dbg->cQ;
   }
-  const uint64_t delta = (uint64_t)1 << (st.w - st.logt);
+  const uint64_t delta = (uint64_t)1 << (st.w - st.logtout);  // Delta' = q / t'
 
   // Steps 1-8: ModSwitch, sign accumulator, BlindRotate, SampleExtract + Delta/2.
   Variant& bv = st.br();
@@ -317,7 +317,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   pm.n_luts = st.n_luts;
   pm.accF = accF;
   pm.n = P.n;
-  pm.t = P.t;
+  pm.t = st.tout;
   pm.delta = delta;
   pm.err = ctx->d_err;
   {
@@ -532,6 +532,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   if (P.lpk < 1 || P.lpk > 64 || P.log2Bpk < 1 || P.log2Bpk > 16) return FDFB_EINVAL;
   if (P.lboot != 1 || P.log2Lboot != (uint32_t)ilog2(P.t)) return FDFB_EINVAL;
   if (P.signed_digits > 1) return FDFB_EINVAL;
+  if (P.t_out && (!is_pow2(P.t_out) || P.t_out < 2 || P.t_out > (1u << 15))) return FDFB_EINVAL;
   const int w = (int)P.log2q, L = ilog2(P.N);
   const Ops* ops0 = find_ops(L, w, 0);
   if (!ops0) return FDFB_EINVAL;
@@ -540,7 +541,7 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   // lazy prime family are kept below only where the blind rotation stays exact.
   const long double q = ldexpl(1.0L, w);
   const long double br_max = 2.0L * P.lg * P.N * (ldexpl(1.0L, P.log2Bg) - 1) * (q / 2);
-  const long double pm_max = (long double)P.N * (P.t - 1) * q;
+  const long double pm_max = (long double)P.N * ((P.t_out ? P.t_out : P.t) - 1) * q;
   const long double enc_max = (long double)P.N * q;
   if (!host::lift_is_exact(ops0->P, br_max) || !host::lift_is_exact(ops0->P, pm_max) ||
       !host::lift_is_exact(ops0->P, enc_max))
@@ -553,6 +554,8 @@ int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out)
   st->w = w;
   st->L = L;
   st->logt = ilog2(P.t);
+  st->tout = P.t_out ? (int)P.t_out : (int)P.t;
+  st->logtout = ilog2((uint32_t)st->tout);
   int max_smem = 0;
   FD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
   for (int vi = 0;; ++vi) {
@@ -736,7 +739,7 @@ int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out
   if (!st || !f || !lut_id_out) return FDFB_EINVAL;
   const int N = (int)st->prm.N, t = (int)st->prm.t;
   for (int m = 0; m < t; ++m)
-    if (f[m] >= (uint32_t)t) return FDFB_EBADLUT;
+    if (f[m] >= (uint32_t)st->tout) return FDFB_EBADLUT;  // entries lie in the output space Z_t'
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
   const size_t off = st->luts_host.size();
@@ -1008,10 +1011,10 @@ int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct
   cudaStream_t cs = as_stream(cuda_stream);
   if (st->w == 32)
     lwe_decrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)ct, count,
-                                                         (int)st->prm.n, st->logt, m_out);
+                                                         (int)st->prm.n, st->logtout, m_out);
   else
     lwe_decrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)ct, count,
-                                                         (int)st->prm.n, st->logt, m_out);
+                                                         (int)st->prm.n, st->logtout, m_out);
   return cuda_err(cudaGetLastError());
 }
 
@@ -1136,7 +1139,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.log2Bg = st->prm.log2Bg;
     br.rtrunc = trunc_bits(st->w, st->prm.log2Bg, st->prm.lg);
     br.batch = batch;
-    br.delta_half = ((uint64_t)1 << (st->w - st->logt)) / 2;
+    br.delta_half = ((uint64_t)1 << (st->w - st->logtout)) / 2;
     br.sign_mode = 1;
     br.smem_r1 = v.br_r1;
     br.smem_exch = v.br_ex;

@@ -41,7 +41,8 @@ class FDFBError(RuntimeError):
 
 class fdfb_params(C.Structure):
     _fields_ = [(k, C.c_uint32) for k in ("n", "N", "k", "log2q", "t", "log2Bg", "lg", "log2Bks",
-                                          "lks", "log2Bpk", "lpk", "log2Lboot", "lboot", "signed_digits")]
+                                          "lks", "log2Bpk", "lpk", "log2Lboot", "lboot", "signed_digits",
+                                          "t_out")]
 
 
 class fdfb_keygen_inputs(C.Structure):
@@ -131,7 +132,7 @@ def _check(rc: int, what: str) -> None:
 
 def params_struct(ps: ParamSet) -> fdfb_params:
     return fdfb_params(ps.n, ps.N, 1, ps.w, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks, ps.log2Bpk,
-                       ps.lpk, int(ps.t).bit_length() - 1, 1, 1 if ps.signed_digits else 0)
+                       ps.lpk, int(ps.t).bit_length() - 1, 1, 1 if ps.signed_digits else 0, ps.t_out)
 
 
 def key_words(ps: ParamSet, which: int) -> int:

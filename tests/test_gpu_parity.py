@@ -780,3 +780,32 @@ def test_signed_digits_match_oracle(F, torch_cuda, ctx, oracle):
             want = oracle.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
             assert np.array_equal(outs[0][c], want), (name, c)
 
+
+# ------------------------------------------------------ output modulus t' --
+
+@pytest.mark.parametrize("t_out", [2, 16])
+def test_other_output_modulus_matches_oracle(F, torch_cuda, ctx, oracle, t_out):
+    """f: Z_4 -> Z_t' (noiseless set Z with t_out = t'): the GPU equals the
+    oracle bit for bit, and every output decrypts (in Z_t') to f(m)."""
+    import dataclasses
+    torch = torch_cuda
+    ps = dataclasses.replace(S.PARAM_SETS["Z"], name=f"Z{t_out}", t_out=t_out)
+    K = oracle_keys("Z", 0)  # keys do not depend on the plaintext moduli
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    rng = np.random.default_rng(40 + t_out)
+    fs = rng.integers(0, t_out, size=(6, ps.t))
+    rot = np.stack([np.stack(oracle.setup_polynomial(ps.N, ps.t, f)) for f in fs])
+    assert [ctx.lut_setup(sid, [int(v) for v in f]) for f in fs] == list(range(6))
+    ids = rng.integers(0, 6, size=48).astype(np.int32)
+    mr, cts = fresh_cts("Z", 0, 48, K, group=70)
+    out, _ = run_gpu(F, torch, ctx, sid, ps, cts, ids, debug=False)
+    want = oracle.fdfb_batch(dataclasses.replace(ps), K, rot, ids, cts)
+    assert np.array_equal(out, want)
+    m_d = torch.empty(48, dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, torch.tensor(K.s, device="cuda"), F.to_device_words(ps, out), m_d)
+    ctx.sync()
+    assert m_d.cpu().numpy().tolist() == [int(fs[i][m]) for i, m in zip(ids, mr.m)]
+    with pytest.raises(F.FDFBError):
+        ctx.lut_setup(sid, [t_out, 0, 0, 0])
+
