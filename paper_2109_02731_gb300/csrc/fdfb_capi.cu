@@ -99,6 +99,7 @@ constexpr int kStages = 6;  // 5: union of all blind-rotation launches (computed
 
 struct fdfb_ctx {
   int device = 0;
+  int sms = 0;  // streaming multiprocessors of the device
   std::vector<std::unique_ptr<SetState>> sets;
   int* d_err = nullptr;
   std::mutex mu;
@@ -210,6 +211,36 @@ int ensure_scratch(SetState& st, int64_t batch, int k = 1) {
   return FDFB_OK;
 }
 
+// Key switching out[m] = (b_m, 0..) - sum_{i,j} Decomp(a_{m,i})_j key[i][j]
+// of `batch` LWE samples of dimension n_in (figure "Key switching algorithm
+// and its setup").  The reduction is split over enough CTAs to give every SM
+// two when the output tiles alone would leave SMs idle; the split parts are
+// added atomically into a zeroed output.
+int launch_keyswitch(const fdfb_ctx* ctx, int w, const void* in, int64_t batch, int n_in,
+                     const void* key, int ell, int log2B, int rt, int out_len, void* out,
+                     cudaStream_t s) {
+  if (batch <= 0) return FDFB_OK;
+  const int64_t tiles = (int64_t)((out_len + KS_BN - 1) / KS_BN) * ((batch + KS_BM - 1) / KS_BM);
+  const int kt = (n_in * ell + KS_BK - 1) / KS_BK;
+  int64_t split = (2 * (int64_t)ctx->sms + tiles - 1) / tiles;
+  if (split > kt / 4) split = kt / 4;  // keep at least four reduction steps per slice
+  if (split > 64) split = 64;
+  if (split < 1) split = 1;
+  dim3 grid((unsigned)((batch + KS_BM - 1) / KS_BM), (unsigned)((out_len + KS_BN - 1) / KS_BN),
+            (unsigned)split);
+  const size_t wb = (size_t)w / 8;
+  if (split > 1) FD_CUDA(cudaMemsetAsync(out, 0, (size_t)batch * out_len * wb, s));
+  if (w == 32)
+    keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>((const uint32_t*)in, batch, n_in,
+                                                          (const uint32_t*)key, ell, log2B, rt, out_len,
+                                                          (uint32_t*)out, (int)split);
+  else
+    keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>((const uint64_t*)in, batch, n_in,
+                                                          (const uint64_t*)key, ell, log2B, rt, out_len,
+                                                          (uint64_t*)out, (int)split);
+  return cuda_err(cudaGetLastError());
+}
+
 // Brackets one launch with an event pair when the measurement hook is on.
 struct StageTimer {
   fdfb_ctx* ctx;
@@ -294,18 +325,9 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
 
   // Steps 9-11, BuildAcc: KeySwitch to RLWE with pK, then PubMux.
   {
-    dim3 grid((unsigned)((2 * N + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
-    const int rt = trunc_bits(st.w, P.log2Bpk, P.lpk);
     StageTimer tm(tctx, 1, s);
-    if (st.w == 32)
-      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint32_t*)sgn, batch, (int)N, (const uint32_t*)st.pk.p, P.lpk, P.log2Bpk, rt,
-          (int)(2 * N), (uint32_t*)cR);
-    else
-      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint64_t*)sgn, batch, (int)N, (const uint64_t*)st.pk.p, P.lpk, P.log2Bpk, rt,
-          (int)(2 * N), (uint64_t*)cR);
-    FD_CUDA(cudaGetLastError());
+    FD_TRY(launch_keyswitch(ctx, st.w, sgn, batch, (int)N, st.pk.p, P.lpk, P.log2Bpk,
+                            trunc_bits(st.w, P.log2Bpk, P.lpk), (int)(2 * N), cR, s));
   }
   PubMuxParams pm{};
   pm.S = st.base().S;
@@ -339,18 +361,9 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
 
   // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q).
   {
-    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((items + KS_BM - 1) / KS_BM));
-    const int rt = trunc_bits(st.w, P.log2Bks, P.lks);
     StageTimer tm(tctx, 4, s);
-    if (st.w == 32)
-      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint32_t*)cQ, items, (int)N, (const uint32_t*)st.ksk.p, P.lks, P.log2Bks, rt,
-          (int)P.n + 1, (uint32_t*)ct_out);
-    else
-      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>(
-          (const uint64_t*)cQ, items, (int)N, (const uint64_t*)st.ksk.p, P.lks, P.log2Bks, rt,
-          (int)P.n + 1, (uint64_t*)ct_out);
-    FD_CUDA(cudaGetLastError());
+    FD_TRY(launch_keyswitch(ctx, st.w, cQ, items, (int)N, st.ksk.p, P.lks, P.log2Bks,
+                            trunc_bits(st.w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
   }
   return FDFB_OK;
 }
@@ -478,6 +491,10 @@ int fdfb_create(fdfb_ctx** out, int device) {
   DeviceGuard g(device);
   auto* ctx = new fdfb_ctx();
   ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->sms = 1;
+  }
   if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -828,18 +845,9 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
   }
   {
-    dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
-    const int rt = trunc_bits(st->w, P.log2Bks, P.lks);
     StageTimer tm(ctx, 4, s);
-    if (st->w == 32)
-      keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>((const uint32_t*)cQ, batch, (int)N,
-                                                            (const uint32_t*)st->ksk.p, P.lks, P.log2Bks,
-                                                            rt, (int)P.n + 1, (uint32_t*)ct_out);
-    else
-      keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>((const uint64_t*)cQ, batch, (int)N,
-                                                            (const uint64_t*)st->ksk.p, P.lks, P.log2Bks,
-                                                            rt, (int)P.n + 1, (uint64_t*)ct_out);
-    FD_CUDA(cudaGetLastError());
+    FD_TRY(launch_keyswitch(ctx, st->w, cQ, batch, (int)N, st->ksk.p, P.lks, P.log2Bks,
+                            trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
   }
   return FDFB_OK;
 }
@@ -961,24 +969,15 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
 int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
                    void* cuda_stream) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || batch < 0 || batch > 0x7fffffffLL * KS_BM) return FDFB_EINVAL;
+  if (!st || batch < 0 || batch > 0x7fffffffLL) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !ct_out) return FDFB_EINVAL;
   if (!st->keys) return FDFB_ENOKEYS;
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(cuda_stream);
   const fdfb_params& P = st->prm;
-  dim3 grid((unsigned)((P.n + 1 + KS_BN - 1) / KS_BN), (unsigned)((batch + KS_BM - 1) / KS_BM));
-  const int rt = trunc_bits(st->w, P.log2Bks, P.lks);
-  if (st->w == 32)
-    keyswitch_kernel<uint32_t><<<grid, KS_THREADS, 0, s>>>((const uint32_t*)ct_in, batch, (int)P.N,
-                                                          (const uint32_t*)st->ksk.p, P.lks, P.log2Bks,
-                                                          rt, (int)P.n + 1, (uint32_t*)ct_out);
-  else
-    keyswitch_kernel<uint64_t><<<grid, KS_THREADS, 0, s>>>((const uint64_t*)ct_in, batch, (int)P.N,
-                                                          (const uint64_t*)st->ksk.p, P.lks, P.log2Bks,
-                                                          rt, (int)P.n + 1, (uint64_t*)ct_out);
-  return cuda_err(cudaGetLastError());
+  return launch_keyswitch(ctx, st->w, ct_in, batch, (int)P.N, st->ksk.p, P.lks, P.log2Bks,
+                          trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s);
 }
 
 int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,

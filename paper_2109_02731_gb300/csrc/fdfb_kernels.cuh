@@ -769,34 +769,51 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
 // as a tiled integer GEMM: rows m (ciphertexts), columns (output words),
 // reduction over (i, j) with the digits generated on the fly.
 // ---------------------------------------------------------------------------
-constexpr int KS_BM = 32, KS_BN = 64, KS_BK = 32, KS_THREADS = 256;  // 2 x 4 outputs per thread
+constexpr int KS_BM = 64, KS_BN = 128, KS_BK = 32, KS_THREADS = 256;  // 8 x 4 outputs per thread
 
+__device__ __forceinline__ void atomic_add_word(uint32_t* p, uint32_t v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_word(uint64_t* p, uint64_t v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// CTA (blockIdx.x, blockIdx.y, blockIdx.z): ciphertexts [64 x, 64 x + 64),
+// output columns [128 y, 128 y + 128), and slice z of `ksplit` equal slices of the
+// reduction (K = n_in l, in steps of 32).  Thread (ty, tx) = (tid / 32,
+// tid % 32) owns rows 8 ty.. and columns 4 tx..; per reduction index it reads
+// its 8 digits as one broadcast 128-bit shared load and its 4 key words as
+// one (u32) or two (u64) 128-bit loads, then does 32 multiply-adds.  With
+// ksplit = 1 each output is written once; otherwise `out` must be zero and the
+// slices add their parts atomically (integer addition mod 2^w: exact in any
+// order), slice 0 adding b.
 template <typename W>
 __global__ void __launch_bounds__(KS_THREADS)
 keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __restrict__ key,
-                 int ell, int log2B, int rtrunc, int out_len, W* __restrict__ out) {
-  __shared__ uint16_t sa[KS_BK][KS_BM];
-  __shared__ W sb[KS_BK][KS_BN];
-  const int tid = threadIdx.x;
-  const int64_t m0 = (int64_t)blockIdx.y * KS_BM;
-  const int c0 = blockIdx.x * KS_BN;
-  const int tm = tid / 16, tn = tid % 16;  // 16 x 16 threads; thread owns rows tm*2.., cols tn*4..
-  W accv[2][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) accv[a][b] = 0;
+                 int ell, int log2B, int rtrunc, int out_len, W* __restrict__ out, int ksplit) {
+  __shared__ __align__(16) uint16_t sa[KS_BK][KS_BM];
+  __shared__ __align__(16) W sb[KS_BK][KS_BN];
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * KS_BM;
+  const int c0 = blockIdx.y * KS_BN;
   const int K = n_in * ell;
+  const int kt = (K + KS_BK - 1) / KS_BK;
+  const int kb = (int)((int64_t)kt * blockIdx.z / ksplit) * KS_BK;
+  const int ke = min(K, (int)((int64_t)kt * (blockIdx.z + 1) / ksplit) * KS_BK);
+  W acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   const W half_rt = rtrunc ? ((W)1 << (rtrunc - 1)) : (W)0;
   const uint32_t dmask = (1u << log2B) - 1;
-  for (int k0 = 0; k0 < K; k0 += KS_BK) {
-    // digits: KS_BK x KS_BM
+  for (int k0 = kb; k0 < ke; k0 += KS_BK) {
+    // digits of the tile's ciphertexts: KS_BK x KS_BM, 8 per thread
+#pragma unroll
     for (int e = tid; e < KS_BK * KS_BM; e += KS_THREADS) {
       const int kk = e / KS_BM, mm = e % KS_BM;
       const int k = k0 + kk;
       const int64_t m = m0 + mm;
       uint16_t d = 0;
-      if (k < K && m < batch) {
+      if (k < ke && m < batch) {
         const int i = k / ell, j = k - i * ell;
         const W x = ct[m * (n_in + 1) + 1 + i];
         const W xt = rtrunc ? (W)((W)(x + half_rt) >> rtrunc) : x;
@@ -804,35 +821,48 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
       }
       sa[kk][mm] = d;
     }
+    // key rows: KS_BK x KS_BN words, 16 per thread, coalesced along a row
+#pragma unroll
     for (int e = tid; e < KS_BK * KS_BN; e += KS_THREADS) {
       const int kk = e / KS_BN, cc = e % KS_BN;
       const int k = k0 + kk, c = c0 + cc;
-      sb[kk][cc] = (k < K && c < out_len) ? key[(size_t)k * out_len + c] : (W)0;
+      sb[kk][cc] = (k < ke && c < out_len) ? key[(size_t)k * out_len + c] : (W)0;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int kk = 0; kk < KS_BK; ++kk) {
-      const uint32_t d0 = sa[kk][tm * 2], d1 = sa[kk][tm * 2 + 1];
+      const uint4 dq = *reinterpret_cast<const uint4*>(&sa[kk][ty * 8]);
+      const uint32_t dw[4] = {dq.x, dq.y, dq.z, dq.w};
+      W kv[4];
+      if constexpr (sizeof(W) == 4) {
+        const uint4 q = *reinterpret_cast<const uint4*>(&sb[kk][tx * 4]);
+        kv[0] = q.x; kv[1] = q.y; kv[2] = q.z; kv[3] = q.w;
+      } else {
+        const ulonglong2 q0 = *reinterpret_cast<const ulonglong2*>(&sb[kk][tx * 4]);
+        const ulonglong2 q1 = *reinterpret_cast<const ulonglong2*>(&sb[kk][tx * 4 + 2]);
+        kv[0] = q0.x; kv[1] = q0.y; kv[2] = q1.x; kv[3] = q1.y;
+      }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const W kv = sb[kk][tn * 4 + b];
-        accv[0][b] += (W)d0 * kv;
-        accv[1][b] += (W)d1 * kv;
+      for (int a = 0; a < 8; ++a) {
+        const W d = (W)((dw[a >> 1] >> ((a & 1) * 16)) & 0xffffu);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += d * kv[b];
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    const int64_t m = m0 + tm * 2 + a;
+  for (int a = 0; a < 8; ++a) {
+    const int64_t m = m0 + ty * 8 + a;
     if (m >= batch) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int c = c0 + tn * 4 + b;
+      const int c = c0 + tx * 4 + b;
       if (c >= out_len) continue;
-      W v = (W)(0 - accv[a][b]);
-      if (c == 0) v = (W)(v + ct[m * (n_in + 1)]);
-      out[m * out_len + c] = v;
+      W v = (W)(0 - acc[a][b]);
+      if (c == 0 && blockIdx.z == 0) v = (W)(v + ct[m * (n_in + 1)]);
+      if (ksplit == 1) out[m * out_len + c] = v;
+      else atomic_add_word(&out[m * out_len + c], v);
     }
   }
 }
