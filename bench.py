@@ -559,7 +559,12 @@ def main():
     peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T slots/s
     achieved = slots / (br_ms / 1e3) / 1e12
     stages = {k: v for k, v in prof.items() if k != "blind_rotate_union"}
-    stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
+    chunked = any(ctx.get_chunks(g["sid"]) > 1 for g in job.groups) and len(job.groups) == 1
+    # launches of different stages overlap when a call is chunked, so their
+    # summed durations no longer give shares (the serialised ncu launch lists
+    # under profiles/ do)
+    stage_share = None if chunked else {
+        k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
     h2d, d2h = job.io_bytes()
     ps0 = job.groups[0]["ps"]
     traffic, traffic_src = None, None
