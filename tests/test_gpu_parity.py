@@ -809,3 +809,36 @@ def test_other_output_modulus_matches_oracle(F, torch_cuda, ctx, oracle, t_out):
     with pytest.raises(F.FDFBError):
         ctx.lut_setup(sid, [t_out, 0, 0, 0])
 
+
+# ------------------------------------------------------------ extreme sizes --
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_widest_digits_and_largest_t(F, torch_cuda, ctx, oracle, signed):
+    """Limits of the parameter space at N = 256: 16-bit digits (B = 2^16, the
+    widest the digit buffers hold, l = 2: an exact 32-bit decomposition) in
+    every gadget, and t = N (one-coefficient windows).  Every registered
+    variant equals the oracle bit for bit; balanced digits reach -2^15."""
+    import dataclasses
+    base = S.PARAM_SETS["Z"]
+    ps = dataclasses.replace(base, name=f"Zmax{int(signed)}", t=256, log2Bg=16, lg=2, log2Bks=16,
+                             lks=2, log2Bpk=16, lpk=2, sigma_lwe=2.0 ** 10, sigma_glwe=2.0 ** 6,
+                             signed_digits=signed)
+    kr = S.key_randomness(ps, 12)
+    K = oracle.Keys(ps, kr)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    fs = S.lut_tables(ps, 12, 2)
+    rot = np.stack([np.stack(oracle.setup_polynomial(ps.N, ps.t, f)) for f in fs])
+    for f in fs:
+        ctx.lut_setup(sid, f)
+    ids = S.lut_assignment(12, 21, 2, "uniform")
+    mr = S.message_randomness(ps, 12, 21)
+    cts = oracle.encrypt_messages(ps, K.s, mr)
+    want = oracle.fdfb_batch(ps, K, rot, ids, cts)
+    count = ctx.variant_info(sid)[1]
+    assert count >= 1
+    for v in range(count):
+        ctx.set_variant(sid, v)
+        out, _ = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+        assert np.array_equal(out, want), v
+
