@@ -226,7 +226,7 @@ struct BRShape {
   static constexpr size_t x64entries() { return ((size_t)Xch64<L, EL>::kEntries + 1) & ~(size_t)1; }
   // 32-bit words of one group's exchange region
   static constexpr size_t group_words() {
-    return M == 2 ? (PP ? 2 : 1) * 2 * x64entries() : (size_t)M * xwords();
+    return (M == 2 || KH == 2) ? (PP ? 2 : 1) * 2 * x64entries() : (size_t)M * xwords();
   }
 };
 
@@ -284,8 +284,8 @@ blind_rotate_kernel(const BRParams prm) {
   constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
   static_assert(P >= 2, "the column owners are groups 0 and 1");
   static_assert(!LZ || (L <= 12 && sizeof(DT) <= 2), "lazy bound: 2^16 + 2 L p < 2^32");
-  static_assert(KH == 1 || (KH == 2 && P == 2 && M == 2 && !WIDE && sizeof(W) == 8),
-                "split keys: q = 2^64, two primes, paired transforms, per-product reduction");
+  static_assert(KH == 1 || (KH == 2 && P == 2 && !WIDE && sizeof(W) == 8),
+                "split keys: q = 2^64, two primes, per-product reduction");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
@@ -332,7 +332,11 @@ blind_rotate_kernel(const BRParams prm) {
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
   using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
+  // forward transforms: M polynomials per pass; inverse transforms: both
+  // columns together whenever the forward is paired or the key is split
+  constexpr int MI = (M == 2 || KH == 2) ? 2 : 1;
   constexpr int XW = (int)(M == 2 ? Sh::x64entries() : Sh::xwords());
+  constexpr int XWI = (int)(MI == 2 ? Sh::x64entries() : Sh::xwords());
   uint32_t* xb = exch + grp * (int)Sh::group_words();
   const int bar = 1 + grp;
   const int rt = prm.rtrunc;
@@ -454,7 +458,7 @@ blind_rotate_kernel(const BRParams prm) {
     // residues in registers; every other group stages its residues for it.
     // (staging slot s of key half h at stage + (s KH + h) N)
     uint32_t own[KH][E];
-    if constexpr (M == 2) {
+    if constexpr (MI == 2) {
 #pragma unroll
       for (int h = 0; h < KH; ++h) {
         uint32_t v[2][E];
@@ -463,7 +467,7 @@ blind_rotate_kernel(const BRParams prm) {
           v[0][k] = acc_to_inv<WIDE, LZ>(macc[h][0][k], p, pneg, ones);
           v[1][k] = acc_to_inv<WIDE, LZ>(macc[h][1][k], p, pneg, ones);
         }
-        ntt_inv_m<L, EL, Y::K - 1, 2, XW, PP>(v, t, twi, p, xb, bar, z);
+        ntt_inv_m<L, EL, Y::K - 1, 2, XWI, PP>(v, t, twi, p, xb, bar, z);
         uint32_t* dst0 = stage + (stage_slot<P>(grp, swap) * KH + h) * N;
 #pragma unroll
         for (int k = 0; k < E; ++k) dst0[Y::j_of(0, t, k)] = csub(v[0][k], p);
