@@ -18,6 +18,7 @@ the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -261,6 +262,8 @@ class Job:
             self._prepare_mlp(args, rank)
         else:
             for gi, g in enumerate(wl.groups):
+                if args.batch is not None and len(wl.groups) == 1:
+                    g = dataclasses.replace(g, batch=args.batch)  # smaller case, e.g. for ncu
                 self.groups.append(self._prepare_group(gi, g, args, rank))
             self.units = sum(x["batch"] * x["k"] for x in self.groups)
 
@@ -406,6 +409,8 @@ def config_for(job, args):
                 "l2": "flushed before every timed step (512 MB write, not timed)"}
     if len(job.groups) == 1:
         g = wl.groups[0]
+        if args.batch is not None:
+            g = dataclasses.replace(g, batch=args.batch)
         ps = S.PARAM_SETS[g.set_name]
         return config_of(args, wl, g, ps)
     return {"workload": f"{wl.name}: " + ", ".join(
@@ -422,6 +427,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tfhe_scale", choices=sorted(S.WORKLOADS))
+    ap.add_argument("--batch", type=int, default=None,
+                    help="override the batch of a single-group workload (a smaller case for profiling; "
+                         "not the workload's benchmark configuration)")
     ap.add_argument("--ref-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
