@@ -848,9 +848,19 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
       }
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const W d = (W)((dw[a >> 1] >> ((a & 1) * 16)) & 0xffffu);
+        const uint32_t d = (dw[a >> 1] >> ((a & 1) * 16)) & 0xffffu;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += d * kv[b];
+        for (int b = 0; b < 4; ++b) {
+          if constexpr (sizeof(W) == 4) {
+            acc[a][b] += (W)d * kv[b];
+          } else {
+            // d < 2^16: d K = d K_lo + 2^32 d K_hi, a 32x32->64 multiply-add
+            // and a 32-bit multiply-add into the high word
+            const uint64_t lo = (uint64_t)d * (uint32_t)kv[b];
+            const uint32_t hi = d * (uint32_t)(kv[b] >> 32);
+            acc[a][b] += lo + ((uint64_t)hi << 32);
+          }
+        }
       }
     }
     __syncthreads();
