@@ -449,6 +449,59 @@ int noalloc_scratch(int device, void** out) {
   return FDFB_OK;
 }
 
+// Chooses how many chunks fdfb_bootstrap splits a batch of `batch` into: the
+// whole pipeline on zero trial ciphertexts (table 0) is timed with 1, 2, 3,
+// 4, 6 and 8 chunks.  Only batches below 8 waves of the blind rotation are
+// tried (beyond that the last partial wave costs little) and only when a
+// table is installed; otherwise one chunk.
+int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
+  int dev_sms = 0;
+  FD_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int per_sm = st.br().ops->br_blocks_per_sm(st.br().br_smem);
+  const int64_t slots = (int64_t)dev_sms * (per_sm > 0 ? per_sm : 1);
+  int best = 1;
+  if (st.n_luts > 0 && batch >= 2 && batch < 8 * slots) {
+    const size_t row = (size_t)(st.prm.n + 1) * st.wbytes();
+    DevBuf in, out, ids;
+    FD_TRY(in.ensure(batch * row));
+    FD_TRY(out.ensure(batch * row));
+    FD_TRY(ids.ensure(batch * sizeof(int32_t)));
+    FD_CUDA(cudaMemsetAsync(in.p, 0, batch * row, s));
+    FD_CUDA(cudaMemsetAsync(ids.p, 0, batch * sizeof(int32_t), s));
+    FD_TRY(ensure_scratch(st, batch, 1));
+    FD_TRY(ensure_chunk_streams(ctx, kMaxChunks));
+    cudaEvent_t a, b;
+    FD_CUDA(cudaEventCreate(&a));
+    FD_CUDA(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    int rc = FDFB_OK;
+    for (int c : {1, 2, 3, 4, 6, 8}) {
+      if (rc != FDFB_OK || c > kMaxChunks) break;
+      float ms_c = 1e30f;
+      for (int rep = 0; rep < 2 && rc == FDFB_OK; ++rep) {
+        cudaEventRecord(a, s);
+        rc = run_chunked(ctx, st, in.p, (const int32_t*)ids.p, batch, 1, out.p, s, c);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = cuda_err(cudaGetLastError());
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < ms_c) ms_c = ms;  // the first run warms caches
+      }
+      if (ms_c < best_ms) {
+        best_ms = ms_c;
+        best = c;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    FD_CUDA(cudaStreamSynchronize(s));
+    if (rc != FDFB_OK) return rc;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  st.chunks = best;
+  return FDFB_OK;
+}
+
 // The TFHE bootstrap's accumulator kernel for ring degree 2^L.
 template <typename W>
 cudaError_t launch_tfhe_acc(int L, int64_t batch, cudaStream_t s, const W* ct, int n, const int32_t* ids,
@@ -1051,59 +1104,6 @@ int fdfb_set_variant(fdfb_ctx* ctx, int set_id, int variant) {
   if (!st || variant < 0 || variant >= (int)st->var.size()) return FDFB_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   st->cur = variant;
-  return FDFB_OK;
-}
-
-// Chooses how many chunks fdfb_bootstrap splits a batch of `batch` into: the
-// whole pipeline on zero trial ciphertexts (table 0) is timed with 1, 2, 3,
-// 4, 6 and 8 chunks.  Only batches below 8 waves of the blind rotation are
-// tried (beyond that the last partial wave costs little) and only when a
-// table is installed; otherwise one chunk.
-int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
-  int dev_sms = 0;
-  FD_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  const int per_sm = st.br().ops->br_blocks_per_sm(st.br().br_smem);
-  const int64_t slots = (int64_t)dev_sms * (per_sm > 0 ? per_sm : 1);
-  int best = 1;
-  if (st.n_luts > 0 && batch >= 2 && batch < 8 * slots) {
-    const size_t row = (size_t)(st.prm.n + 1) * st.wbytes();
-    DevBuf in, out, ids;
-    FD_TRY(in.ensure(batch * row));
-    FD_TRY(out.ensure(batch * row));
-    FD_TRY(ids.ensure(batch * sizeof(int32_t)));
-    FD_CUDA(cudaMemsetAsync(in.p, 0, batch * row, s));
-    FD_CUDA(cudaMemsetAsync(ids.p, 0, batch * sizeof(int32_t), s));
-    FD_TRY(ensure_scratch(st, batch, 1));
-    FD_TRY(ensure_chunk_streams(ctx, kMaxChunks));
-    cudaEvent_t a, b;
-    FD_CUDA(cudaEventCreate(&a));
-    FD_CUDA(cudaEventCreate(&b));
-    float best_ms = 1e30f;
-    int rc = FDFB_OK;
-    for (int c : {1, 2, 3, 4, 6, 8}) {
-      if (rc != FDFB_OK || c > kMaxChunks) break;
-      float ms_c = 1e30f;
-      for (int rep = 0; rep < 2 && rc == FDFB_OK; ++rep) {
-        cudaEventRecord(a, s);
-        rc = run_chunked(ctx, st, in.p, (const int32_t*)ids.p, batch, 1, out.p, s, c);
-        cudaEventRecord(b, s);
-        if (cudaEventSynchronize(b) != cudaSuccess) rc = cuda_err(cudaGetLastError());
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0 && ms < ms_c) ms_c = ms;  // the first run warms caches
-      }
-      if (ms_c < best_ms) {
-        best_ms = ms_c;
-        best = c;
-      }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    FD_CUDA(cudaStreamSynchronize(s));
-    if (rc != FDFB_OK) return rc;
-  }
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  st.chunks = best;
   return FDFB_OK;
 }
 
