@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <memory>
 #include <mutex>
@@ -241,16 +243,26 @@ int launch_keyswitch(const fdfb_ctx* ctx, int w, const void* in, int64_t batch, 
   return cuda_err(cudaGetLastError());
 }
 
-// Brackets one launch with an event pair when the measurement hook is on.
+// Pipeline stages as NVTX ranges (shown by external profilers on the host
+// timeline, with the launches they enqueue).
+const char* const kStageNames[kStages] = {
+    "fdfb: sign blind rotation", "fdfb: packing key switch", "fdfb: PubMux / TFHE accumulator",
+    "fdfb: function blind rotation", "fdfb: LWE key switch", "fdfb: blind rotations"};
+
+// Brackets one launch with an NVTX range, and with an event pair when the
+// measurement hook is on (the no-allocation path passes ctx = nullptr: no
+// events are created there; the NVTX range needs no runtime object).
 struct StageTimer {
   fdfb_ctx* ctx;
   int stage;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   StageTimer(fdfb_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
+    nvtxRangePushA(kStageNames[stage]);
     if (ctx && ctx->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
   }
   ~StageTimer() {
+    nvtxRangePop();
     if (!a) return;
     cudaEvent_t b;
     if (cudaEventCreate(&b) == cudaSuccess) {

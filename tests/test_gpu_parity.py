@@ -344,6 +344,15 @@ def test_errors_and_edge_cases(F, torch_cuda, ctx, oracle):
         ctx.sync()
     assert e.value.code == -6
     ctx.sync()  # latch cleared
+    # an impossible scratch allocation (2^30 ciphertexts: terabytes) fails with
+    # FDFB_ENOMEM before any launch, and the context keeps working
+    ids1 = torch_cuda.zeros(2, dtype=torch_cuda.int32, device=d)
+    with pytest.raises(F.FDFBError) as e:
+        ctx.bootstrap(sid, ct, ids1, out, batch=1 << 30)
+    assert e.value.code == -2
+    ctx.sync()
+    ctx.bootstrap(sid, ct, ids1, out)
+    ctx.sync()
     # keys missing
     sid2 = ctx.register(ps)
     ctx.lut_setup(sid2, [0, 1, 2, 3])
