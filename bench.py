@@ -55,11 +55,11 @@ def workload_desc(name: str):
 
 
 # DRAM bytes (read + write) of one blind-rotation launch over the whole batch,
-# from the ncu captures summarised under profiles/ (set, variant, batch); the
-# bench reports them only for that configuration of the current kernel.
+# measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the current
+# kernel for (set, variant, batch); reported only for that configuration.
 KERNEL_TRAFFIC = {
-    ("B", 7, 1024): 86.26e6,    # profiles/blind_rotate_tfhe_scale.md
-    ("D", 6, 1000): 3.19754e9,  # profiles/blind_rotate_n2048.md
+    ("B", 7, 1024): 86.26e6,    # tfhe_scale workload
+    ("D", 6, 1000): 3.19754e9,  # n2048 workload
 }
 
 
@@ -569,8 +569,7 @@ def main():
     stages = {k: v for k, v in prof.items() if k != "blind_rotate_union"}
     chunked = any(ctx.get_chunks(g["sid"]) > 1 for g in job.groups) and len(job.groups) == 1
     # launches of different stages overlap when a call is chunked, so their
-    # summed durations no longer give shares (the serialised ncu launch lists
-    # under profiles/ do)
+    # summed durations no longer give shares (a serialised ncu launch list does)
     stage_share = None if chunked else {
         k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
     h2d, d2h = job.io_bytes()

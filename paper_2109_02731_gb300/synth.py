@@ -79,10 +79,11 @@ class ParamSet:
         return (1 << self.w) // self.tout
 
 
-# Sets A-C come straight from the workload list; D and the bold choices of
-# the hot-path scope table (packing-key gadget, sigmas of the 2^64 sets) are
-# readings fixed in the design doc.  Z is the noiseless exact-decomposition set
-# used for the exhaustive correctness pin.
+# Sets A-C are the parameters of the toy, TFHE-scale and large-plaintext
+# workloads.  Set D (N = 2048), the packing-key gadgets and the noise levels of
+# the 2^64 sets are choices of this library where the workloads leave them
+# open.  Z is the noiseless exact-decomposition set used for the exhaustive
+# correctness pin.
 PARAM_SETS: Dict[str, ParamSet] = {
     "A": ParamSet("A", n=64, N=256, w=32, t=4, log2Bg=8, lg=3, log2Bks=4, lks=5,
                   log2Bpk=8, lpk=3, sigma_lwe=2.0 ** 12, sigma_glwe=2.0 ** 7),
