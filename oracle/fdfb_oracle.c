@@ -33,6 +33,15 @@
  *   G6  Every rounding is round-half-up.
  *   G7  NSgn(x) = 1 iff x > 0 (the LaTeX source redefines \ge as >).
  *   G8  SetupPolynomial runs m ascending, then e ascending; later writes win.
+ *   G20 Several functions of one input share the sign part (ModSwitch, sign
+ *       rotation, SampleExtract + Delta/2, packing KeySwitch); PubMux, the
+ *       function rotation and the LWE KeySwitch run per function.
+ *   G21 Optional balanced blind-rotation digits: the same x~ written with
+ *       digits in [-B/2, B/2), carrying upward; the top carry is dropped
+ *       (B^l 2^r = 2^w).  The key switches keep unsigned digits.
+ *   G23 Optional output modulus t' (f: Z_t -> Z_t'): Delta' = q / t' scales
+ *       the sign LWE and PubMux, the PubMux selector is reduced mod t', and
+ *       SetupPolynomial's windows stay those of t.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -49,7 +58,7 @@ typedef struct {
     int32_t n, N, w, t;
     int32_t log2Bg, lg, log2Bks, lks, log2Bpk, lpk;
     int32_t signed_digits;  /* blind rotation decomposes into balanced digits (G21) */
-    int32_t t_out;          /* output plaintext modulus t' (0: t' = t), G13 */
+    int32_t t_out;          /* output plaintext modulus t' (0: t' = t), G23 */
 } or_params;
 
 /* The output space Z_t' of f: Z_t -> Z_t' (footnote of Section 1.1: the
