@@ -536,8 +536,8 @@ def main():
         ms_total, e2e_ms = slowest_rank([ms_total, e2e_ms], dev)
 
     plain = None
-    if (args.plain and rank == 0 and not job.wl.mlp_layers and job.groups[0]["k"] == 1
-            and job.groups[0].get("mode") != "tfhe"):
+    if (args.plain and rank == 0 and not job.wl.mlp_layers and len(job.groups) == 1
+            and job.groups[0]["k"] == 1 and job.groups[0].get("mode") != "tfhe"):
         reps = 8
         g = job.groups[0]
         one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()
