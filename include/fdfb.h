@@ -81,6 +81,15 @@ typedef struct {
   uint32_t t_out;
 } fdfb_params;
 
+/* Concurrency.  Every call is stream-ordered.  A parameter set owns one
+ * scratch area for its pipeline intermediates, so bootstrap calls on the
+ * same set must be ordered on the GPU (one stream, or events between
+ * streams); calls on different sets may run concurrently.  Registration,
+ * key installation and table setup take the context's lock and synchronise
+ * the device where they replace device buffers; issue them before the calls
+ * that use them.  A call that grows scratch (a larger batch than before)
+ * allocates, so make it once outside any stream capture. */
+
 /* Creates a context on CUDA device `device`.  *out receives the handle. */
 int fdfb_create(fdfb_ctx** out, int device);
 
