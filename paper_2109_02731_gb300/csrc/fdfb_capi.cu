@@ -330,6 +330,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.smem_exch = bv.br_ex;
   br.rep = 1;
   br.signed_digits = (int)P.signed_digits;
+  br.err = ctx->d_err;
   {
     StageTimer tm(tctx, 0, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -905,6 +906,7 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
   br.smem_exch = bv.br_ex;
   br.rep = 1;
   br.signed_digits = (int)P.signed_digits;
+  br.err = ctx->d_err;
   {
     StageTimer tm(ctx, 3, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -1156,6 +1158,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.smem_exch = v.br_ex;
     br.rep = 1;
     br.signed_digits = (int)st->prm.signed_digits;
+    br.err = ctx->d_err;
     float ms_v = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, s);

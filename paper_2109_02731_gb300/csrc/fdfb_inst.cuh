@@ -6,13 +6,13 @@ namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1, bool SGV = false>
+          int KH = 1, bool SGV = false, bool TK = false>
 struct Inst {
   // SGV: also build the blind rotation with balanced digits (parameter sets
   // with signed_digits only use variants that have it)
   template <bool SG>
-  static constexpr auto kernel() { return blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH, SG>; }
-  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
+  static constexpr auto kernel() { return blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH, SG, TK>; }
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {

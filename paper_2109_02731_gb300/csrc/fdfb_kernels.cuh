@@ -29,6 +29,40 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory by the copy engine, completing on an mbarrier.
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier generic-proxy accesses of shared memory before
+// its later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t m = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
+}
+// Waits for phase `parity` of the mbarrier to complete, giving up after
+// `limit` polls (the caller latches FDFB_ETIMEOUT): returns whether it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+  const uint32_t m = (uint32_t)__cvta_generic_to_shared(mbar);
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(m), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -203,9 +237,11 @@ struct BRParams {
   uint32_t smem_r1, smem_exch;  // byte offsets inside dynamic shared memory
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
   int signed_digits;            // balanced digits: the launcher picks the kernel built with SG
+  int* err;                     // device error latch (FDFB_ETIMEOUT if a key copy never lands)
 };
 
-template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1>
+template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1,
+          bool TK = false>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -218,8 +254,12 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * group_words() * 4;
+    return acc + an + r1 + (size_t)P * group_words() * 4 + kstage_bytes();
   }
+  // TK: per group, the key rows of one pair (2M rows x N words), then one
+  // mbarrier per group
+  static constexpr size_t kpair_words() { return (size_t)2 * M * KH * N; }
+  static constexpr size_t kstage_bytes() { return TK ? (size_t)P * kpair_words() * 4 + (size_t)P * 8 : 0; }
   // 32-bit words of one polynomial's exchange buffer (M = 1)
   static constexpr size_t xwords() { return ((size_t)Xch<L, EL>::kWords + 3) & ~(size_t)3; }
   // 64-bit entries of one paired exchange buffer (M = 2)
@@ -275,9 +315,13 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // transforms, and each half's product sum (at most 2l N (B-1) 2^31) is lifted
 // exactly from two primes: acc += X_lo + 2^32 X_hi mod 2^64.
 // SG: balanced digits in [-B/2, B/2) (a parameter set's signed_digits).
+// TK: each group's key rows of the next pair (2M rows) are copied into shared
+// memory by the bulk-copy engine while the group transforms that pair's
+// digits; one thread per group issues the copy, completion is an mbarrier
+// phase (bounded wait, FDFB_ETIMEOUT on expiry).
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1, bool SG = false>
+          int KH = 1, bool SG = false, bool TK = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -322,6 +366,18 @@ blind_rotate_kernel(const BRParams prm) {
     const W* a0 = reinterpret_cast<const W*>(prm.acc0) + ci * 2 * N;
     for (int j = tid; j < 2 * N; j += THREADS) acc[j] = a0[j];
   }
+  // TK: the staged pair of key rows of each group, and its mbarrier
+  constexpr uint32_t kPairWords = (uint32_t)(2 * M * KH * N);
+  uint32_t* kst = reinterpret_cast<uint32_t*>(
+      smem + prm.smem_exch + (size_t)P * BRShape<L, EL, P, W, DT, M, PP, KH, TK>::group_words() * 4);
+  uint64_t* kmb = reinterpret_cast<uint64_t*>(kst + (size_t)P * kPairWords) + (tid / G);
+  kst += (size_t)(tid / G) * kPairWords;
+  if constexpr (TK) {
+    if (tid % G == 0) {
+      mbar_init(kmb, 1);
+      fence_mbar_init();
+    }
+  }
   __syncthreads();
 
   const uint32_t p = prm.S.p[grp];
@@ -331,7 +387,7 @@ blind_rotate_kernel(const BRParams prm) {
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
-  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH>;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK>;
   // forward transforms: M polynomials per pass; inverse transforms: both
   // columns together whenever the forward is paired or the key is split
   constexpr int MI = (M == 2 || KH == 2) ? 2 : 1;
@@ -351,6 +407,14 @@ blind_rotate_kernel(const BRParams prm) {
   // in L2).
   const uint32_t kblock = (uint32_t)(R * 2 * KH * N * 4);
   if (t == 0) prefetch_l2_bulk(prm.bsk + (size_t)grp * R * 2 * KH * N, kblock);
+  // TK: the first pair's rows; kph is the parity of the staged pair's phase,
+  // kfail latches an expired wait (no further copies or waits after it)
+  uint32_t kph = 0, kfph = 0;
+  bool kfail = false;
+  constexpr uint32_t kWaitLimit = 1u << 20;
+  if constexpr (TK) {
+    if (t == 0 && n > 0) bulk_copy_g2s(kst, prm.bsk + (size_t)grp * R * 2 * KH * N, kPairWords * 4, kmb);
+  }
   for (int i = 0; i < n; ++i) {
     const int a = aN[i];
     if (t == 0 && i + 1 < n) prefetch_l2_bulk(prm.bsk + ((size_t)(i + 1) * P + grp) * R * 2 * KH * N, kblock);
@@ -423,6 +487,14 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
           for (int k = 0; k < E; ++k) v[m][k] = csub(csub(v[m][k], 2 * p), p);
       }
+      if constexpr (TK) {
+        if (!kfail && !mbar_wait(kmb, kph, kWaitLimit)) {
+          kfail = true;
+          kfph = kph;
+          if (prm.err) atomicExch(prm.err, -4);  // FDFB_ETIMEOUT
+        }
+        kph ^= 1u;
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
 #pragma unroll
@@ -430,10 +502,11 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             const uint4* kp =
-                reinterpret_cast<const uint4*>(krow + (((size_t)(r0 + m) * 2 + (c ^ swap)) * KH + h) * N) + t;
+                TK ? reinterpret_cast<const uint4*>(kst + (((size_t)m * 2 + (c ^ swap)) * KH + h) * N) + t
+                   : reinterpret_cast<const uint4*>(krow + (((size_t)(r0 + m) * 2 + (c ^ swap)) * KH + h) * N) + t;
 #pragma unroll
             for (int q4 = 0; q4 < E / 4; ++q4) {
-              const uint4 kk = ldg_stream(kp + q4 * G);
+              const uint4 kk = TK ? kp[q4 * G] : ldg_stream(kp + q4 * G);
               const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
@@ -448,6 +521,20 @@ blind_rotate_kernel(const BRParams prm) {
                 }
               }
             }
+          }
+        }
+      }
+      if constexpr (TK) {
+        // the group is done with the staged rows: stage the next pair (this
+        // step's, else the next step's first)
+        named_bar(bar, G);
+        if (t == 0 && !kfail) {
+          const bool more = r0 + M < R;
+          if (more || i + 1 < n) {
+            const uint32_t* src = more ? krow + (size_t)(r0 + M) * 2 * KH * N
+                                       : prm.bsk + ((size_t)(i + 1) * P + grp) * R * 2 * KH * N;
+            fence_proxy_async_smem();
+            bulk_copy_g2s(kst, src, kPairWords * 4, kmb);
           }
         }
       }
@@ -525,6 +612,12 @@ blind_rotate_kernel(const BRParams prm) {
       }
     }
     __syncthreads();
+  }
+
+  if constexpr (TK) {
+    // an expired wait leaves at most the copy it waited for in flight: give it
+    // a bounded chance to land before the CTA's shared memory is released
+    if (kfail && t == 0) mbar_wait(kmb, kfph, kWaitLimit);
   }
 
   // SampleExtract of coefficient 0 (appendix figure "Sample and key
