@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdfb_oracle.c")
+_SRC_Q = os.path.join(_HERE, "fdfb_oracle_q.c")  # prime-modulus parameter sets
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
@@ -36,10 +37,11 @@ class or_debug(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, OpenMP for threads over items)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_Q))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, _SRC_Q])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -86,6 +88,28 @@ def lib():
                 "or_tfhe_batch": ([vp, vp, vp, vp, vp, i64, vp, vp], None),
                 "or_fdfb_batch_multi": ([vp, vp, vp, vp, vp, vp, i32, i64, vp, vp], None),
                 "or_lwe_affine": ([i32, i32, i32, i32, vp, vp, vp], None),
+                # prime-modulus sets (fdfb_oracle_q.c; wrapped in oracle/prime_q.py)
+                "orq_mulmod": ([C.c_uint64, C.c_uint64, C.c_uint64], C.c_uint64),
+                "orq_delta": ([C.c_uint64, i32], C.c_uint64),
+                "orq_delta_half": ([C.c_uint64, i32], C.c_uint64),
+                "orq_poly_mul": ([i32, C.c_uint64, vp, vp, vp], None),
+                "orq_poly_mul_xk": ([i32, C.c_uint64, vp, i64, vp], None),
+                "orq_decomp": ([i32, i32, C.c_uint64, vp], None),
+                "orq_lwe_encrypt": ([i32, C.c_uint64, vp, vp, i64, C.c_uint64, vp], None),
+                "orq_lwe_phase": ([i32, C.c_uint64, vp, vp], C.c_uint64),
+                "orq_rlwe_encrypt": ([i32, C.c_uint64, vp, vp, vp, vp, vp], None),
+                "orq_rlwe_phase": ([i32, C.c_uint64, vp, vp, vp], None),
+                "orq_keygen_bsk": ([vp, vp, vp, vp, vp, vp], None),
+                "orq_keygen_pk": ([vp, vp, vp, vp, vp], None),
+                "orq_keygen_ksk": ([vp, vp, vp, vp, vp, vp], None),
+                "orq_extprod": ([vp, vp, vp, vp], None),
+                "orq_blind_rotate": ([vp, vp, vp, vp], None),
+                "orq_sample_extract": ([i32, C.c_uint64, vp, vp], None),
+                "orq_keyswitch": ([i32, C.c_uint64, i32, i32, i32, vp, vp, vp], None),
+                "orq_modswitch": ([C.c_uint64, i32, i32, vp, vp], None),
+                "orq_pubmux": ([vp, vp, vp, vp, vp], None),
+                "orq_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
+                "orq_fdfb_batch": ([vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

@@ -318,3 +318,153 @@ def mlp_inputs_and_weights(seed: int, layers: List[int], n_inputs: int):
         w = st.sub(1 + i).below(layers[i + 1] * layers[i], 16).reshape(layers[i + 1], layers[i]) - 8
         ws.append(w.astype(np.int64))
     return x.astype(np.int64), ws
+
+
+# --------------------------------------------------------------------------
+# Prime-modulus parameter sets (the paper's Table 1)
+# --------------------------------------------------------------------------
+
+Q1 = (1 << 62) - 65535
+Q2 = (1 << 63) - 278527
+Q3 = (1 << 48) - 163839
+Q4 = (1 << 32) - 139263
+
+
+def _ceil_div(a: int, b: int) -> int:
+    return -(-a // b)
+
+
+@dataclasses.dataclass(frozen=True)
+class QParamSet:
+    """A parameter set of Table 1: RLWE side modulo a prime Q, LWE side
+    modulo q = 2N, exact gadget decompositions with l = ceil(log_B Q)
+    digits, l_boot = ceil(log_{L_boot} Q) sign rotations, uniform RLWE key
+    in Z_Q^N, binary LWE key.
+
+    sigma_lwe  : the key-switching key (LWE samples mod Q)
+    sigma_glwe : the bootstrapping and packing keys (RLWE samples mod Q)
+    sigma_in   : fresh input ciphertexts (LWE samples mod q = 2N)
+    """
+    name: str
+    n: int
+    N: int
+    Q: int
+    t: int
+    log2Bg: int
+    log2Bks: int
+    log2Bpk: int
+    log2Lboot: int
+    sigma_lwe: float
+    sigma_glwe: float
+    sigma_in: float = 3.2
+
+    @property
+    def k(self) -> int:          # Q < 2^k
+        return int(self.Q).bit_length()
+
+    @property
+    def logN(self) -> int:
+        return int(self.N).bit_length() - 1
+
+    @property
+    def logq(self) -> int:       # q = 2N
+        return self.logN + 1
+
+    @property
+    def q(self) -> int:
+        return 2 * self.N
+
+    @property
+    def lg(self) -> int:
+        return _ceil_div(self.k, self.log2Bg)
+
+    @property
+    def lks(self) -> int:
+        return _ceil_div(self.k, self.log2Bks)
+
+    @property
+    def lpk(self) -> int:
+        return _ceil_div(self.k, self.log2Bpk)
+
+    @property
+    def lboot(self) -> int:
+        return _ceil_div(self.k, self.log2Lboot)
+
+    @property
+    def delta_q(self) -> int:    # Delta_{q,t} of the input and output ciphertexts
+        return self.q // self.t
+
+
+# Table 1 columns with N <= 4096 (ring degree 2^13 needs more shared memory
+# per ciphertext than one SM has), and QZ, a small set of the same shape for
+# the exhaustive checks.  t is the largest plaintext modulus the paper's
+# correctness table gives a negligible error probability for.
+Q_PARAM_SETS: Dict[str, QParamSet] = {
+    "FDFB-80-6": QParamSet("FDFB-80-6", n=700, N=2048, Q=Q1, t=64, log2Bg=11, log2Bks=6,
+                           log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
+    "FDFB-100-6": QParamSet("FDFB-100-6", n=1050, N=2048, Q=Q1, t=64, log2Bg=11, log2Bks=1,
+                            log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
+    "FDFB-80-7": QParamSet("FDFB-80-7", n=700, N=4096, Q=Q2, t=128, log2Bg=9, log2Bks=4,
+                           log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 39, sigma_glwe=3.2),
+    "FDFB-100-7": QParamSet("FDFB-100-7", n=1100, N=4096, Q=Q2, t=128, log2Bg=9, log2Bks=1,
+                            log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
+    "QZ": QParamSet("QZ", n=24, N=256, Q=Q1, t=8, log2Bg=11, log2Bks=6, log2Bpk=13, log2Lboot=11,
+                    sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
+}
+
+
+def _below_big(st: Stream, count: int, m: int) -> np.ndarray:
+    """Integers in [0, m) for m < 2^64: a raw 64-bit output reduced mod m
+    (bias below m / 2^64)."""
+    return st.raw(count) % np.uint64(m)
+
+
+@dataclasses.dataclass
+class QKeyRandomness:
+    """Everything key generation draws for a prime-Q set.
+
+    s      : uint8[n]            binary LWE key
+    sk     : uint64[N]           RLWE key, uniform in Z_Q (s_F = its coefficients)
+    bsk_a  : uint64[n][2lg][N]   uniform mod Q;  bsk_e int64 (sigma_glwe)
+    pk_a   : uint64[N][lpk][N]   uniform mod Q;  pk_e int64 (sigma_glwe)
+    ksk_a  : uint64[N][lks][n]   uniform mod Q;  ksk_e int64[N][lks] (sigma_lwe)
+    """
+    s: np.ndarray
+    sk: np.ndarray
+    bsk_a: np.ndarray
+    bsk_e: np.ndarray
+    pk_a: np.ndarray
+    pk_e: np.ndarray
+    ksk_a: np.ndarray
+    ksk_e: np.ndarray
+
+
+def q_key_randomness(ps: QParamSet, seed: int) -> QKeyRandomness:
+    st = Stream(seed, STREAM_KEYS, hash_name(ps.name))
+    n, N, Q = ps.n, ps.N, ps.Q
+    s = st.sub(1).bits(n)
+    sk = _below_big(st.sub(2), N, Q)
+    bsk_a = _below_big(st.sub(3), n * 2 * ps.lg * N, Q).reshape(n, 2 * ps.lg, N)
+    bsk_e = st.sub(4).gaussian(n * 2 * ps.lg * N, ps.sigma_glwe).reshape(n, 2 * ps.lg, N)
+    pk_a = _below_big(st.sub(5), N * ps.lpk * N, Q).reshape(N, ps.lpk, N)
+    pk_e = st.sub(6).gaussian(N * ps.lpk * N, ps.sigma_glwe).reshape(N, ps.lpk, N)
+    ksk_a = _below_big(st.sub(7), N * ps.lks * n, Q).reshape(N, ps.lks, n)
+    ksk_e = st.sub(8).gaussian(N * ps.lks, ps.sigma_lwe).reshape(N, ps.lks)
+    return QKeyRandomness(s, sk, bsk_a, bsk_e, pk_a, pk_e, ksk_a, ksk_e)
+
+
+def q_message_randomness(ps: QParamSet, seed: int, count: int, group: int = 0,
+                         m: Optional[np.ndarray] = None) -> MessageRandomness:
+    """Messages in Z_t, masks uniform mod q = 2N, noise sigma_in."""
+    st = Stream(seed, STREAM_MESSAGES, hash_name(ps.name), group)
+    if m is None:
+        m = st.sub(1).below(count, ps.t)
+    a = st.sub(2).below(count * ps.n, ps.q).astype(np.uint64).reshape(count, ps.n)
+    e = st.sub(3).gaussian(count, ps.sigma_in)
+    return MessageRandomness(np.asarray(m, dtype=np.int64), a, e)
+
+
+def q_lut_tables(ps: QParamSet, seed: int, count: int, group: int = 0) -> np.ndarray:
+    """`count` random lookup tables f: Z_t -> Z_t, int64[count][t]."""
+    st = Stream(seed, STREAM_LUTS, hash_name(ps.name), group)
+    return st.below(count * ps.t, ps.t).reshape(count, ps.t)

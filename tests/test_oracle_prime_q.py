@@ -1,0 +1,267 @@
+"""Pins of the prime-modulus oracle (`oracle/fdfb_oracle_q.c`) against what
+the paper and the mathematics fix: brute-force ring products with Python
+integers, exact recomposition of the gadget digits, exact rounding with
+fractions, the GLWE phase identities, the noise bounds of the external
+product, blind rotation and key switching, PubMux on noiseless inputs (an
+exact identity), and the bootstrap's decryption on every message."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.prime_q as OQ
+from paper_2109_02731_gb300 import synth as S
+
+PS = S.Q_PARAM_SETS["QZ"]
+Q = PS.Q
+
+
+@pytest.fixture(scope="module")
+def keys():
+    kr = S.q_key_randomness(PS, 11)
+    return kr, OQ.QKeys(PS, kr)
+
+
+def centred(x: int) -> int:
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+def negacyclic(a, b, N):
+    """Brute force: sum_{i,j} a_i b_j X^{i+j} with X^N = -1, Python integers."""
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                out[k] += int(a[i]) * int(b[j])
+            else:
+                out[k - N] -= int(a[i]) * int(b[j])
+    return [v % Q for v in out]
+
+
+def test_moduli_of_table_1():
+    # Table 1's caption: Q_1 = 2^62 - 65535, ..., Q_4 = 2^32 - 139263;
+    # every set's q is 2N and l = ceil(log_B Q)
+    assert (S.Q1, S.Q2, S.Q3, S.Q4) == (2 ** 62 - 65535, 2 ** 63 - 278527, 2 ** 48 - 163839,
+                                        2 ** 32 - 139263)
+    for ps in S.Q_PARAM_SETS.values():
+        assert ps.q == 2 * ps.N
+        for log2B, ell in ((ps.log2Bg, ps.lg), (ps.log2Bks, ps.lks), (ps.log2Bpk, ps.lpk),
+                           (ps.log2Lboot, ps.lboot)):
+            assert 2 ** (log2B * ell) > ps.Q >= 2 ** (log2B * (ell - 1))
+    p = S.Q_PARAM_SETS["FDFB-80-6"]
+    assert (p.lg, p.lks, p.lpk, p.lboot) == (6, 11, 5, 6)
+
+
+def test_poly_mul_brute_force():
+    rng = np.random.default_rng(1)
+    for N in (1, 2, 8):
+        a = [int(x) for x in rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)]
+        b = [int(x) for x in rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)]
+        a[0] = Q - 1
+        got = [int(x) for x in OQ.poly_mul(Q, a, b)]
+        assert got == negacyclic(a, b, N)
+
+
+def test_poly_mul_xk_is_monomial_product():
+    rng = np.random.default_rng(2)
+    N = 8
+    p = [int(x) for x in rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)]
+    for k in (-17, -1, 0, 3, 8, 15, 16, 21):
+        mono = [0] * N
+        kk = k % (2 * N)
+        mono[kk % N] = 1 if kk < N else Q - 1
+        assert [int(x) for x in OQ.poly_mul_xk(Q, p, k)] == negacyclic(p, mono, N)
+
+
+@pytest.mark.parametrize("log2B", [1, 6, 11, 13])
+def test_exact_decomposition_recomposes(log2B):
+    ell = -(-62 // log2B)
+    rng = np.random.default_rng(log2B)
+    xs = [0, 1, Q - 1, Q // 2] + [int(x) % Q for x in rng.integers(0, 2 ** 63, 50, dtype=np.uint64)]
+    for x in xs:
+        d = [int(v) for v in OQ.decomp(log2B, ell, x)]
+        assert all(0 <= v < 2 ** log2B for v in d)
+        assert sum(v << (log2B * j) for j, v in enumerate(d)) == x
+
+
+def test_deltas_and_modswitch_round_exactly():
+    for t in (2, 8, 64, 128):
+        assert OQ.delta(Q, t) == int(Fraction(Q, t) + Fraction(1, 2))
+        assert OQ.delta_half(Q, t) == int(Fraction(Q, 2 * t) + Fraction(1, 2))
+    rng = np.random.default_rng(3)
+    xs = [0, 1, Q - 1, Q // 2, (Q + 1) // 2] + [int(x) % Q for x in rng.integers(0, 2 ** 63, 200, dtype=np.uint64)]
+    for logq in (9, 12, 13):
+        got = OQ.modswitch(Q, logq, xs)
+        want = [int(Fraction(2 ** logq * x, Q) + Fraction(1, 2)) % 2 ** logq for x in xs]
+        assert [int(v) for v in got] == want
+
+
+def test_rlwe_phase_is_message_plus_noise(keys):
+    kr, _ = keys
+    N = PS.N
+    rng = np.random.default_rng(4)
+    a = kr.pk_a[0, 0]
+    e = rng.integers(-50, 50, N)
+    mu = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+    ct = OQ.rlwe_encrypt(Q, kr.sk, a, e, mu)
+    ph = [int(x) for x in OQ.rlwe_phase(Q, kr.sk, ct)]
+    assert ph == [(int(m) + int(x)) % Q for m, x in zip(mu, e)]
+    # b = a * sk + e + mu by brute force on the first coefficients
+    full = negacyclic([int(x) for x in a], [int(x) for x in kr.sk], N)
+    assert [int(x) for x in ct[0][:4]] == [(full[k] + int(e[k]) + int(mu[k])) % Q for k in range(4)]
+
+
+def test_key_rows_carry_the_gadget(keys):
+    kr, K = keys
+    N, lg = PS.N, PS.lg
+    for i in (0, 5):
+        for r in range(2 * lg):
+            c, j = divmod(r, lg)
+            row = K.bsk[i, r]
+            g = int(kr.s[i]) * (1 << (PS.log2Bg * j)) % Q
+            if c == 0:
+                ph = OQ.rlwe_phase(Q, kr.sk, row)
+                want = [(int(e) + (g if k == 0 else 0)) % Q for k, e in enumerate(kr.bsk_e[i, r])]
+            else:
+                # component 1 carries s_i g_j: phase = e - s_i g_j sk
+                ph = OQ.rlwe_phase(Q, kr.sk, row)
+                want = [(int(e) - g * int(kr.sk[k])) % Q for k, e in enumerate(kr.bsk_e[i, r])]
+            assert [int(x) for x in ph] == want
+    # ksK[i][j] = LWE_s(s_F[i] B^(j-1))
+    for i in (0, 100):
+        for j in (0, PS.lks - 1):
+            ph = OQ.lwe_phase_q(Q, kr.s.astype(np.uint64), K.ksk[i, j])
+            assert ph == (int(kr.sk[i]) * (1 << (PS.log2Bks * j)) + int(kr.ksk_e[i, j])) % Q
+
+
+def test_external_product_message_and_noise(keys):
+    kr, K = keys
+    N = PS.N
+    rng = np.random.default_rng(5)
+    i = int(np.flatnonzero(kr.s)[0])  # RGSW(1)
+    mu = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+    d = OQ.rlwe_encrypt(Q, kr.sk, kr.pk_a[1, 0], np.zeros(N, np.int64), mu)
+    out = OQ.extprod(PS, K.bsk[i], d)
+    ph = OQ.rlwe_phase(Q, kr.sk, out)
+    # phase = 1 * mu + sum_r D_r e_r: |noise| <= 2 lg N (B - 1) max|e|
+    bound = 2 * PS.lg * N * (2 ** PS.log2Bg - 1) * int(np.abs(kr.bsk_e[i]).max())
+    noise = [centred(int(p) - int(m)) for p, m in zip(ph, mu)]
+    assert max(abs(v) for v in noise) <= bound
+    assert max(abs(v) for v in noise) > 0
+
+
+def test_blind_rotation_rotates_by_the_phase(keys):
+    kr, K = keys
+    N, n = PS.N, PS.n
+    rng = np.random.default_rng(6)
+    ctN = np.concatenate([[0], rng.integers(0, 2 * N, n)]).astype(np.uint64)
+    h = OQ.delta_half(Q, PS.t)
+    acc0 = np.zeros((2, N), dtype=np.uint64)
+    acc0[0, 0] = h
+    acc = OQ.blind_rotate(PS, K.bsk, acc0, ctN)
+    # message h X^{-sum a_i s_i}
+    rot = -int(sum(int(a) * int(s) for a, s in zip(ctN[1:], kr.s)))
+    want = OQ.poly_mul_xk(Q, acc0[0], rot)
+    ph = OQ.rlwe_phase(Q, kr.sk, acc)
+    noise = [centred(int(p) - int(w)) for p, w in zip(ph, want)]
+    bound = n * 2 * PS.lg * N * (2 ** PS.log2Bg - 1) * int(np.abs(kr.bsk_e).max())
+    assert max(abs(v) for v in noise) <= bound
+    assert max(abs(v) for v in noise) < h // 1000
+
+
+def test_sample_extract_is_coefficient_zero(keys):
+    kr, K = keys
+    rng = np.random.default_rng(7)
+    N = PS.N
+    mu = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+    ct = OQ.rlwe_encrypt(Q, kr.sk, kr.pk_a[2, 0], np.zeros(N, np.int64), mu)
+    lwe = OQ.sample_extract(Q, ct)
+    assert OQ.lwe_phase_q(Q, kr.sk, lwe) == int(mu[0])
+
+
+def test_keyswitch_preserves_phase(keys):
+    kr, K = keys
+    N, n = PS.N, PS.n
+    rng = np.random.default_rng(8)
+    a = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+    m = 123456789123
+    ct = OQ.lwe_encrypt_q(Q, kr.sk, a, 0, m)
+    out = OQ.keyswitch(Q, PS.log2Bks, PS.lks, K.ksk, ct)
+    ph = OQ.lwe_phase_q(Q, kr.s.astype(np.uint64), out)
+    bound = N * PS.lks * (2 ** PS.log2Bks - 1) * int(np.abs(kr.ksk_e).max())
+    assert abs(centred(ph - m)) <= bound
+    # packing key: LWE dim N -> RLWE, constant term keeps the phase
+    rl = OQ.keyswitch(Q, PS.log2Bpk, PS.lpk, K.pk, ct).reshape(2, N)
+    rph = OQ.rlwe_phase(Q, kr.sk, rl)
+    bound = N * PS.lpk * (2 ** PS.log2Bpk - 1) * int(np.abs(kr.pk_e).max()) * 1
+    assert abs(centred(int(rph[0]) - m)) <= bound
+    assert all(abs(centred(int(v))) <= bound for v in rph[1:])
+
+
+def test_pubmux_is_exact_on_noiseless_inputs():
+    # c_i = [m L^(i-1), 0] (trivial RLWE samples): out = [Delta p_0 + m p, 0]
+    # exactly, so m = 0 gives Delta p_0 and m = Delta gives Delta p_1
+    N = PS.N
+    rng = np.random.default_rng(9)
+    p0 = rng.integers(-PS.t + 1, PS.t, N)
+    p1 = rng.integers(-PS.t + 1, PS.t, N)
+    D = OQ.delta(Q, PS.t)
+    for m, pick in ((0, p0), (D, p1)):
+        c = np.zeros((PS.lboot, 2, N), dtype=np.uint64)
+        for i in range(PS.lboot):
+            c[i, 0, 0] = m * (1 << (PS.log2Lboot * i)) % Q
+        out = OQ.pubmux(PS, c, p0, p1)
+        want = [D * int(v) % Q for v in pick]
+        assert [int(x) for x in out[0]] == want
+        assert not out[1].any()
+
+
+def test_bootstrap_every_message(keys):
+    kr, K = keys
+    tables = S.q_lut_tables(PS, 11, 2)
+    rot = OQ.rotation_polys(PS, tables)
+    for li, f in enumerate(tables):
+        mr = S.q_message_randomness(PS, 11, PS.t, group=li, m=np.arange(PS.t))
+        cts = OQ.encrypt_messages(PS, kr.s, mr)
+        out = OQ.fdfb_batch(PS, K, rot, np.full(PS.t, li, np.int32), cts, threads=oracle.max_threads())
+        assert [OQ.decrypt(PS, kr.s, o) for o in out] == [int(v) for v in f]
+
+
+def test_bootstrap_intermediates(keys):
+    kr, K = keys
+    f = S.q_lut_tables(PS, 11, 1)[0]
+    rot = OQ.rotation_polys(PS, [f])[0]
+    for m in (0, PS.t - 1):
+        mr = S.q_message_randomness(PS, 12, 1, m=np.array([m]))
+        ct = OQ.encrypt_messages(PS, kr.s, mr)[0]
+        out, dbg = OQ.fdfb_bootstrap(PS, K, rot[0], rot[1], ct, debug=True)
+        # sign LWE i encrypts L^(i-1) * 2 round(Q/2t) * beta, beta = [phase_N in [0, N)]
+        phN = (int(ct[0]) - sum(int(a) * int(s) for a, s in zip(ct[1:], kr.s))) % PS.q
+        beta = 1 if phN < PS.N else 0
+        h = OQ.delta_half(Q, PS.t)
+        for i in range(PS.lboot):
+            ph = OQ.lwe_phase_q(Q, kr.sk, dbg["sgn"][i])
+            want = (1 << (PS.log2Lboot * i)) * 2 * h * beta % Q
+            assert abs(centred(ph - want)) < h // 1000
+        # cKS decrypts under s to Delta_Q f(m); out is its ModSwitch to q
+        ph = OQ.lwe_phase_q(Q, kr.s.astype(np.uint64), dbg["cKS"])
+        assert abs(centred(ph - OQ.delta(Q, PS.t) * int(f[m]))) < OQ.delta(Q, PS.t) // 8
+        assert np.array_equal(out, OQ.modswitch(Q, PS.logq, dbg["cKS"]))
+
+
+def test_single_digit_pubmux_decrypts_alike(keys):
+    # l_boot = 1 (L_boot >= Q): one sign rotation, the selector one digit
+    # of 62 bits; the outputs differ in their noise but decrypt alike
+    import dataclasses
+    kr, K = keys
+    ps1 = dataclasses.replace(PS, log2Lboot=62)
+    assert ps1.lboot == 1
+    f = S.q_lut_tables(PS, 11, 1)[0]
+    rot = OQ.rotation_polys(PS, [f])
+    mr = S.q_message_randomness(PS, 13, PS.t, m=np.arange(PS.t))
+    cts = OQ.encrypt_messages(PS, kr.s, mr)
+    out = OQ.fdfb_batch(ps1, K, rot, np.zeros(PS.t, np.int32), cts, threads=oracle.max_threads())
+    assert [OQ.decrypt(PS, kr.s, o) for o in out] == [int(v) for v in f]
