@@ -79,6 +79,32 @@ typedef struct {
    * PubMux by Delta' = q / t', table entries lie in Z_t', and the bootstrap's
    * outputs encrypt Delta' f(m). */
   uint32_t t_out;
+  /* Prime-modulus parameter sets (Table 1); 0 selects q = Q = 2^log2q
+   * (everything above).  Q = 2^k - c with 33 <= k <= 63 and odd c < 2^20
+   * (the paper's Q_1 = 2^62 - 65535, Q_2 = 2^63 - 278527, Q_3 = 2^48 -
+   * 163839) runs the paper's Bootstrap figure literally:
+   *   - the RLWE side (keys, accumulators, the extracted and key-switched
+   *     LWE samples) lives mod Q in 64-bit words (log2q = 64);
+   *   - the LWE side lives mod q = 2N: input and output ciphertexts are
+   *     [n+1] 64-bit words in [0, 2N), Delta_q = 2N / t, so the first
+   *     ModSwitch (q -> 2N) is the identity and the last is ModSwitch(Q -> q),
+   *     round(q x / Q) round half up;
+   *   - every gadget decomposition is exact: lg, lks, lpk must equal
+   *     ceil(k / log2B) for their bases (digits of x in [0, Q), least
+   *     significant first, gadget B^(j-1));
+   *   - lboot = ceil(k / log2Lboot) <= 8 sign blind rotations per input, the
+   *     i-th starting from L_boot^(i-1) round(Q / 2t) sgnP X^{b_N} and adding
+   *     the same constant after SampleExtract; each sign LWE is key switched
+   *     to RLWE; PubMux splits p = rotP'_0 - rotP'_1 in Z_Q into lboot
+   *     base-L_boot digits and returns [round(Q/t) rotP'_1, 0] + sum_i p[i]
+   *     c_R,i; the function rotation, SampleExtract and KeySwitch(ksK) follow,
+   *     then ModSwitch(Q -> q);
+   *   - N is 256, 2048 or 4096; signed_digits and t_out must be 0;
+   *     fdfb_bootstrap_multi (k > 1), the TFHE bootstrap and fdfb_lwe_affine
+   *     are not available (FDFB_EINVAL).
+   * Keys are uploaded in the canonical layouts as residues mod Q; the RLWE
+   * key of fdfb_keys_generate is uniform in Z_Q^N (fdfb_keygen_inputs.sk_q). */
+  uint64_t Q;
 } fdfb_params;
 
 /* Concurrency.  Every call is stream-ordered.  A parameter set owns one
@@ -129,7 +155,8 @@ int fdfb_keys_upload(fdfb_ctx* ctx, int set_id, const void* bsk, const void* pk,
 /* Randomness of key generation (host pointers; words are w-bit residues,
  * noise is signed):  s[n], sk[N] binary keys (s_F = Coefs(sk));
  * bsk_a/bsk_e [n][2 lg][N]; pk_a/pk_e [N][lpk][N]; ksk_a [N][lks][n];
- * ksk_e [N][lks]. */
+ * ksk_e [N][lks].  Prime-modulus sets: the masks are 64-bit residues mod Q,
+ * sk is unused and sk_q [N] (uint64 residues mod Q) is the RLWE key. */
 typedef struct {
   const uint8_t* s;
   const uint8_t* sk;
@@ -139,6 +166,7 @@ typedef struct {
   const int64_t* pk_e;
   const void* ksk_a;
   const int64_t* ksk_e;
+  const uint64_t* sk_q;
 } fdfb_keygen_inputs;
 
 /* Generates the keys on the GPU from the given randomness -- BRKeyGen and
@@ -209,13 +237,19 @@ int fdfb_bootstrap_multi(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
  *   sgn  words [N+1]   SampleExtract of the sign rotation + [Delta/2, 0]
  *   cR   words [2N]    KeySwitch(sgn, pK)
  *   accF words [2N]    PubMux(cR, rotP'_1, rotP'_0)
- *   cQ   words [N+1]   SampleExtract of the function rotation */
+ *   cQ   words [N+1]   SampleExtract of the function rotation
+ *   cKS  words [n+1]   (prime-modulus sets) KeySwitch(cQ, ksK) mod Q, before
+ *                      ModSwitch(Q -> q)
+ * Prime-modulus sets hold lboot sign LWEs and packed RLWEs per input (sgn
+ * [lboot][N+1], cR [lboot][2N]) and produce no ctN (the input is already
+ * modulo 2N). */
 typedef struct {
   void* ctN;
   void* sgn;
   void* cR;
   void* accF;
   void* cQ;
+  void* cKS;
 } fdfb_debug_bufs;
 
 int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
@@ -267,13 +301,13 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
 
 /* LWE key switching with the installed ksK (figure "Key switching algorithm
  * and its setup"): ct_in device [batch][N+1] words under s_F, ct_out device
- * [batch][n+1] words under s. */
+ * [batch][n+1] words under s (prime-modulus sets: both mod Q). */
 int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
                    void* cuda_stream);
 
 /* LWE encryption b = <a, s> + e + Delta m (device pointers):  s uint8[n];
  * a [count][n] words; e int64[count]; m int64[count] (in Z_t);
- * ct_out [count][n+1] words. */
+ * ct_out [count][n+1] words.  Prime-modulus sets: mod q = 2N, Delta = 2N/t. */
 int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,
                      const int64_t* m, int64_t count, void* ct_out, void* cuda_stream);
 

@@ -23,6 +23,19 @@ const Ops* ops_n10(int w, int variant);
 const Ops* ops_n11(int w, int variant);
 const Ops* ops_n12(int w, int variant);
 
+const Ops* ops_q_n8(int variant);
+const Ops* ops_q_n11(int variant);
+const Ops* ops_q_n12(int variant);
+
+const Ops* find_ops_q(int L, int variant) {
+  switch (L) {
+    case 8: return ops_q_n8(variant);
+    case 11: return ops_q_n11(variant);
+    case 12: return ops_q_n12(variant);
+    default: return nullptr;
+  }
+}
+
 const Ops* find_ops(int L, int w, int variant) {
   switch (L) {
     case 8: return ops_n8(w, variant);
@@ -90,6 +103,12 @@ struct SetState {
   int n_tpolys = 0;
   DevBuf scratch;   // sgn | cR | accF | cQ for the largest batch seen
   int chunks = 1;  // pieces fdfb_bootstrap splits a large batch into (set by fdfb_autotune)
+  // prime-modulus sets (prm.Q != 0)
+  ModQ mq{};                 // mq.Q == 0 for the power-of-two sets
+  int lboot = 1;             // sign rotations per input
+  uint64_t sgn_scale[8] = {0};  // L_boot^i round(Q / 2t) mod Q
+  uint64_t delta_q = 0;      // round(Q / t)
+  DevBuf pk_split, ksk_split;  // key-switch layouts: 32-bit halves as columns
   size_t wbytes() const { return (size_t)w / 8; }
   Variant& base() { return *var[0]; }
   Variant& br() { return *var[cur]; }
@@ -195,16 +214,37 @@ int install_bsk_ntt(SetState& st, cudaStream_t s) {
   for (auto& v : st.var) {
     FD_TRY(v->bsk_ntt.ensure((size_t)P.n * v->ops->P * 2 * P.lg * 2 * v->ops->key_halves * N * 4));
     FD_CUDA(v->ops->bsk_ntt(v->S, st.bsk.p, (int64_t)P.n * 2 * P.lg, 2 * (int)P.lg,
-                            (uint32_t*)v->bsk_ntt.p, s));
+                            (uint32_t*)v->bsk_ntt.p, st.mq.Q, s));
   }
   return FDFB_OK;
+}
+
+// Prime-modulus sets: the key-switching keys as 32-bit halves in separate
+// columns (what keyswitch_kernel<uint64_t, uint32_t> reads).
+int install_split_keys(SetState& st, cudaStream_t s) {
+  const fdfb_params& P = st.prm;
+  const int64_t N = P.N, n = P.n;
+  FD_TRY(st.pk_split.ensure((size_t)N * P.lpk * 2 * N * 2 * 4));
+  FD_TRY(st.ksk_split.ensure((size_t)N * P.lks * (n + 1) * 2 * 4));
+  split_halves_kernel<<<1024, 256, 0, s>>>((const uint64_t*)st.pk.p, N * P.lpk, (int)(2 * N),
+                                          (uint32_t*)st.pk_split.p);
+  split_halves_kernel<<<1024, 256, 0, s>>>((const uint64_t*)st.ksk.p, N * P.lks, (int)(n + 1),
+                                          (uint32_t*)st.ksk_split.p);
+  return cuda_err(cudaGetLastError());
 }
 
 // Pipeline intermediates for `batch` inputs with k tables each: per input the
 // sign LWE [N+1] and the packed RLWE [2N], per (input, table) the function
 // accumulator [2N] and the extracted LWE [N+1].
+// Prime-modulus sets (k = 1): per input lboot sign LWEs [N+1], their raw
+// packing key-switch sums [4N] and packed RLWEs [2N], then accF [2N], cQ
+// [N+1] and the raw LWE key-switch sums [2(n+1)], all 64-bit words.
 size_t scratch_bytes(const SetState& st, int64_t batch, int k) {
   const size_t N = st.prm.N;
+  if (st.mq.Q) {
+    const size_t lb = st.lboot, n = st.prm.n;
+    return (size_t)batch * (lb * ((N + 1) + 4 * N + 2 * N) + 2 * N + (N + 1) + 2 * (n + 1)) * 8;
+  }
   return ((size_t)batch * ((N + 1) + 2 * N) + (size_t)batch * k * (2 * N + (N + 1))) * st.wbytes();
 }
 
@@ -243,6 +283,37 @@ int launch_keyswitch(const fdfb_ctx* ctx, int w, const void* in, int64_t batch, 
   return cuda_err(cudaGetLastError());
 }
 
+// Prime-modulus key switching: the exact sums of the two key halves
+// (keyswitch_kernel<uint64_t, uint32_t>, raw), then ks_finalize_q_kernel:
+// out = ([b, 0..] - sums) mod Q, and with logq > 0 ModSwitch(Q -> 2^logq).
+int launch_keyswitch_q(const fdfb_ctx* ctx, const SetState& st, const uint64_t* in, int64_t batch,
+                       int n_in, const uint32_t* key_split, int ell, int log2B, int out_len,
+                       uint64_t* sums, int logq, uint64_t* out, cudaStream_t s) {
+  if (batch <= 0) return FDFB_OK;
+  const int cols = 2 * out_len;
+  const int64_t tiles = (int64_t)((cols + KS_BN - 1) / KS_BN) * ((batch + KS_BM - 1) / KS_BM);
+  const int kt = (n_in * ell + KS_BK - 1) / KS_BK;
+  int64_t split = (2 * (int64_t)ctx->sms + tiles - 1) / tiles;
+  if (split > kt / 4) split = kt / 4;
+  if (split > 64) split = 64;
+  if (split < 1) split = 1;
+  dim3 grid((unsigned)((batch + KS_BM - 1) / KS_BM), (unsigned)((cols + KS_BN - 1) / KS_BN), (unsigned)split);
+  if (split > 1) FD_CUDA(cudaMemsetAsync(sums, 0, (size_t)batch * cols * 8, s));
+  keyswitch_kernel<uint64_t, uint32_t><<<grid, KS_THREADS, 0, s>>>(in, batch, n_in, key_split, ell, log2B, 0,
+                                                                   cols, sums, (int)split, 1);
+  FD_CUDA(cudaGetLastError());
+  const int64_t total = batch * out_len;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->sms);
+  ks_finalize_q_kernel<<<blocks, 256, 0, s>>>(in, n_in, batch, sums, out_len, st.mq, logq, out);
+  return cuda_err(cudaGetLastError());
+}
+
+void fill_br_q(BRParams& br, const SetState& st) {
+  br.mq = st.mq;
+  for (int i = 0; i < 8; ++i) br.sgn_scale[i] = st.sgn_scale[i];
+  br.rtrunc = 0;
+}
+
 // Pipeline stages as NVTX ranges (shown by external profilers on the host
 // timeline, with the launches they enqueue).
 const char* const kStageNames[kStages] = {
@@ -274,6 +345,105 @@ struct StageTimer {
   }
 };
 
+// The Bootstrap figure for a prime-modulus set (one table per input):
+// lboot sign rotations per input (item i of input b starts from L_boot^i
+// Delta/2 sgnP X^{b_N}), SampleExtract + the same constant, the packing key
+// switch of every sign LWE, PubMux over the lboot digits of p, the function
+// rotation, SampleExtract, KeySwitch(ksK) and ModSwitch(Q -> q = 2N).
+int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
+                   int64_t batch, int k, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
+                   void* fixed_scratch, bool timed) {
+  if (k != 1) return FDFB_EINVAL;
+  const fdfb_params& P = st.prm;
+  const size_t N = P.N, n = P.n, lb = st.lboot;
+  if (batch * (int64_t)lb > 0x7fffffff) return FDFB_EINVAL;
+  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, 1));
+  unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
+  fdfb_ctx* tctx = timed ? ctx : nullptr;
+  uint64_t* sgn = (uint64_t*)base;
+  uint64_t* sums_pk = sgn + (size_t)batch * lb * (N + 1);
+  uint64_t* cR = sums_pk + (size_t)batch * lb * 4 * N;
+  uint64_t* accF = cR + (size_t)batch * lb * 2 * N;
+  uint64_t* cQ = accF + (size_t)batch * 2 * N;
+  uint64_t* sums_ks = cQ + (size_t)batch * (N + 1);
+  if (dbg) {
+    if (dbg->sgn) sgn = (uint64_t*)dbg->sgn;
+    if (dbg->cR) cR = (uint64_t*)dbg->cR;
+    if (dbg->accF) accF = (uint64_t*)dbg->accF;
+    if (dbg->cQ) cQ = (uint64_t*)dbg->cQ;
+  }
+  const int64_t items = batch * (int64_t)lb;
+  Variant& bv = st.br();
+  BRParams br{};
+  br.S = bv.S;
+  br.bsk = (const uint32_t*)bv.bsk_ntt.p;
+  br.ct = ct_in;
+  br.acc0 = nullptr;
+  br.lwe_out = sgn;
+  br.ctN_out = nullptr;
+  br.n = P.n;
+  br.lg = P.lg;
+  br.log2Bg = P.log2Bg;
+  br.batch = items;
+  br.sign_mode = 1;
+  br.smem_r1 = bv.br_r1;
+  br.smem_exch = bv.br_ex;
+  br.rep = (int)lb;
+  br.signed_digits = 0;
+  br.err = ctx->d_err;
+  fill_br_q(br, st);
+  {
+    StageTimer tm(tctx, 0, s);
+    FD_CUDA(bv.ops->br(br, items, bv.br_smem, s));
+  }
+  {
+    StageTimer tm(tctx, 1, s);
+    FD_TRY(launch_keyswitch_q(ctx, st, sgn, items, (int)N, (const uint32_t*)st.pk_split.p, P.lpk,
+                              P.log2Bpk, (int)(2 * N), sums_pk, 0, cR, s));
+  }
+  PubMuxQParams pm{};
+  pm.S = st.base().S;
+  pm.mq = st.mq;
+  pm.cR = cR;
+  pm.ct = (const uint64_t*)ct_in;
+  pm.rep = 1;
+  pm.lut_ids = lut_ids;
+  pm.luts = (const int16_t*)st.luts.p;
+  pm.n_luts = st.n_luts;
+  pm.accF = accF;
+  pm.n = P.n;
+  pm.lboot = (int)lb;
+  pm.log2Lboot = (int)P.log2Lboot;
+  pm.delta = st.delta_q;
+  pm.err = ctx->d_err;
+  {
+    StageTimer tm(tctx, 2, s);
+    FD_CUDA(st.base().ops->pubmux_q(pm, batch, s));
+  }
+  br.acc0 = accF;
+  br.lwe_out = cQ;
+  br.sign_mode = 0;
+  br.batch = batch;
+  br.rep = 1;
+  {
+    StageTimer tm(tctx, 3, s);
+    FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
+  }
+  {
+    StageTimer tm(tctx, 4, s);
+    FD_TRY(launch_keyswitch_q(ctx, st, cQ, batch, (int)N, (const uint32_t*)st.ksk_split.p, P.lks,
+                              P.log2Bks, (int)n + 1, sums_ks, (int)st.L + 1, (uint64_t*)ct_out, s));
+    if (dbg && dbg->cKS) {
+      const int64_t total = batch * (int64_t)(n + 1);
+      const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->sms);
+      ks_finalize_q_kernel<<<blocks, 256, 0, s>>>(cQ, (int)N, batch, sums_ks, (int)n + 1, st.mq, 0,
+                                                 (uint64_t*)dbg->cKS);
+      FD_CUDA(cudaGetLastError());
+    }
+  }
+  return FDFB_OK;
+}
+
 // One bootstrap pipeline on one parameter set (figure "functional-
 // bootstrapping", left), steps 1-14, for `batch` inputs and k tables per
 // input: steps 1-10 (sign rotation, packing key switch) once per input, steps
@@ -290,6 +460,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   if (!st.keys) return FDFB_ENOKEYS;
   if (st.n_luts == 0) return FDFB_EBADLUT;
   if (batch * (int64_t)k > 0x7fffffff) return FDFB_EINVAL;
+  if (st.mq.Q) return run_pipeline_q(ctx, st, ct_in, lut_ids, batch, k, ct_out, dbg, s, fixed_scratch, timed);
   const fdfb_params& P = st.prm;
   const size_t N = P.N, wb = st.wbytes();
   const int64_t items = batch * k;
@@ -515,6 +686,179 @@ int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
   return FDFB_OK;
 }
 
+// Registration of a prime-modulus set (fdfb_params.Q != 0): checks the
+// shape (Q = 2^k - c, exact decompositions, l_boot <= 8), the exactness of
+// every lift with the primes of each variant, and builds the variants.
+int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
+  if (P.k != 1 || P.log2q != 64) return FDFB_EINVAL;
+  if (P.N != 256 && P.N != 2048 && P.N != 4096) return FDFB_EINVAL;
+  if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
+  if (!is_pow2(P.t) || P.t < 2 || P.t > P.N) return FDFB_EINVAL;
+  if (P.signed_digits || P.t_out) return FDFB_EINVAL;
+  const uint64_t Q = P.Q;
+  int kbits = 64;
+  while (kbits > 0 && !((Q >> (kbits - 1)) & 1)) --kbits;
+  if (kbits < 33 || kbits > 63) return FDFB_EINVAL;
+  const uint64_t c = ((uint64_t)1 << kbits) - Q;
+  if (!(Q & 1) || c == 0 || c >= ((uint64_t)1 << 20)) return FDFB_EINVAL;
+  auto exact_l = [&](uint32_t log2B, uint32_t l) {
+    return log2B >= 1 && log2B <= 16 && l == (uint32_t)((kbits + (int)log2B - 1) / (int)log2B);
+  };
+  if (!exact_l(P.log2Bg, P.lg) || !exact_l(P.log2Bks, P.lks) || !exact_l(P.log2Bpk, P.lpk)) return FDFB_EINVAL;
+  if (P.log2Lboot < 1 || P.log2Lboot > 63 ||
+      P.lboot != (uint32_t)((kbits + (int)P.log2Lboot - 1) / (int)P.log2Lboot) || P.lboot > 8)
+    return FDFB_EINVAL;
+  if (P.lg > 7) return FDFB_EINVAL;
+  const int L = ilog2(P.N);
+  const Ops* ops0 = find_ops_q(L, 0);
+  if (!ops0 || ops0->P != 3) return FDFB_EINVAL;
+  const long double B = ldexpl(1.0L, (int)P.log2Bg), Qh = (long double)Q / 2;
+  const long double br_max = 2.0L * P.lg * P.N * (B - 1) * Qh;
+  const long double pm_max = (long double)P.lboot * P.N * (ldexpl(1.0L, (int)std::min<uint32_t>(P.log2Lboot, 62)) - 1) * Qh;
+  const long double enc_max = (long double)P.N * ldexpl(1.0L, kSkLimbBits - 1) * Qh;
+  if (!host::lift_is_exact(3, br_max) || !host::lift_is_exact(3, pm_max) || !host::lift_is_exact(3, enc_max))
+    return FDFB_EINVAL;
+
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  auto st = std::make_unique<SetState>();
+  st->prm = P;
+  st->w = 64;
+  st->L = L;
+  st->logt = ilog2(P.t);
+  st->tout = (int)P.t;
+  st->logtout = st->logt;
+  st->mq = ModQ{Q, c, kbits};
+  st->lboot = (int)P.lboot;
+  const uint64_t h = (uint64_t)(((unsigned __int128)Q + P.t) / (2 * (uint64_t)P.t));  // round(Q / 2t)
+  st->delta_q = (uint64_t)(((unsigned __int128)Q + P.t / 2) / P.t);                // round(Q / t)
+  uint64_t Lpow = 1;
+  for (int i = 0; i < st->lboot; ++i) {
+    st->sgn_scale[i] = host::mulmod(Lpow, h, Q);
+    Lpow = host::mulmod(Lpow, P.log2Lboot >= 64 ? 0 : (((uint64_t)1 << P.log2Lboot) % Q), Q);
+  }
+  int max_smem = 0;
+  FD_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  for (int vi = 0;; ++vi) {
+    const Ops* ops = find_ops_q(L, vi);
+    if (!ops) break;
+    if ((int)P.log2Bg > ops->max_log2B) continue;
+    if (ops->key_halves == 2 && !host::lift_is_exact(ops->P, 2.0L * P.lg * P.N * (B - 1) * ldexpl(1.0L, 31)))
+      continue;
+    if (ops->key_halves == 1 && !host::lift_is_exact(ops->P, br_max)) continue;
+    auto v = std::make_unique<Variant>();
+    v->ops = ops;
+    v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);
+    if (v->br_smem > (size_t)max_smem) continue;
+    FD_CUDA(ops->br_prepare(v->br_smem));
+    std::vector<uint2> fwd, inv;
+    host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv, ops->family);
+    FD_TRY(v->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
+    FD_CUDA(cudaMemcpy(v->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+    FD_CUDA(cudaMemcpy((uint2*)v->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),
+                       cudaMemcpyHostToDevice));
+    v->S.tw_fwd = (const uint2*)v->tw.p;
+    v->S.tw_inv = (const uint2*)v->tw.p + fwd.size();
+    st->var.push_back(std::move(v));
+  }
+  if (st->var.empty() || st->var[0]->ops != ops0) return FDFB_EINVAL;
+  ctx->sets.push_back(std::move(st));
+  *set_id_out = (int)ctx->sets.size() - 1;
+  return FDFB_OK;
+}
+
+// Key generation of a prime-modulus set: GLWE samples with the uniform key
+// sk_q (rlwe_encrypt_q_kernel over its 13-bit limbs) and LWE samples mod Q.
+int keys_generate_q(fdfb_ctx* ctx, SetState* st, const fdfb_keygen_inputs* in, cudaStream_t s) {
+  if (!in->sk_q) return FDFB_EINVAL;
+  const fdfb_params& P = st->prm;
+  const size_t n = P.n, N = P.N;
+  const uint64_t Q = st->mq.Q;
+  for (size_t j = 0; j < N; ++j)
+    if (in->sk_q[j] >= Q) return FDFB_EINVAL;
+  uint64_t wb_, wp_, wk_;
+  fdfb_key_words(&P, 0, &wb_);
+  fdfb_key_words(&P, 1, &wp_);
+  fdfb_key_words(&P, 2, &wk_);
+  FD_TRY(st->bsk.ensure(wb_ * 8));
+  FD_TRY(st->pk.ensure(wp_ * 8));
+  FD_TRY(st->ksk.ensure(wk_ * 8));
+  Variant& v0 = st->base();
+  DevBuf d_sk, d_limbs, d_skl, d_s, d_a, d_e, d_mu, d_comp;
+  FD_TRY(d_sk.ensure(N * 8));
+  FD_TRY(d_limbs.ensure((size_t)kSkLimbs * 2 * N * 8));
+  FD_TRY(d_skl.ensure((size_t)kSkLimbs * v0.ops->P * 2 * N * 4));
+  FD_TRY(d_s.ensure(n));
+  FD_CUDA(cudaMemcpyAsync(d_sk.p, in->sk_q, N * 8, cudaMemcpyHostToDevice, s));
+  FD_CUDA(cudaMemcpyAsync(d_s.p, in->s, n, cudaMemcpyHostToDevice, s));
+  sk_limbs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((const uint64_t*)d_sk.p, (int)N, st->mq,
+                                                             (uint64_t*)d_limbs.p);
+  FD_CUDA(cudaGetLastError());
+  FD_CUDA(v0.ops->bsk_ntt(v0.S, d_limbs.p, kSkLimbs, 1, (uint32_t*)d_skl.p, Q, s));
+  auto glwe = [&](size_t rows, const void* a, const int64_t* e, const std::vector<uint64_t>& mu,
+                  const std::vector<uint8_t>& comp, void* out) -> int {
+    FD_TRY(d_a.ensure(rows * N * 8));
+    FD_TRY(d_e.ensure(rows * N * 8));
+    FD_TRY(d_mu.ensure(rows * 8));
+    FD_TRY(d_comp.ensure(rows));
+    FD_CUDA(cudaMemcpyAsync(d_a.p, a, rows * N * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_e.p, e, rows * N * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_comp.p, comp.data(), rows, cudaMemcpyHostToDevice, s));
+    RlweEncQParams rp{v0.S, st->mq, (const uint32_t*)d_skl.p, (const uint64_t*)d_a.p, (const int64_t*)d_e.p,
+                      (const uint64_t*)d_mu.p, (const uint8_t*)d_comp.p, (uint64_t*)out};
+    FD_CUDA(v0.ops->rlwe_enc_q(rp, (int64_t)rows, s));
+    FD_CUDA(cudaStreamSynchronize(s));
+    return FDFB_OK;
+  };
+  auto gpow = [&](uint32_t log2B, int j) {  // B^j mod Q
+    uint64_t r = 1;
+    for (int i = 0; i < j; ++i) r = host::mulmod(r, ((uint64_t)1 << log2B) % Q, Q);
+    return r;
+  };
+  {  // BRKeyGen: row r = c lg + j adds s_i B^j to component c
+    const size_t rows = n * 2 * P.lg;
+    std::vector<uint64_t> mu(rows);
+    std::vector<uint8_t> comp(rows);
+    for (size_t i = 0; i < n; ++i)
+      for (size_t r = 0; r < 2 * P.lg; ++r) {
+        mu[i * 2 * P.lg + r] = in->s[i] ? gpow(P.log2Bg, (int)(r % P.lg)) : 0;
+        comp[i * 2 * P.lg + r] = (uint8_t)(r / P.lg);
+      }
+    FD_TRY(glwe(rows, in->bsk_a, in->bsk_e, mu, comp, st->bsk.p));
+  }
+  {  // pK: RLWE(s_F[i] B_pk^j), s_F = Coefs(sk_q)
+    const size_t rows = N * P.lpk;
+    std::vector<uint64_t> mu(rows);
+    std::vector<uint8_t> comp(rows, 0);
+    for (size_t i = 0; i < N; ++i)
+      for (size_t j = 0; j < P.lpk; ++j) mu[i * P.lpk + j] = host::mulmod(in->sk_q[i], gpow(P.log2Bpk, (int)j), Q);
+    FD_TRY(glwe(rows, in->pk_a, in->pk_e, mu, comp, st->pk.p));
+  }
+  {  // ksK: LWE_s(s_F[i] B_ks^j)
+    const size_t rows = N * P.lks;
+    std::vector<uint64_t> mu(rows);
+    for (size_t i = 0; i < N; ++i)
+      for (size_t j = 0; j < P.lks; ++j) mu[i * P.lks + j] = host::mulmod(in->sk_q[i], gpow(P.log2Bks, (int)j), Q);
+    FD_TRY(d_a.ensure(rows * n * 8));
+    FD_TRY(d_e.ensure(rows * 8));
+    FD_TRY(d_mu.ensure(rows * 8));
+    FD_CUDA(cudaMemcpyAsync(d_a.p, in->ksk_a, rows * n * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_e.p, in->ksk_e, rows * 8, cudaMemcpyHostToDevice, s));
+    FD_CUDA(cudaMemcpyAsync(d_mu.p, mu.data(), rows * 8, cudaMemcpyHostToDevice, s));
+    lwe_encrypt_q_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(
+        (const uint8_t*)d_s.p, (const uint64_t*)d_a.p, (const int64_t*)d_e.p, (const uint64_t*)d_mu.p,
+        (int64_t)rows, (int)n, st->mq, (uint64_t*)st->ksk.p);
+    FD_CUDA(cudaGetLastError());
+    FD_CUDA(cudaStreamSynchronize(s));
+  }
+  FD_TRY(install_bsk_ntt(*st, s));
+  FD_TRY(install_split_keys(*st, s));
+  FD_CUDA(cudaStreamSynchronize(s));
+  st->keys = true;
+  return FDFB_OK;
+}
+
 // The TFHE bootstrap's accumulator kernel for ring degree 2^L.
 template <typename W>
 cudaError_t launch_tfhe_acc(int L, int64_t batch, cudaStream_t s, const W* ct, int n, const int32_t* ids,
@@ -606,6 +950,7 @@ int fdfb_key_words(const fdfb_params* p, int which, uint64_t* words_out) {
 int fdfb_params_register(fdfb_ctx* ctx, const fdfb_params* prm, int* set_id_out) {
   if (!ctx || !prm || !set_id_out) return FDFB_EINVAL;
   const fdfb_params& P = *prm;
+  if (P.Q) return register_q(ctx, P, set_id_out);
   if (P.k != 1 || (P.log2q != 32 && P.log2q != 64)) return FDFB_EINVAL;
   if (!is_pow2(P.N) || P.N < 256 || P.N > 4096) return FDFB_EINVAL;
   if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
@@ -693,6 +1038,7 @@ int fdfb_keys_upload(fdfb_ctx* ctx, int set_id, const void* bsk, const void* pk,
   FD_CUDA(cudaMemcpyAsync(st->pk.p, pk, wp_ * wb, cudaMemcpyHostToDevice, s));
   FD_CUDA(cudaMemcpyAsync(st->ksk.p, ksk, wk_ * wb, cudaMemcpyHostToDevice, s));
   FD_TRY(install_bsk_ntt(*st, s));
+  if (st->mq.Q) FD_TRY(install_split_keys(*st, s));
   FD_CUDA(cudaStreamSynchronize(s));
   st->keys = true;
   return FDFB_OK;
@@ -706,6 +1052,7 @@ int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, 
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(cuda_stream);
+  if (st->mq.Q) return keys_generate_q(ctx, st, in, s);
   const fdfb_params& P = st->prm;
   const size_t n = P.n, N = P.N, wb = st->wbytes();
   const int w = st->w;
@@ -785,11 +1132,11 @@ int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, 
     if (w == 32)
       lwe_encrypt_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint8_t*)d_s.p, (const uint32_t*)d_a.p,
                                                           (const int64_t*)d_e.p, (const int64_t*)d_m.p,
-                                                          (int64_t)rows, (int)n, 1, (uint32_t*)st->ksk.p);
+                                                          (int64_t)rows, (int)n, 1, (uint32_t*)st->ksk.p, 32);
     else
       lwe_encrypt_kernel<uint64_t><<<blocks, 256, 0, s>>>((const uint8_t*)d_s.p, (const uint64_t*)d_a.p,
                                                           (const int64_t*)d_e.p, (const int64_t*)d_m.p,
-                                                          (int64_t)rows, (int)n, 1, (uint64_t*)st->ksk.p);
+                                                          (int64_t)rows, (int)n, 1, (uint64_t*)st->ksk.p, 64);
     FD_CUDA(cudaGetLastError());
   }
   FD_TRY(install_bsk_ntt(*st, s));
@@ -840,7 +1187,7 @@ int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out
 
 int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_id_out) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || !poly || !poly_id_out) return FDFB_EINVAL;
+  if (!st || !poly || !poly_id_out || st->mq.Q) return FDFB_EINVAL;
   const size_t N = st->prm.N;
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
@@ -865,7 +1212,7 @@ int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_
 int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* poly_ids,
                         int64_t batch, void* ct_out, void* cuda_stream) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || batch < 0 || batch > 0x7fffffff) return FDFB_EINVAL;
+  if (!st || batch < 0 || batch > 0x7fffffff || st->mq.Q) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !poly_ids || !ct_out) return FDFB_EINVAL;
   if (!st->keys) return FDFB_ENOKEYS;
@@ -1043,6 +1390,15 @@ int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, 
   DeviceGuard g(ctx->device);
   cudaStream_t s = as_stream(cuda_stream);
   const fdfb_params& P = st->prm;
+  if (st->mq.Q) {
+    DevBuf sums;
+    FD_TRY(sums.ensure((size_t)batch * 2 * (P.n + 1) * 8));
+    FD_TRY(launch_keyswitch_q(ctx, *st, (const uint64_t*)ct_in, batch, (int)P.N,
+                              (const uint32_t*)st->ksk_split.p, P.lks, P.log2Bks, (int)P.n + 1,
+                              (uint64_t*)sums.p, 0, (uint64_t*)ct_out, s));
+    FD_CUDA(cudaStreamSynchronize(s));  // the sums buffer is released on return
+    return FDFB_OK;
+  }
   return launch_keyswitch(ctx, st->w, ct_in, batch, (int)P.N, st->ksk.p, P.lks, P.log2Bks,
                           trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s);
 }
@@ -1054,15 +1410,17 @@ int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a,
   if (count == 0) return FDFB_OK;
   if (!s || !a || !e || !m || !ct_out) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  const uint64_t delta = (uint64_t)1 << (st->w - st->logt);
+  // prime-modulus sets encrypt mod q = 2N
+  const int logq = st->mq.Q ? st->L + 1 : st->w;
+  const uint64_t delta = (uint64_t)1 << (logq - st->logt);
   const unsigned blocks = (unsigned)((count + 7) / 8);
   cudaStream_t cs = as_stream(cuda_stream);
   if (st->w == 32)
     lwe_encrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)a, e, m, count,
-                                                         (int)st->prm.n, delta, (uint32_t*)ct_out);
+                                                         (int)st->prm.n, delta, (uint32_t*)ct_out, logq);
   else
     lwe_encrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)a, e, m, count,
-                                                         (int)st->prm.n, delta, (uint64_t*)ct_out);
+                                                         (int)st->prm.n, delta, (uint64_t*)ct_out, logq);
   return cuda_err(cudaGetLastError());
 }
 
@@ -1073,21 +1431,22 @@ int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct
   if (count == 0) return FDFB_OK;
   if (!s || !ct || !m_out) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
+  const int logq = st->mq.Q ? st->L + 1 : st->w;
   const unsigned blocks = (unsigned)((count + 7) / 8);
   cudaStream_t cs = as_stream(cuda_stream);
   if (st->w == 32)
     lwe_decrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)ct, count,
-                                                         (int)st->prm.n, st->logtout, m_out);
+                                                         (int)st->prm.n, st->logtout, m_out, logq);
   else
     lwe_decrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)ct, count,
-                                                         (int)st->prm.n, st->logtout, m_out);
+                                                         (int)st->prm.n, st->logtout, m_out, logq);
   return cuda_err(cudaGetLastError());
 }
 
 int fdfb_lwe_affine(fdfb_ctx* ctx, int set_id, const int32_t* W, int n_in, int n_out, const void* x,
                     int64_t batch, void* y, void* cuda_stream) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || n_in < 1 || n_out < 1 || batch < 0 || batch > 65535) return FDFB_EINVAL;
+  if (!st || n_in < 1 || n_out < 1 || batch < 0 || batch > 65535 || st->mq.Q) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!W || !x || !y) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
@@ -1159,6 +1518,7 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.rep = 1;
     br.signed_digits = (int)st->prm.signed_digits;
     br.err = ctx->d_err;
+    if (st->mq.Q) fill_br_q(br, *st);
     float ms_v = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, s);

@@ -168,6 +168,73 @@ FD_HD uint64_t garner(const uint32_t* x, const PrimeSet& S) {
 }
 
 // ---------------------------------------------------------------------------
+// Arithmetic modulo a pseudo-Mersenne modulus Q = 2^k - c (32 <= k <= 63,
+// odd c < 2^20): the prime moduli of the paper's parameter sets (Table 1).
+// Residues are uint64_t in [0, Q).
+// ---------------------------------------------------------------------------
+struct ModQ {
+  uint64_t Q;  // 0: the set works modulo 2^w instead
+  uint64_t c;  // Q = 2^k - c
+  int k;
+};
+
+// x mod Q for any x < 2^128: replace x by (x >> k) c + (x mod 2^k) while x
+// has bits at or above 2^k (each fold divides the excess by 2^k / c >= 2^12,
+// so a 128-bit x needs at most 11 folds; x < 2^96, the lifts' range, needs at
+// most 6 at k = 32 and 2 at k >= 48), then one conditional subtraction
+// (x < 2^k = Q + c <= 2Q).
+FD_HD uint64_t modq_u128(unsigned __int128 x, const ModQ& m) {
+  const unsigned __int128 lo_mask = (((unsigned __int128)1) << m.k) - 1;
+#pragma unroll 1
+  for (int it = 0; it < 12 && (x >> m.k) != 0; ++it) x = (x >> m.k) * m.c + (x & lo_mask);
+  uint64_t r = (uint64_t)x;
+  return r >= m.Q ? r - m.Q : r;
+}
+// residue of a signed integer |x| < 2^127
+FD_HD uint64_t modq_i128(__int128 x, const ModQ& m) {
+  if (x >= 0) return modq_u128((unsigned __int128)x, m);
+  const uint64_t r = modq_u128((unsigned __int128)(-x), m);
+  return r ? m.Q - r : 0;
+}
+FD_HD uint64_t addq(uint64_t a, uint64_t b, uint64_t Q) {
+  const uint64_t s = a + b;  // < 2Q < 2^64
+  return s >= Q ? s - Q : s;
+}
+FD_HD uint64_t subq(uint64_t a, uint64_t b, uint64_t Q) { return a >= b ? a - b : a + (Q - b); }
+FD_HD uint64_t negq(uint64_t a, uint64_t Q) { return a ? Q - a : 0; }
+FD_HD uint64_t mulq(uint64_t a, uint64_t b, const ModQ& m) {
+  return modq_u128((unsigned __int128)a * b, m);
+}
+// centred representative of a residue in [0, Q), as a 64-bit two's complement
+FD_HD uint64_t centre_q(uint64_t x, uint64_t Q) { return x > Q / 2 ? x - Q : x; }
+
+// The exact integer X in (-M/2, M/2), M = p_0 .. p_{P-1}, with residues
+// x[i] in [0, p_i): Garner's mixed-radix digits y_j, X = sum_j y_j M_j,
+// minus M when the top digit puts X in the upper half.
+template <int P>
+FD_HD __int128 garner_exact(const uint32_t* x, const PrimeSet& S) {
+  uint32_t y[P];
+  y[0] = x[0];
+  unsigned __int128 X = y[0];
+  unsigned __int128 Mj = 1;
+#pragma unroll
+  for (int j = 1; j < P; ++j) {
+    const uint32_t pj = S.p[j];
+    uint32_t v = x[j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      const uint32_t d = v + 2 * pj - y[i];
+      v = csub(mul_shoup(d, S.gc[i][j], S.gcs[i][j], pj), pj);
+    }
+    y[j] = v;
+    Mj *= S.p[j - 1];
+    X += Mj * v;
+  }
+  if (y[P - 1] > S.half_top) X -= Mj * S.p[P - 1];
+  return (__int128)X;
+}
+
+// ---------------------------------------------------------------------------
 // NTT register layouts.
 //
 // One NTT of size N = 2^L is computed by G = 2^(L-EL) threads, each holding

@@ -238,10 +238,16 @@ struct BRParams {
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
   int signed_digits;            // balanced digits: the launcher picks the kernel built with SG
   int* err;                     // device error latch (FDFB_ETIMEOUT if a key copy never lands)
+  // prime-modulus sets (the kernel built with MQ): words are residues mod
+  // Q, the input LWE words already lie in [0, 2N) (q = 2N), and sign item i
+  // starts from (and adds after extraction) sgn_scale[i % rep] instead of
+  // delta_half
+  ModQ mq;
+  uint64_t sgn_scale[8];
 };
 
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1,
-          bool TK = false>
+          bool TK = false, bool MQ = false>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -249,7 +255,8 @@ struct BRShape {
   static size_t smem_bytes(int n, int lg, uint32_t* r1_off, uint32_t* exch_off) {
     size_t acc = 2 * (size_t)N * sizeof(W);
     size_t an = ((size_t)n * 2 + 15) & ~(size_t)15;
-    size_t dig = (2 * (size_t)lg * N * sizeof(DT) + 15) & ~(size_t)15;
+    // MQ keeps d itself ([2][N] words) and cuts the digits out as it loads them
+    size_t dig = MQ ? 2 * (size_t)N * sizeof(W) : (2 * (size_t)lg * N * sizeof(DT) + 15) & ~(size_t)15;
     size_t stage = (size_t)2 * (P - 1) * KH * N * 4;
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
@@ -319,9 +326,12 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // memory by the bulk-copy engine while the group transforms that pair's
 // digits; one thread per group issues the copy, completion is an mbarrier
 // phase (bounded wait, FDFB_ETIMEOUT on expiry).
+// MQ: prime modulus Q (Table 1): d = acc X^{-a} - acc mod Q, exact digits
+// (l log2 B >= log2 Q), the products lifted to the exact integer and reduced
+// mod Q; the input ciphertext is already modulo 2N.
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1, bool SG = false, bool TK = false>
+          int KH = 1, bool SG = false, bool TK = false, bool MQ = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -330,10 +340,12 @@ blind_rotate_kernel(const BRParams prm) {
   static_assert(!LZ || (L <= 12 && sizeof(DT) <= 2), "lazy bound: 2^16 + 2 L p < 2^32");
   static_assert(KH == 1 || (KH == 2 && P == 2 && !WIDE && sizeof(W) == 8),
                 "split keys: q = 2^64, two primes, per-product reduction");
+  static_assert(!MQ || (sizeof(W) == 8 && !SG && !LZ), "prime modulus: 64-bit words, unsigned digits");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
   DT* dig = reinterpret_cast<DT*>(smem + prm.smem_r1);                      // [2 lg][N]
+  W* dq = reinterpret_cast<W*>(smem + prm.smem_r1);                         // MQ: [2][N]
   uint32_t* stage = reinterpret_cast<uint32_t*>(smem + prm.smem_r1);        // [2 (P-1)][N]
   uint32_t* exch = reinterpret_cast<uint32_t*>(smem + prm.smem_exch);       // [P][xwords]
 
@@ -345,21 +357,28 @@ blind_rotate_kernel(const BRParams prm) {
   const W* ct = reinterpret_cast<const W*>(prm.ct) + (ci / prm.rep) * (n + 1);
 
   // ModSwitch of the mask; b_N for the sign accumulator.
+  const uint64_t Qm = prm.mq.Q;
   for (int i = tid; i < n; i += THREADS) {
-    uint32_t a = modswitch_2n<W, L>(ct[1 + i]);
+    uint32_t a = MQ ? (uint32_t)ct[1 + i] & (2 * N - 1) : modswitch_2n<W, L>(ct[1 + i]);
     aN[i] = (uint16_t)a;
     if (prm.ctN_out) prm.ctN_out[ci * (n + 1) + 1 + i] = a;
   }
   if (prm.sign_mode) {
-    const int bN = (int)modswitch_2n<W, L>(ct[0]);
+    const int bN = MQ ? (int)((uint32_t)ct[0] & (2 * N - 1)) : (int)modswitch_2n<W, L>(ct[0]);
     if (prm.ctN_out && tid == 0) prm.ctN_out[ci * (n + 1)] = (uint32_t)bN;
     // acc = [(Delta/2) sgnP X^{b_N}, 0], sgnP = 1 - sum_{i>=2} X^{i-1}
-    const W h = (W)prm.delta_half;
+    // (MQ: item i of an input carries L_boot^i Delta/2)
+    const W h = MQ ? (W)prm.sgn_scale[ci % prm.rep] : (W)prm.delta_half;
     for (int j = tid; j < N; j += THREADS) {
       bool neg;
       int m = rot_src<L>(j, bN, neg);
-      W c = (m == 0) ? h : (W)(0 - h);
-      acc[j] = neg ? (W)(0 - c) : c;
+      if constexpr (MQ) {
+        const W c = (m == 0) ? h : (W)negq(h, Qm);
+        acc[j] = neg ? (W)negq(c, Qm) : c;
+      } else {
+        W c = (m == 0) ? h : (W)(0 - h);
+        acc[j] = neg ? (W)(0 - c) : c;
+      }
       acc[N + j] = 0;
     }
   } else {
@@ -369,7 +388,7 @@ blind_rotate_kernel(const BRParams prm) {
   // TK: the staged pair of key rows of each group, and its mbarrier
   constexpr uint32_t kPairWords = (uint32_t)(2 * M * KH * N);
   uint32_t* kst = reinterpret_cast<uint32_t*>(
-      smem + prm.smem_exch + (size_t)P * BRShape<L, EL, P, W, DT, M, PP, KH, TK>::group_words() * 4);
+      smem + prm.smem_exch + (size_t)P * BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ>::group_words() * 4);
   uint64_t* kmb = reinterpret_cast<uint64_t*>(kst + (size_t)P * kPairWords) + (tid / G);
   kst += (size_t)(tid / G) * kPairWords;
   if constexpr (TK) {
@@ -387,7 +406,7 @@ blind_rotate_kernel(const BRParams prm) {
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
-  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK>;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ>;
   // forward transforms: M polynomials per pass; inverse transforms: both
   // columns together whenever the forward is paired or the key is split
   constexpr int MI = (M == 2 || KH == 2) ? 2 : 1;
@@ -427,6 +446,11 @@ blind_rotate_kernel(const BRParams prm) {
       const int m = (j + a) & (2 * N - 1);
       const W neg = (W)0 - (W)(m >> L);  // all ones when negated
       const W* ac = acc + c * N;
+      if constexpr (MQ) {
+        const uint64_t v = ac[m & (N - 1)];
+        dq[idx] = subq(neg ? negq(v, Qm) : v, ac[j], Qm);
+        continue;
+      }
       const W rv = (W)((ac[m & (N - 1)] ^ neg) - neg);
       const W d = (W)(rv - ac[j]);
       const W xt = (W)((W)(d + half_rt) >> rt);
@@ -470,7 +494,14 @@ blind_rotate_kernel(const BRParams prm) {
       for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-          const uint32_t dv = dig[(r0 + m) * N + Y::j_of(0, t, k)];
+          uint32_t dv;
+          if constexpr (MQ) {
+            // row r = c lg + l: digit l of component c of d
+            const int r = r0 + m, cc = r >= lg ? 1 : 0, l = r - cc * lg;
+            dv = (uint32_t)(dq[cc * N + Y::j_of(0, t, k)] >> (l * log2Bg)) & dmask;
+          } else {
+            dv = dig[(r0 + m) * N + Y::j_of(0, t, k)];
+          }
           if constexpr (SG) {
             // a negative balanced digit enters the transform as d + p
             using SDT = typename std::make_signed<DT>::type;
@@ -598,6 +629,21 @@ blind_rotate_kernel(const BRParams prm) {
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const int j = Y::j_of(0, t, k);
+        if constexpr (MQ) {
+          // the exact sum (one lift over P primes, or X_lo + 2^32 X_hi) mod Q
+          __int128 X = 0;
+#pragma unroll
+          for (int h = 0; h < KH; ++h) {
+            uint32_t x[P];
+#pragma unroll
+            for (int g = 0; g < P; ++g)
+              x[g] = (g == c) ? own[h][k] : stage[(stage_slot<P>(g, c) * KH + h) * N + j];
+            const __int128 Xh = garner_exact<P>(x, prm.S);
+            X += h == 0 ? Xh : Xh * ((__int128)1 << 32);
+          }
+          acc[c * N + j] = (W)addq(acc[c * N + j], modq_i128(X, prm.mq), Qm);
+          continue;
+        }
         W add = 0;
 #pragma unroll
         for (int h = 0; h < KH; ++h) {
@@ -625,9 +671,15 @@ blind_rotate_kernel(const BRParams prm) {
   W* out = reinterpret_cast<W*>(prm.lwe_out) + ci * (N + 1);
   for (int k = tid; k <= N; k += THREADS) {
     W v;
-    if (k == 0) v = (W)(acc[0] + (prm.sign_mode ? (W)prm.delta_half : (W)0));
-    else if (k == 1) v = acc[N];
-    else v = (W)(0 - acc[N + (N - (k - 1))]);
+    if constexpr (MQ) {
+      if (k == 0) v = (W)addq(acc[0], prm.sign_mode ? prm.sgn_scale[ci % prm.rep] : 0, Qm);
+      else if (k == 1) v = acc[N];
+      else v = (W)negq(acc[N + (N - (k - 1))], Qm);
+    } else {
+      if (k == 0) v = (W)(acc[0] + (prm.sign_mode ? (W)prm.delta_half : (W)0));
+      else if (k == 1) v = acc[N];
+      else v = (W)(0 - acc[N + (N - (k - 1))]);
+    }
     out[k] = v;
   }
 }
@@ -815,10 +867,11 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_kernel(const
 // shift, so that K = K_lo + 2^32 K_hi with |K_lo|, |K_hi| <= 2^31).
 // Transform output j = t E + k (thread t of the last pass, register k) is
 // stored at (k / 4) 4G + 4t + k % 4, so that the blind rotation's 128-bit
-// key loads are contiguous across a warp.
+// key loads are contiguous across a warp.  With Q != 0 (prime-modulus sets)
+// the words are residues mod Q and are centred in (-Q/2, Q/2] first.
 template <int L, int EL, int P, typename W, int KH = 1>
 __global__ void __launch_bounds__(P * (1 << (L - EL)))
-bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
+bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out, uint64_t Q) {
   static_assert(KH == 1 || sizeof(W) == 8, "key halves are for 64-bit words");
   using Y = Layout<L, EL>;
   constexpr int N = Y::N, E = Y::E, G = Y::G;
@@ -836,7 +889,8 @@ bsk_to_ntt_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out) {
       uint32_t v[E];
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const W x = src[c * N + Y::j_of(0, t, k)];
+        W x = src[c * N + Y::j_of(0, t, k)];
+        if (Q) x = (W)centre_q((uint64_t)x, Q);
         if (KH == 1) {
           v[k] = mod_centred<W>(x, S, grp);
         } else {
@@ -882,12 +936,19 @@ __device__ __forceinline__ void atomic_add_word(uint64_t* p, uint64_t v) {
 // ksplit = 1 each output is written once; otherwise `out` must be zero and the
 // slices add their parts atomically (integer addition mod 2^w: exact in any
 // order), slice 0 adding b.
-template <typename W>
+//
+// KW = uint32_t with W = uint64_t (prime-modulus sets, raw = 1): the key holds
+// the 32-bit halves of the words mod Q as separate columns and the kernel
+// writes the exact 64-bit column sums (no negation, no b): every term
+// d K_half < 2^16 2^32 and n_in l <= 2^18 terms keep them below 2^64;
+// ks_finalize_q_kernel recombines and reduces them.
+template <typename W, typename KW = W>
 __global__ void __launch_bounds__(KS_THREADS)
-keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __restrict__ key,
-                 int ell, int log2B, int rtrunc, int out_len, W* __restrict__ out, int ksplit) {
+keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const KW* __restrict__ key,
+                 int ell, int log2B, int rtrunc, int out_len, W* __restrict__ out, int ksplit,
+                 int raw = 0) {
   __shared__ __align__(16) uint16_t sa[KS_BK][KS_BM];
-  __shared__ __align__(16) W sb[KS_BK][KS_BN];
+  __shared__ __align__(16) KW sb[KS_BK][KS_BN];
   const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * KS_BM;
   const int c0 = blockIdx.y * KS_BN;
@@ -923,7 +984,7 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
     for (int e = tid; e < KS_BK * KS_BN; e += KS_THREADS) {
       const int kk = e / KS_BN, cc = e % KS_BN;
       const int k = k0 + kk, c = c0 + cc;
-      sb[kk][cc] = (k < ke && c < out_len) ? key[(size_t)k * out_len + c] : (W)0;
+      sb[kk][cc] = (k < ke && c < out_len) ? key[(size_t)k * out_len + c] : (KW)0;
     }
     __syncthreads();
 #pragma unroll 4
@@ -931,7 +992,7 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
       const uint4 dq = *reinterpret_cast<const uint4*>(&sa[kk][ty * 8]);
       const uint32_t dw[4] = {dq.x, dq.y, dq.z, dq.w};
       W kv[4];
-      if constexpr (sizeof(W) == 4) {
+      if constexpr (sizeof(KW) == 4) {
         const uint4 q = *reinterpret_cast<const uint4*>(&sb[kk][tx * 4]);
         kv[0] = q.x; kv[1] = q.y; kv[2] = q.z; kv[3] = q.w;
       } else {
@@ -944,7 +1005,7 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
         const uint32_t d = (dw[a >> 1] >> ((a & 1) * 16)) & 0xffffu;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          if constexpr (sizeof(W) == 4) {
+          if constexpr (sizeof(W) == 4 || sizeof(KW) == 4) {
             acc[a][b] += (W)d * kv[b];
           } else {
             // d < 2^16: d K = d K_lo + 2^32 d K_hi, a 32x32->64 multiply-add
@@ -966,8 +1027,8 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
     for (int b = 0; b < 4; ++b) {
       const int c = c0 + tx * 4 + b;
       if (c >= out_len) continue;
-      W v = (W)(0 - acc[a][b]);
-      if (c == 0 && blockIdx.z == 0) v = (W)(v + ct[m * (n_in + 1)]);
+      W v = raw ? acc[a][b] : (W)(0 - acc[a][b]);
+      if (!raw && c == 0 && blockIdx.z == 0) v = (W)(v + ct[m * (n_in + 1)]);
       if (ksplit == 1) out[m * out_len + c] = v;
       else atomic_add_word(&out[m * out_len + c], v);
     }
@@ -975,9 +1036,11 @@ keyswitch_kernel(const W* __restrict__ ct, int64_t batch, int n_in, const W* __r
 }
 
 // LWE encryption b = <a, s> + e + Delta m, one warp per ciphertext.
+// Words are taken mod q = 2^logq (logq = w for the power-of-two sets; 2N
+// for the prime-modulus sets, whose LWE side lives mod q = 2N).
 template <typename W>
 __global__ void lwe_encrypt_kernel(const uint8_t* s, const W* a, const int64_t* e, const int64_t* m,
-                                   int64_t count, int n, uint64_t delta, W* out) {
+                                   int64_t count, int n, uint64_t delta, W* out, int logq) {
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (c >= count) return;
@@ -989,13 +1052,16 @@ __global__ void lwe_encrypt_kernel(const uint8_t* s, const W* a, const int64_t* 
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc = (W)(acc + __shfl_xor_sync(0xffffffffu, acc, o));
-  if (lane == 0) out[c * (n + 1)] = (W)(acc + (W)e[c] + (W)delta * (W)m[c]);
+  if (lane == 0) {
+    const W mask = logq >= Word<W>::bits ? (W)~(W)0 : (W)(((W)1 << logq) - 1);
+    out[c * (n + 1)] = (W)((acc + (W)e[c] + (W)delta * (W)m[c]) & mask);
+  }
 }
 
 // Decryption round(t * phase / q) mod t (power-of-two t, round half up).
 template <typename W>
 __global__ void lwe_decrypt_kernel(const uint8_t* s, const W* ct, int64_t count, int n, int logt,
-                                   int32_t* m) {
+                                   int32_t* m, int logq) {
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (c >= count) return;
@@ -1004,9 +1070,9 @@ __global__ void lwe_decrypt_kernel(const uint8_t* s, const W* ct, int64_t count,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc = (W)(acc + __shfl_xor_sync(0xffffffffu, acc, o));
   if (lane == 0) {
-    constexpr int WB = Word<W>::bits;
+    const W mask = logq >= Word<W>::bits ? (W)~(W)0 : (W)(((W)1 << logq) - 1);
     const W ph = (W)(ct[c * (n + 1)] - acc);
-    const W r = (W)((W)(ph + ((W)1 << (WB - logt - 1))) >> (WB - logt));
+    const W r = (W)((W)((W)(ph + ((W)1 << (logq - logt - 1))) & mask) >> (logq - logt));
     m[c] = (int32_t)r;
   }
 }
@@ -1044,6 +1110,289 @@ lwe_affine_kernel(const int32_t* __restrict__ Wm, int n_in, int n_out, const W* 
 #pragma unroll
     for (int o = 0; o < AFF_TO; ++o)
       if (o0 + o < n_out) y[((size_t)b * n_out + o0 + o) * len + k] = acc[o];
+}
+
+
+// ---------------------------------------------------------------------------
+// Prime-modulus sets (Table 1): the pieces of the pipeline that differ from
+// the power-of-two path.
+// ---------------------------------------------------------------------------
+
+// out[m][c] = ([b_m, 0, ..] - S[m][c]) mod Q, S = sums[m][c] + 2^32
+// sums[m][out_len + c] (the raw key-switch sums of the two key halves), and
+// with logq > 0 then ModSwitch(Q -> q = 2^logq): round(q v / Q) mod q, round
+// half up (appendix figure "Modulus switching algorithm").
+static __global__ void ks_finalize_q_kernel(const uint64_t* __restrict__ ct, int n_in, int64_t batch,
+                                     const uint64_t* __restrict__ sums, int out_len, ModQ mq, int logq,
+                                     uint64_t* __restrict__ out) {
+  const int64_t total = batch * out_len;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = idx / out_len;
+    const int c = (int)(idx - m * out_len);
+    const uint64_t* row = sums + m * 2 * out_len;
+    const unsigned __int128 S = (unsigned __int128)row[c] + ((unsigned __int128)row[out_len + c] << 32);
+    const uint64_t r = modq_u128(S, mq);
+    uint64_t v = c == 0 ? subq(ct[m * (n_in + 1)], r, mq.Q) : negq(r, mq.Q);
+    if (logq > 0) {
+      const unsigned __int128 num = ((unsigned __int128)v << (logq + 1)) + mq.Q;
+      v = (uint64_t)(num / ((unsigned __int128)2 * mq.Q)) & ((1ull << logq) - 1);
+    }
+    out[idx] = v;
+  }
+}
+
+// Key words mod Q, [rows][cols], to the key-switch layout [rows][2 cols] of
+// their 32-bit halves (low halves first).
+static __global__ void split_halves_kernel(const uint64_t* __restrict__ in, int64_t rows, int cols,
+                                    uint32_t* __restrict__ out) {
+  const int64_t total = rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols;
+    const int c = (int)(idx - r * cols);
+    const uint64_t x = in[idx];
+    out[r * 2 * cols + c] = (uint32_t)x;
+    out[r * 2 * cols + cols + c] = (uint32_t)(x >> 32);
+  }
+}
+
+// PubMux over l_boot RLWE samples (figure "cmux-accumulator-builder"):
+// p = p_1 - p_0 in Z_Q with (p_0, p_1) = (rotP'_1, rotP'_0), its base-L_boot
+// digits p[i], acc_F = [Delta p_0, 0] + sum_i p[i] * c_R,i mod Q.  The l_boot
+// products of each column are summed in the transform domain (exact while
+// l_boot N (L_boot - 1) Q / 2 stays below half the primes' product) and
+// lifted once.  cR: [batch / rep][lboot][2][N] words mod Q.
+struct PubMuxQParams {
+  PrimeSet S;
+  ModQ mq;
+  const uint64_t* cR;
+  const uint64_t* ct;      // [batch / rep][n+1] input LWE mod 2N (for b_N)
+  int rep;
+  const int32_t* lut_ids;  // [batch]
+  const int16_t* luts;     // [n_luts][2][N]
+  int n_luts;
+  uint64_t* accF;          // [batch][2N]
+  int n, lboot, log2Lboot;
+  uint64_t delta;          // round(Q / t)
+  int* err;
+};
+
+template <int L, int EL, int P>
+__global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_q_kernel(const PubMuxQParams prm) {
+  using Y = Layout<L, EL>;
+  constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  constexpr int XW = (Xch<L, EL>::kWords + 3) & ~3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // [P][2][N]
+  uint32_t* exch = stage + P * 2 * N;                   // [P][XW]
+  const int64_t ci = blockIdx.x;
+  const int64_t src = ci / prm.rep;
+  const uint64_t Q = prm.mq.Q;
+  const uint64_t* ct = prm.ct + src * (prm.n + 1);
+  const int bN = (int)(ct[0] & (2 * N - 1));
+  int lut = prm.lut_ids[ci];
+  if (lut < 0 || lut >= prm.n_luts) {
+    if (threadIdx.x == 0) atomicExch(prm.err, -6);
+    lut = 0;
+  }
+  const int16_t* r0 = prm.luts + (size_t)lut * 2 * N;
+  const int16_t* r1 = r0 + N;
+  auto rotated = [&](const int16_t* poly, int j) -> int {
+    bool neg;
+    int m = rot_src<L>(j, bN, neg);
+    int v = poly[m];
+    return neg ? -v : v;
+  };
+  const int tid = threadIdx.x;
+  const int grp = tid / G;
+  const int t = tid - grp * G;
+  const uint32_t p = prm.S.p[grp];
+  const uint32_t pneg = prm.S.pneg[grp];
+  const uint32_t z = prm.S.zero;
+  const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
+  const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
+  uint32_t* xb = exch + grp * XW;
+  const int bar = 1 + grp;
+  const uint64_t dmask = (1ull << prm.log2Lboot) - 1;
+  const uint64_t* cR = prm.cR + src * (size_t)prm.lboot * 2 * N;
+
+  uint32_t accm[2][E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) accm[0][k] = accm[1][k] = 0;
+  for (int i = 0; i < prm.lboot; ++i) {
+    uint32_t sv[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int j = Y::j_of(0, t, k);
+      const int pd = rotated(r0, j) - rotated(r1, j);  // p_1 - p_0, |pd| < 2t
+      const uint64_t pq = pd >= 0 ? (uint64_t)pd : Q - (uint64_t)(-pd);
+      sv[k] = (uint32_t)((pq >> (i * prm.log2Lboot)) & dmask);
+    }
+    ntt_fwd<L, EL, 0>(sv, t, twf, p, xb, bar, z);
+#pragma unroll
+    for (int k = 0; k < E; ++k) sv[k] = csub(csub(sv[k], 2 * p), p);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint32_t v[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k)
+        v[k] = mod_centred<uint64_t>(centre_q(cR[((size_t)i * 2 + c) * N + Y::j_of(0, t, k)], Q), prm.S, grp);
+      ntt_fwd<L, EL, 0>(v, t, twf, p, xb, bar, z);
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const uint32_t x = csub(csub(v[k], 2 * p), p);
+        const uint32_t m = redc((uint64_t)x * sv[k], p, pneg);  // x s 2^-32, < 2p
+        const uint32_t s2 = accm[c][k] + m;
+        accm[c][k] = umin32(s2, s2 - 2 * p);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+      v[k] = csub(mul_shoup(csub(accm[c][k], p), prm.S.ninv_m[grp], prm.S.ninv_ms[grp], p), p);
+    ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+#pragma unroll
+    for (int k = 0; k < E; ++k) stage[(grp * 2 + c) * N + Y::j_of(0, t, k)] = csub(v[k], p);
+  }
+  __syncthreads();
+  uint64_t* out = prm.accF + ci * 2 * N;
+  for (int idx = tid; idx < 2 * N; idx += THREADS) {
+    uint32_t x[P];
+#pragma unroll
+    for (int g = 0; g < P; ++g) x[g] = stage[g * 2 * N + idx];
+    uint64_t r = modq_i128(garner_exact<P>(x, prm.S), prm.mq);
+    if (idx < N) {
+      const int p0 = rotated(r1, idx);
+      const uint64_t p0q = p0 >= 0 ? (uint64_t)p0 : Q - (uint64_t)(-p0);
+      r = addq(r, mulq(prm.delta, p0q, prm.mq), Q);
+    }
+    out[idx] = r;
+  }
+}
+
+// RLWE samples mod Q with a uniform key sk in Z_Q^N (key generation of the
+// prime-modulus sets): out = [b = a sk + e + mu, a], mu added to coefficient
+// 0 of component comp.  a sk is exact as sum_k 2^(13 k) (a * sk_k) over the
+// balanced 13-bit limbs sk_k of the centred key (|sk_k| <= 2^12, five limbs
+// for |sk| < 2^62): each limb product is below N 2^12 2^62 <= 2^86 in
+// magnitude and lifts exactly from three primes.  skl: the limbs in the
+// transform domain, [5][P][2][N] in the blind rotation's key layout
+// (bsk_to_ntt_kernel with R = 1 on rows [limb, 0]: times N^-1 2^32).
+struct RlweEncQParams {
+  PrimeSet S;
+  ModQ mq;
+  const uint32_t* skl;
+  const uint64_t* a;       // [count][N] mod Q
+  const int64_t* e;        // [count][N]
+  const uint64_t* mu;      // [count] mod Q
+  const uint8_t* comp;     // [count]
+  uint64_t* out;           // [count][2][N]
+};
+constexpr int kSkLimbs = 5, kSkLimbBits = 13;
+
+template <int L, int EL, int P>
+__global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_q_kernel(const RlweEncQParams prm) {
+  using Y = Layout<L, EL>;
+  constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
+  constexpr int XW = (Xch<L, EL>::kWords + 3) & ~3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // [P][N]
+  uint32_t* exch = stage + P * 2 * N;                   // [P][XW]
+  const int64_t it = blockIdx.x;
+  const uint64_t Q = prm.mq.Q;
+  const uint64_t* a = prm.a + it * N;
+  const int64_t* e = prm.e + it * N;
+  uint64_t* out = prm.out + it * 2 * N;
+  const int tid = threadIdx.x;
+  const int grp = tid / G;
+  const int t = tid - grp * G;
+  const uint32_t p = prm.S.p[grp];
+  const uint32_t pneg = prm.S.pneg[grp];
+  const uint32_t z = prm.S.zero;
+  uint32_t* xb = exch + grp * XW;
+  const int bar = 1 + grp;
+  // b starts as e + mu (component 0), a as given (+ mu on component 1)
+  for (int j = tid; j < N; j += THREADS) {
+    const int64_t ev = e[j];
+    uint64_t b = ev >= 0 ? (uint64_t)ev % Q : negq((uint64_t)(-ev) % Q, Q);
+    uint64_t av = a[j];
+    if (j == 0) {
+      if (prm.comp[it] == 0) b = addq(b, prm.mu[it], Q);
+      else av = addq(av, prm.mu[it], Q);
+    }
+    out[j] = b;
+    out[N + j] = av;
+  }
+  uint32_t va[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) va[k] = mod_centred<uint64_t>(centre_q(a[Y::j_of(0, t, k)], Q), prm.S, grp);
+  ntt_fwd<L, EL, 0>(va, t, prm.S.tw_fwd + (size_t)grp * N, p, xb, bar, z);
+#pragma unroll
+  for (int k = 0; k < E; ++k) va[k] = csub(csub(va[k], 2 * p), p);
+  for (int l = 0; l < kSkLimbs; ++l) {
+    const uint32_t* kl = prm.skl + ((size_t)l * P + grp) * 2 * N;  // component 0 of limb row l
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint32_t kv = kl[(k >> 2) * 4 * G + t * 4 + (k & 3)];
+      v[k] = csub(redc((uint64_t)va[k] * kv, p, pneg), p);  // a sk_l N^-1
+    }
+    ntt_inv<L, EL, Y::K - 1>(v, t, prm.S.tw_inv + (size_t)grp * N, p, xb, bar, z);
+    __syncthreads();  // the previous limb's lift has read the staging area
+#pragma unroll
+    for (int k = 0; k < E; ++k) stage[grp * N + Y::j_of(0, t, k)] = csub(v[k], p);
+    __syncthreads();
+    const uint64_t w = modq_u128((unsigned __int128)1 << (kSkLimbBits * l), prm.mq);  // 2^(13 l) mod Q
+    for (int j = tid; j < N; j += THREADS) {
+      uint32_t x[P];
+#pragma unroll
+      for (int g = 0; g < P; ++g) x[g] = stage[g * N + j];
+      const uint64_t X = modq_i128(garner_exact<P>(x, prm.S), prm.mq);
+      out[j] = addq(out[j], mulq(X, w, prm.mq), Q);
+    }
+  }
+}
+
+// The balanced 13-bit limbs of the centred key as rows [5][2][N] of words
+// mod Q (a negative limb d stored as Q + d; component 1 left zero), for
+// bsk_to_ntt_kernel.
+static __global__ void sk_limbs_kernel(const uint64_t* __restrict__ sk, int N, ModQ mq, uint64_t* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    int64_t x = (int64_t)centre_q(sk[j], mq.Q);
+    for (int l = 0; l < kSkLimbs; ++l) {
+      const int64_t d = ((x + (1 << (kSkLimbBits - 1))) & ((1 << kSkLimbBits) - 1)) - (1 << (kSkLimbBits - 1));
+      out[(size_t)l * 2 * N + j] = d >= 0 ? (uint64_t)d : mq.Q - (uint64_t)(-d);
+      out[(size_t)l * 2 * N + N + j] = 0;
+      x = (x - d) >> kSkLimbBits;
+    }
+  }
+}
+
+// LWE samples mod Q under the binary key s (the key-switching key of the
+// prime-modulus sets): out = [b = <a, s> + e + mu, a], one warp per sample.
+static __global__ void lwe_encrypt_q_kernel(const uint8_t* s, const uint64_t* a, const int64_t* e,
+                                     const uint64_t* mu, int64_t count, int n, ModQ mq, uint64_t* out) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= count) return;
+  const uint64_t Q = mq.Q;
+  uint64_t acc = 0;
+  for (int i = lane; i < n; i += 32) {
+    const uint64_t ai = a[c * n + i];
+    if (s[i]) acc = addq(acc, ai, Q);
+    out[c * (n + 1) + 1 + i] = ai;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = addq(acc, __shfl_xor_sync(0xffffffffu, acc, o), Q);
+  if (lane == 0) {
+    const int64_t ev = e[c];
+    const uint64_t eq = ev >= 0 ? (uint64_t)ev % Q : negq((uint64_t)(-ev) % Q, Q);
+    out[c * (n + 1)] = addq(addq(acc, eq, Q), mu[c], Q);
+  }
 }
 
 }  // namespace fdfb

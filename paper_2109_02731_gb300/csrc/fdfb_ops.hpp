@@ -17,15 +17,20 @@ struct Ops {
   cudaError_t (*pubmux)(const PubMuxParams& prm, int64_t batch, cudaStream_t st);
   cudaError_t (*rlwe_enc)(const RlweEncParams& prm, int64_t count, cudaStream_t st);
   cudaError_t (*bsk_ntt)(const PrimeSet& S, const void* bsk, int64_t rows, int R, uint32_t* out,
-                         cudaStream_t st);
+                         uint64_t Q, cudaStream_t st);
   int family;  // NTT prime family of the blind rotation (0: 30-bit primes, 1: lazy family)
   int (*br_blocks_per_sm)(size_t smem);  // resident blind-rotation CTAs per SM
   int key_halves;  // 2: 64-bit key words split into 32-bit halves over two primes
   int has_signed;  // also built with balanced blind-rotation digits
+  int mq;          // built for the prime-modulus sets (words mod Q, exact digits)
+  cudaError_t (*pubmux_q)(const PubMuxQParams& prm, int64_t batch, cudaStream_t st);
+  cudaError_t (*rlwe_enc_q)(const RlweEncQParams& prm, int64_t count, cudaStream_t st);
 };
 
 // Returns the launcher table of register-layout variant `variant` for
-// N = 2^L and word size w, or nullptr past the last variant.
+// N = 2^L and word size w, or nullptr past the last variant; find_ops_q the
+// variants built for the prime-modulus sets (64-bit words).
 const Ops* find_ops(int L, int w, int variant);
+const Ops* find_ops_q(int L, int variant);
 
 }  // namespace fdfb

@@ -16,7 +16,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import build as _build
-from .synth import KeyRandomness, ParamSet
+from .synth import KeyRandomness, ParamSet, QKeyRandomness, QParamSet
 
 FDFB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOKEYS", -6: "EBADLUT"}
@@ -42,15 +42,16 @@ class FDFBError(RuntimeError):
 class fdfb_params(C.Structure):
     _fields_ = [(k, C.c_uint32) for k in ("n", "N", "k", "log2q", "t", "log2Bg", "lg", "log2Bks",
                                           "lks", "log2Bpk", "lpk", "log2Lboot", "lboot", "signed_digits",
-                                          "t_out")]
+                                          "t_out")] + [("Q", C.c_uint64)]
 
 
 class fdfb_keygen_inputs(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("s", "sk", "bsk_a", "bsk_e", "pk_a", "pk_e", "ksk_a", "ksk_e")]
+    _fields_ = [(k, C.c_void_p) for k in ("s", "sk", "bsk_a", "bsk_e", "pk_a", "pk_e", "ksk_a", "ksk_e",
+                                          "sk_q")]
 
 
 class fdfb_debug_bufs(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("ctN", "sgn", "cR", "accF", "cQ")]
+    _fields_ = [(k, C.c_void_p) for k in ("ctN", "sgn", "cR", "accF", "cQ", "cKS")]
 
 
 class fdfb_group(C.Structure):
@@ -130,9 +131,12 @@ def _check(rc: int, what: str) -> None:
         raise FDFBError(rc, what)
 
 
-def params_struct(ps: ParamSet) -> fdfb_params:
+def params_struct(ps) -> fdfb_params:
+    if isinstance(ps, QParamSet):
+        return fdfb_params(ps.n, ps.N, 1, 64, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks, ps.log2Bpk,
+                           ps.lpk, ps.log2Lboot, ps.lboot, 0, 0, ps.Q)
     return fdfb_params(ps.n, ps.N, 1, ps.w, ps.t, ps.log2Bg, ps.lg, ps.log2Bks, ps.lks, ps.log2Bpk,
-                       ps.lpk, int(ps.t).bit_length() - 1, 1, 1 if ps.signed_digits else 0, ps.t_out)
+                       ps.lpk, int(ps.t).bit_length() - 1, 1, 1 if ps.signed_digits else 0, ps.t_out, 0)
 
 
 def key_words(ps: ParamSet, which: int) -> int:
@@ -164,13 +168,13 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def word_np(ps: ParamSet):
-    return np.uint32 if ps.w == 32 else np.uint64
+def word_np(ps):
+    return np.uint32 if getattr(ps, "w", 64) == 32 else np.uint64
 
 
-def word_torch(ps: ParamSet):
+def word_torch(ps):
     import torch
-    return torch.int32 if ps.w == 32 else torch.int64
+    return torch.int32 if getattr(ps, "w", 64) == 32 else torch.int64
 
 
 def to_host_words(ps: ParamSet, t) -> np.ndarray:
@@ -181,7 +185,7 @@ def to_host_words(ps: ParamSet, t) -> np.ndarray:
 def to_device_words(ps: ParamSet, a: np.ndarray, device="cuda"):
     import torch
     arr = np.ascontiguousarray(np.asarray(a).astype(word_np(ps)))
-    sgn = np.int32 if ps.w == 32 else np.int64
+    sgn = np.int32 if word_np(ps) == np.uint32 else np.int64
     return torch.from_numpy(arr.view(sgn)).to(device)
 
 
@@ -221,14 +225,19 @@ class Context:
         _check(self.L.fdfb_keys_upload(self.h, set_id, b.ctypes.data, p.ctypes.data, k.ctypes.data,
                                        _stream(stream)), "fdfb_keys_upload")
 
-    def keys_generate(self, set_id: int, kr: KeyRandomness, stream=None):
+    def keys_generate(self, set_id: int, kr, stream=None):
+        """kr: KeyRandomness, or QKeyRandomness for a prime-modulus set (its
+        RLWE key, uniform mod Q, goes to sk_q)."""
         ps = self.sets[set_id]
         dt = word_np(ps)
-        keep = [np.ascontiguousarray(kr.s.astype(np.uint8)), np.ascontiguousarray(kr.sk.astype(np.uint8)),
+        prime = isinstance(kr, QKeyRandomness)
+        sk8 = np.zeros(ps.N, np.uint8) if prime else kr.sk.astype(np.uint8)
+        keep = [np.ascontiguousarray(kr.s.astype(np.uint8)), np.ascontiguousarray(sk8),
                 np.ascontiguousarray(kr.bsk_a.astype(dt)), np.ascontiguousarray(kr.bsk_e.astype(np.int64)),
                 np.ascontiguousarray(kr.pk_a.astype(dt)), np.ascontiguousarray(kr.pk_e.astype(np.int64)),
                 np.ascontiguousarray(kr.ksk_a.astype(dt)), np.ascontiguousarray(kr.ksk_e.astype(np.int64))]
-        inp = fdfb_keygen_inputs(*[a.ctypes.data for a in keep])
+        keep.append(np.ascontiguousarray(kr.sk.astype(np.uint64)) if prime else None)
+        inp = fdfb_keygen_inputs(*[None if a is None else a.ctypes.data for a in keep])
         _check(self.L.fdfb_keys_generate(self.h, set_id, C.byref(inp), _stream(stream)),
                "fdfb_keys_generate")
 
@@ -295,7 +304,7 @@ class Context:
         return int(out.value)
 
     def bootstrap_debug(self, set_id: int, ct_in, lut_ids, ct_out, dbg: dict, stream=None):
-        d = fdfb_debug_bufs(*[_ptr(dbg.get(k)) for k in ("ctN", "sgn", "cR", "accF", "cQ")])
+        d = fdfb_debug_bufs(*[_ptr(dbg.get(k)) for k in ("ctN", "sgn", "cR", "accF", "cQ", "cKS")])
         _check(self.L.fdfb_bootstrap_debug(self.h, set_id, _ptr(ct_in), _ptr(lut_ids),
                                            int(ct_in.shape[0]), _ptr(ct_out), C.byref(d),
                                            _stream(stream)), "fdfb_bootstrap_debug")

@@ -1,0 +1,211 @@
+"""GPU parity for the prime-modulus parameter sets (Table 1): the CUDA
+library, through its C ABI, against the prime-Q oracle on the same seeded
+inputs.  Everything is exact integer arithmetic (mod Q on the RLWE side,
+mod q = 2N on the LWE side), so every comparison is bit-exact."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2109_02731_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+QZ = S.Q_PARAM_SETS["QZ"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def F(torch_cuda):
+    from paper_2109_02731_gb300 import fdfb
+    return fdfb
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def OQ(oracle):
+    import oracle.prime_q as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def qz(ctx, OQ):
+    """QZ registered with the oracle's keys and two tables."""
+    kr = S.q_key_randomness(QZ, 21)
+    K = OQ.QKeys(QZ, kr)
+    sid = ctx.register(QZ)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    tables = S.q_lut_tables(QZ, 21, 2)
+    assert [ctx.lut_setup(sid, f) for f in tables] == [0, 1]
+    rot = OQ.rotation_polys(QZ, tables)
+    return sid, kr, K, tables, rot
+
+
+def run_q(F, torch, ctx, sid, ps, cts, ids, debug=True):
+    ct_d = F.to_device_words(ps, cts)
+    ids_d = torch.tensor(np.asarray(ids, dtype=np.int32), device="cuda")
+    out_d = torch.empty_like(ct_d)
+    b, N, lb = len(cts), ps.N, ps.lboot
+    if debug:
+        e = lambda *shape: torch.empty(shape, dtype=torch.int64, device="cuda")
+        dbg = dict(sgn=e(b, lb, N + 1), cR=e(b, lb, 2 * N), accF=e(b, 2 * N), cQ=e(b, N + 1),
+                   cKS=e(b, ps.n + 1))
+        ctx.bootstrap_debug(sid, ct_d, ids_d, out_d, dbg)
+    else:
+        ctx.bootstrap(sid, ct_d, ids_d, out_d)
+    ctx.sync()
+    out = F.to_host_words(ps, out_d).astype(np.uint64)
+    if not debug:
+        return out, None
+    return out, {k: F.to_host_words(ps, v).astype(np.uint64) for k, v in dbg.items()}
+
+
+def test_every_variant_matches_the_oracle(F, torch_cuda, ctx, OQ, qz):
+    """Every message of Z_t under both tables plus a ragged tail: outputs and
+    every intermediate bit for bit equal to the oracle, for every layout."""
+    sid, kr, K, tables, rot = qz
+    m = np.concatenate([np.arange(QZ.t), np.arange(QZ.t), [0, QZ.t - 1, 3]])
+    ids = np.concatenate([np.zeros(QZ.t), np.ones(QZ.t), [1, 0, 1]]).astype(np.int32)
+    mr = S.q_message_randomness(QZ, 22, len(m), m=m)
+    cts = OQ.encrypt_messages(QZ, kr.s, mr)
+    refs = [OQ.fdfb_bootstrap(QZ, K, rot[i][0], rot[i][1], c, debug=True) for c, i in zip(cts, ids)]
+    cur, count, _ = ctx.variant_info(sid)
+    assert count == 3
+    for v in range(count):
+        ctx.set_variant(sid, v)
+        out, dbg = run_q(F, torch_cuda, ctx, sid, QZ, cts, ids)
+        for c, (o, d) in enumerate(refs):
+            for key in ("sgn", "cR", "accF", "cQ", "cKS"):
+                assert np.array_equal(dbg[key][c].reshape(d[key].shape), d[key]), f"{key}, variant {v}, ct {c}"
+            assert np.array_equal(out[c], o), f"output, variant {v}, ct {c}"
+        dec = [OQ.decrypt(QZ, kr.s, o) for o in out]
+        assert dec == [int(tables[i][mm]) for mm, i in zip(m, ids)]
+    ctx.set_variant(sid, cur)
+
+
+def test_plain_call_and_autotune_match(F, torch_cuda, ctx, OQ, qz):
+    sid, kr, K, tables, rot = qz
+    mr = S.q_message_randomness(QZ, 23, 40)
+    cts = OQ.encrypt_messages(QZ, kr.s, mr)
+    ids = S.lut_assignment(23, 40, 2, "uniform")
+    ref = OQ.fdfb_batch(QZ, K, rot, ids, cts, threads=8)
+    out, _ = run_q(F, torch_cuda, ctx, sid, QZ, cts, ids, debug=False)
+    assert np.array_equal(out, ref)
+    best, ms = ctx.autotune(sid, 40)
+    assert ms > 0
+    out2, _ = run_q(F, torch_cuda, ctx, sid, QZ, cts, ids, debug=False)
+    assert np.array_equal(out2, ref)
+
+
+def test_keygen_matches_the_oracle(ctx, OQ):
+    kr = S.q_key_randomness(QZ, 24)
+    sid = ctx.register(QZ)
+    ctx.keys_generate(sid, kr)
+    bsk, pk, ksk = ctx.keys_download(sid)
+    K = OQ.QKeys(QZ, kr)
+    assert np.array_equal(bsk.astype(np.uint64), K.bsk)
+    assert np.array_equal(pk.astype(np.uint64), K.pk)
+    assert np.array_equal(ksk.astype(np.uint64), K.ksk)
+
+
+def test_lwe_side_and_keyswitch(F, torch_cuda, ctx, OQ, oracle, qz):
+    sid, kr, K, tables, rot = qz
+    torch = torch_cuda
+    mr = S.q_message_randomness(QZ, 25, 33)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    a_d = F.to_device_words(QZ, mr.a)
+    ct_d = torch.empty((33, QZ.n + 1), dtype=torch.int64, device="cuda")
+    ctx.lwe_encrypt(sid, s_d, a_d, torch.tensor(mr.e, device="cuda"), torch.tensor(mr.m, device="cuda"), ct_d)
+    m_d = torch.empty(33, dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, s_d, ct_d, m_d)
+    ctx.sync()
+    assert np.array_equal(F.to_host_words(QZ, ct_d).astype(np.uint64), OQ.encrypt_messages(QZ, kr.s, mr))
+    assert np.array_equal(m_d.cpu().numpy(), mr.m)
+    # standalone key switch mod Q: LWE under s_F (dimension N) -> under s
+    rng = np.random.default_rng(5)
+    x = (rng.integers(0, 2 ** 63, (7, QZ.N + 1), dtype=np.uint64) % np.uint64(QZ.Q))
+    x_d = F.to_device_words(QZ, x)
+    y_d = torch.empty((7, QZ.n + 1), dtype=torch.int64, device="cuda")
+    ctx.keyswitch(sid, x_d, y_d)
+    ctx.sync()
+    y = F.to_host_words(QZ, y_d).astype(np.uint64)
+    for i in range(7):
+        assert np.array_equal(y[i], OQ.keyswitch(QZ.Q, QZ.log2Bks, QZ.lks, K.ksk, x[i]))
+
+
+def test_registration_rules(F, ctx):
+    def reg(ps):
+        return ctx.register(ps)
+    with pytest.raises(F.FDFBError):
+        reg(dataclasses.replace(QZ, N=1024))              # no layout at N = 1024
+    with pytest.raises(F.FDFBError):
+        reg(dataclasses.replace(QZ, Q=S.Q1 + 1))          # even modulus
+    with pytest.raises(F.FDFBError):
+        reg(dataclasses.replace(QZ, Q=S.Q4))              # k = 32 < 33
+    with pytest.raises(F.FDFBError):
+        reg(dataclasses.replace(QZ, log2Lboot=7))         # l_boot = 9 > 8
+    # a caller-given l that is not ceil(k / log2 B)
+    from paper_2109_02731_gb300.fdfb import fdfb_params
+    import ctypes as C
+    p = F.params_struct(QZ)
+    p.lg = p.lg + 1
+    sid = C.c_int()
+    assert ctx.L.fdfb_params_register(ctx.h, C.byref(p), C.byref(sid)) == -1
+
+
+def test_unavailable_calls_refuse(F, torch_cuda, ctx, qz):
+    sid = qz[0]
+    torch = torch_cuda
+    ct = torch.zeros((2, QZ.n + 1), dtype=torch.int64, device="cuda")
+    ids = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    out = torch.empty((2, 2, QZ.n + 1), dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FDFBError):
+        ctx.bootstrap_multi(sid, ct, ids, out)
+    with pytest.raises(F.FDFBError):
+        ctx.tfhe_poly_setup(sid, np.zeros(QZ.N, np.uint64))
+
+
+@pytest.mark.parametrize("name", ["FDFB-80-6", "FDFB-80-7"])
+def test_full_size_decrypts_and_variants_agree(F, torch_cuda, ctx, OQ, name):
+    """The paper's parameter sets at full size, keys generated on the GPU:
+    every output decrypts to f(m), and every layout variant (and the
+    autotuned, chunked call) returns the same bits."""
+    ps = S.Q_PARAM_SETS[name]
+    kr = S.q_key_randomness(ps, 31)
+    sid = ctx.register(ps)
+    ctx.keys_generate(sid, kr)
+    tables = S.q_lut_tables(ps, 31, 3)
+    for f in tables:
+        ctx.lut_setup(sid, f)
+    batch = 300
+    mr = S.q_message_randomness(ps, 32, batch)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    ids = S.lut_assignment(32, batch, 3, "uniform")
+    cur, count, _ = ctx.variant_info(sid)
+    outs = []
+    for v in range(count):
+        ctx.set_variant(sid, v)
+        out, _ = run_q(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+        outs.append(out)
+    for v in range(1, count):
+        assert np.array_equal(outs[v], outs[0]), f"variant {v}"
+    dec = [OQ.decrypt(ps, kr.s, o) for o in outs[0]]
+    assert dec == [int(tables[i][m]) for m, i in zip(mr.m, ids)]
+    ctx.autotune(sid, batch)
+    out, _ = run_q(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+    assert np.array_equal(out, outs[0])
