@@ -50,8 +50,19 @@ SM_MAX_GHZ = 2.07
 def workload_desc(name: str):
     wl = S.WORKLOADS[name]
     g = wl.groups[0]
-    ps = S.PARAM_SETS[g.set_name]
+    ps = S.param_set(g.set_name)
     return wl, g, ps
+
+
+def is_prime_set(ps) -> bool:
+    return isinstance(ps, S.QParamSet)
+
+
+# The paper's own times per bootstrap for its parameter sets (Table 3: one
+# bootstrap, not parallelised, on a 60-core Xeon Cascade Lake VM with a
+# 64-bit prime-modulus NTT): context for the prime-modulus workloads.
+PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7": 9278.0,
+                          "FDFB-100-7": 13781.0}
 
 
 # DRAM bytes (read + write) of one blind-rotation launch over the whole batch,
@@ -70,7 +81,7 @@ def br_algorithmic_slots(ps, batch: int) -> float:
     product = 1 multiply-high (2 slots: the pipe runs it at half rate) + 2
     multiply-low (1 slot each), and 4 l N P pointwise products, each one
     32x32->64 multiply-add (2 slots); n CMux steps per ciphertext."""
-    P = 2 if ps.w == 32 else 3
+    P = 2 if getattr(ps, "w", 64) == 32 else 3  # prime-modulus sets: three primes
     bfly = (2 * ps.lg + 2) * P * (ps.N // 2) * ps.logN
     mac = 4 * ps.lg * ps.N * P
     return float(batch) * ps.n * (4.0 * bfly + 2.0 * mac)
@@ -142,7 +153,58 @@ def slowest_rank(values, device):
 def rank_messages(ps, seed: int, batch: int, rank: int, group: int = 0):
     """The message randomness of one rank's shard: every rank bootstraps its
     own batch (weak scaling), drawn from its own sub-stream."""
+    if is_prime_set(ps):
+        return S.q_message_randomness(ps, seed, batch, group=1000 * rank + group)
     return S.message_randomness(ps, seed, batch, group=1000 * rank + group)
+
+
+def q_oracle_sample(ps, seconds_target: float = 10.0):
+    """The prime-modulus oracle's time per bootstrap, from a bounded sample:
+    one bootstrap of these sets takes the schoolbook oracle hours (about
+    (l_boot + 1) n CMux steps of 2 (2 l) N^2 products mod Q), so the sample
+    times whole CMux steps of the blind rotation (a ciphertext whose first
+    masks are nonzero: the oracle skips steps with a_i = 0), one packing key
+    switch, PubMux and the LWE key switch, at full size, and scales each by
+    its count per bootstrap.  Key material of the right shapes is drawn
+    uniformly mod Q without key generation: the products cost the same for
+    any values.  Returns (seconds per bootstrap, description)."""
+    import oracle.prime_q as OQ
+    rng = np.random.default_rng(0)
+    Q, N, n, lg, lb = ps.Q, ps.N, ps.n, ps.lg, ps.lboot
+    uni = lambda *shape: rng.integers(0, 2 ** 63, shape, dtype=np.uint64) % np.uint64(Q)
+    def cmux_steps(steps):
+        pset = dataclasses.replace(ps, n=steps)
+        ctN = np.zeros(steps + 1, dtype=np.uint64)
+        ctN[1:] = 1 + np.arange(steps)
+        bsk, acc = uni(steps, 2 * lg, 2, N), uni(2, N)
+        t0 = time.perf_counter()
+        OQ.blind_rotate(pset, bsk, acc, ctN)
+        return (time.perf_counter() - t0) / steps
+
+    t1 = cmux_steps(1)
+    steps = int(min(16, max(1, seconds_target * 0.6 / max(t1, 1e-3))))
+    t_step = cmux_steps(steps) if steps > 1 else t1
+    lwe = uni(N + 1)
+    pk = uni(N, ps.lpk, 2, N)
+    t0 = time.perf_counter()
+    OQ.keyswitch(Q, ps.log2Bpk, ps.lpk, pk, lwe)
+    t_pk = time.perf_counter() - t0
+    del pk
+    ksk = uni(N, ps.lks, n + 1)
+    t0 = time.perf_counter()
+    OQ.keyswitch(Q, ps.log2Bks, ps.lks, ksk, lwe)
+    t_ks = time.perf_counter() - t0
+    cR = uni(lb, 2, N)
+    p0 = rng.integers(-ps.t + 1, ps.t, N)
+    t0 = time.perf_counter()
+    OQ.pubmux(ps, cR, p0, -p0)
+    t_pm = time.perf_counter() - t0
+    sec = (lb + 1) * n * t_step + lb * t_pk + t_pm + t_ks
+    desc = (f"{steps} full-size CMux step(s) ({t_step:.2f} s each, x {(lb + 1) * n} per bootstrap), one "
+            f"packing key switch ({t_pk:.2f} s, x {lb}), PubMux ({t_pm:.2f} s) and the LWE key switch "
+            f"({t_ks:.2f} s) of the schoolbook oracle on one core, scaled to one bootstrap "
+            f"({sec / 3600:.2f} h)")
+    return sec, desc
 
 
 def dist_setup():
@@ -160,6 +222,28 @@ def run_reference(args):
         return 0
     import oracle as O
     wl, g, ps = workload_desc(args.workload)
+    if is_prime_set(ps):
+        for _ in range(args.warmup):
+            q_oracle_sample(ps)
+        secs = []
+        desc = ""
+        for _ in range(args.steps):
+            sec, desc = q_oracle_sample(ps)
+            secs.append(sec)
+        value = args.steps / sum(secs)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded key-shaped words, no key generation: the oracle's cost does not "
+                    "depend on the values)",
+            "config": config_of(args, wl, g, ps),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return 0
     cores = O.max_threads()
     O.set_threads(cores)
     K = O.Keys(ps, S.key_randomness(ps, wl.seed))
@@ -206,6 +290,14 @@ def run_reference(args):
 
 
 def config_of(args, wl, g, ps):
+    if is_prime_set(ps):
+        return {"workload": f"{wl.name}: FDFB, the paper's set {ps.name} (Table 1): n={ps.n} N={ps.N} "
+                            f"Q=2^{ps.k}-{(1 << ps.k) - ps.Q} q=2N={ps.q} t={ps.t} B_g=2^{ps.log2Bg} l_g={ps.lg} "
+                            f"B_ks=2^{ps.log2Bks} l_ks={ps.lks} B_pk=2^{ps.log2Bpk} l_pk={ps.lpk} "
+                            f"L_boot=2^{ps.log2Lboot} l_boot={ps.lboot} (exact decompositions, uniform RLWE "
+                            f"key), {g.batch} ciphertexts per GPU, {g.n_luts} tables ({g.lut_assign})",
+                "batch_per_gpu": g.batch, "param_set": ps.name, "seed": wl.seed,
+                "l2": "flushed before every timed step (512 MB write, not timed)"}
     kind = "TFHE bootstrap (one blind rotation of a test polynomial)" if g.mode == "tfhe" else "FDFB"
     return {"workload": f"{wl.name}: {kind} n={ps.n} N={ps.N} q=2^{ps.w} t={ps.t} B_g=2^{ps.log2Bg} "
                         f"l_g={ps.lg} B_ks=2^{ps.log2Bks} l_ks={ps.lks} B_pk=2^{ps.log2Bpk} l_pk={ps.lpk}, "
@@ -219,6 +311,9 @@ def config_of(args, wl, g, ps):
 def cpu_baseline(wl, g, ps, seconds_target=20.0):
     """The oracle timed on a bounded sample (rank 0, one GPU only)."""
     import oracle as O
+    if is_prime_set(ps):
+        sec, desc = q_oracle_sample(ps)
+        return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     cores = O.max_threads()
     O.set_threads(cores)
     K = O.Keys(ps, S.key_randomness(ps, wl.seed))
@@ -269,11 +364,12 @@ class Job:
 
     def _prepare_group(self, gi, g, args, rank):
         torch, F, ctx, dev, wl = self.torch, self.F, self.ctx, self.dev, self.wl
-        ps = S.PARAM_SETS[g.set_name]
+        ps = S.param_set(g.set_name)
         sid = ctx.register(ps)
-        kr = S.key_randomness(ps, wl.seed)
+        prime = is_prime_set(ps)
+        kr = S.q_key_randomness(ps, wl.seed) if prime else S.key_randomness(ps, wl.seed)
         ctx.keys_generate(sid, kr)
-        fs = S.lut_tables(ps, wl.seed, g.n_luts, gi)
+        fs = (S.q_lut_tables if prime else S.lut_tables)(ps, wl.seed, g.n_luts, gi)
         for f in fs:
             ctx.lut_setup(sid, f)
         if g.mode == "tfhe":
@@ -304,7 +400,7 @@ class Job:
             want = np.array([fs[i][m] for i, m in zip(ids_np, mr.m)])
             out = torch.empty_like(ct)
         return {"sid": sid, "ps": ps, "batch": g.batch, "k": k, "ct": ct, "ids": ids, "out": out,
-                "s": s_d, "want": want, "mode": g.mode}
+                "s": s_d, "want": want, "mode": g.mode, "lboot": ps.lboot if prime else 1}
 
     def _prepare_mlp(self, args, rank):
         from paper_2109_02731_gb300 import mlp
@@ -371,7 +467,8 @@ class Job:
             return 2 * sum(br_algorithmic_slots(ps, b) for b in self.mlp_batches)
         # one sign rotation per input, one function rotation per (input, table);
         # the TFHE bootstrap has the function rotation only
-        return sum((0 if g.get("mode") == "tfhe" else br_algorithmic_slots(g["ps"], g["batch"]))
+        # (prime-modulus sets: l_boot sign rotations per input)
+        return sum((0 if g.get("mode") == "tfhe" else br_algorithmic_slots(g["ps"], g["batch"] * g.get("lboot", 1)))
                    + br_algorithmic_slots(g["ps"], g["batch"] * g["k"]) for g in self.groups)
 
     def io_bytes(self):
@@ -395,7 +492,8 @@ class Job:
             return sum(1 + 5 * pipelines(g, b) for b in self.mlp_batches)
         if any(g.get("mode") == "tfhe" for g in self.groups):
             return 3 * len(self.groups)  # accumulator, blind rotation, key switch
-        return sum(5 * pipelines(g, g["batch"]) for g in self.groups)
+        # prime-modulus sets: each key switch is a sum kernel and a finalize kernel
+        return sum((7 if is_prime_set(g["ps"]) else 5) * pipelines(g, g["batch"]) for g in self.groups)
 
 
 def config_for(job, args):
@@ -411,7 +509,7 @@ def config_for(job, args):
         g = wl.groups[0]
         if args.batch is not None:
             g = dataclasses.replace(g, batch=args.batch)
-        ps = S.PARAM_SETS[g.set_name]
+        ps = S.param_set(g.set_name)
         return config_of(args, wl, g, ps)
     return {"workload": f"{wl.name}: " + ", ".join(
                 f"set {g['ps'].name} (N={g['ps'].N} q=2^{g['ps'].w} t={g['ps'].t}) x {g['batch']}"
@@ -586,7 +684,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32" if all(g["ps"].w == 32 for g in job.groups) else "u64",
+        "dtype": "u32" if all(getattr(g["ps"], "w", 64) == 32 for g in job.groups) else "u64",
         "data": "synthetic (seeded SplitMix64 keys, messages and tables; keys generated on the GPU)",
         "config": config_for(job, args),
         "decrypt_ok": decrypt_ok,
@@ -609,9 +707,14 @@ def main():
     if plain:
         line["plain_path"] = plain
         line["batched_over_plain"] = value / plain["value"]
+    if is_prime_set(ps0) and ps0.name in PAPER_MS_PER_BOOTSTRAP:
+        ms = PAPER_MS_PER_BOOTSTRAP[ps0.name]
+        line["paper_context"] = {"ms_per_bootstrap": ms, "bootstraps_per_s": 1e3 / ms,
+                                 "source": "Table 3 (one bootstrap, not parallelised; 60-core Xeon "
+                                           "Cascade Lake VM, 64-bit prime-modulus NTT)"}
     if world == 1 and not args.no_cpu_baseline and len(job.groups) == 1 and not job.wl.mlp_layers:
         g = job.wl.groups[0]
-        line["cpu_baseline"] = cpu_baseline(job.wl, g, S.PARAM_SETS[g.set_name])
+        line["cpu_baseline"] = cpu_baseline(job.wl, g, S.param_set(g.set_name))
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

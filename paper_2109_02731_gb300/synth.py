@@ -136,6 +136,10 @@ WORKLOADS: Dict[str, Workload] = {
     "tfhe_plain": Workload("tfhe_plain", 1, [Group("B", 1024, 4, "round_robin", mode="tfhe")]),
     "mlp": Workload("mlp", 4, [Group("D", 0, 2, "uniform")],
                     mlp_layers=[784, 128, 64, 10], mlp_inputs=64),
+    # the paper's own parameter sets (Table 1, prime Q), literal Bootstrap:
+    # l_boot = 6 sign rotations and one function rotation per input
+    "paper_80_6": Workload("paper_80_6", 5, [Group("FDFB-80-6", 1000, 4, "uniform")]),
+    "paper_80_7": Workload("paper_80_7", 6, [Group("FDFB-80-7", 456, 4, "uniform")]),
 }
 
 # Sub-stream identifiers (xored into the master seed before mixing).
@@ -468,3 +472,8 @@ def q_lut_tables(ps: QParamSet, seed: int, count: int, group: int = 0) -> np.nda
     """`count` random lookup tables f: Z_t -> Z_t, int64[count][t]."""
     st = Stream(seed, STREAM_LUTS, hash_name(ps.name), group)
     return st.below(count * ps.t, ps.t).reshape(count, ps.t)
+
+
+def param_set(name: str):
+    """A power-of-two set (PARAM_SETS) or a prime-modulus set (Q_PARAM_SETS)."""
+    return PARAM_SETS[name] if name in PARAM_SETS else Q_PARAM_SETS[name]
