@@ -196,6 +196,18 @@ FD_HD uint64_t modq_i128(__int128 x, const ModQ& m) {
   const uint64_t r = modq_u128((unsigned __int128)(-x), m);
   return r ? m.Q - r : 0;
 }
+// Residue of a lifted product sum, |x| < 2^96.  For k >= 48 (Q_1, Q_2,
+// Q_3) branch-free: x + Q 2^(97-k) lies in (0, 2^98), and two folds bring it
+// below 2^k + 2^42 <= 2Q (the excess shrinks by 2^k / c >= 2^28 per fold).
+FD_HD uint64_t modq_lift(__int128 x, const ModQ& m) {
+  if (m.k < 48) return modq_i128(x, m);
+  const unsigned __int128 lo_mask = (((unsigned __int128)1) << m.k) - 1;
+  unsigned __int128 y = (unsigned __int128)(x + (__int128)((unsigned __int128)m.Q << (97 - m.k)));
+  y = (y >> m.k) * m.c + (y & lo_mask);
+  y = (y >> m.k) * m.c + (y & lo_mask);
+  const uint64_t r = (uint64_t)y;
+  return r >= m.Q ? r - m.Q : r;
+}
 FD_HD uint64_t addq(uint64_t a, uint64_t b, uint64_t Q) {
   const uint64_t s = a + b;  // < 2Q < 2^64
   return s >= Q ? s - Q : s;

@@ -288,13 +288,19 @@ constexpr int br_blocks_for_regs(int threads, int regs) {
 // of at most 8 products is Montgomery-reduced: with transform values below p
 // (< 8 p^2 -> below 3p) it is corrected once; with the lazy family's
 // unreduced transform values (below 2^32: < 2^35 p -> below 9p) it is
-// brought into [0, 2p) by Shoup's product by 1.
-template <bool WIDE, bool LZ, typename Acc>
+// brought into [0, 2p) by Shoup's product by 1.  R14: up to 14 products (the
+// exact decompositions of the prime-modulus sets, l <= 7): < 14 p^2 < 2^63.8
+// reduces below 4.5p and is corrected twice.
+template <bool WIDE, bool LZ, typename Acc, bool R14 = false>
 __device__ __forceinline__ uint32_t acc_to_inv(Acc a, uint32_t p, uint32_t pneg, uint32_t ones) {
   if constexpr (WIDE) {
     const uint32_t r = redc((uint64_t)a, p, pneg);
-    if constexpr (LZ) return mul_shoup(r, 1u, ones, p);
-    else return umin32(r, r - 2 * p);
+    if constexpr (LZ) {
+      return mul_shoup(r, 1u, ones, p);
+    } else {
+      const uint32_t r1 = umin32(r, r - 2 * p);
+      return R14 ? umin32(r1, r1 - 2 * p) : r1;
+    }
   } else {
     return (uint32_t)a;
   }
@@ -582,8 +588,8 @@ blind_rotate_kernel(const BRParams prm) {
         uint32_t v[2][E];
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-          v[0][k] = acc_to_inv<WIDE, LZ>(macc[h][0][k], p, pneg, ones);
-          v[1][k] = acc_to_inv<WIDE, LZ>(macc[h][1][k], p, pneg, ones);
+          v[0][k] = acc_to_inv<WIDE, LZ, Acc, MQ>(macc[h][0][k], p, pneg, ones);
+          v[1][k] = acc_to_inv<WIDE, LZ, Acc, MQ>(macc[h][1][k], p, pneg, ones);
         }
         ntt_inv_m<L, EL, Y::K - 1, 2, XWI, PP>(v, t, twi, p, xb, bar, z);
         uint32_t* dst0 = stage + (stage_slot<P>(grp, swap) * KH + h) * N;
@@ -602,7 +608,7 @@ blind_rotate_kernel(const BRParams prm) {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][0][k], p, pneg, ones);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ, Acc, MQ>(macc[0][0][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         uint32_t* dst = stage + stage_slot<P>(grp, swap) * N;
 #pragma unroll
@@ -611,7 +617,7 @@ blind_rotate_kernel(const BRParams prm) {
       {
         uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ>(macc[0][1][k], p, pneg, ones);
+        for (int k = 0; k < E; ++k) v[k] = acc_to_inv<WIDE, LZ, Acc, MQ>(macc[0][1][k], p, pneg, ones);
         ntt_inv<L, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
         if (grp < 2) {
 #pragma unroll
@@ -641,7 +647,7 @@ blind_rotate_kernel(const BRParams prm) {
             const __int128 Xh = garner_exact<P>(x, prm.S);
             X += h == 0 ? Xh : Xh * ((__int128)1 << 32);
           }
-          acc[c * N + j] = (W)addq(acc[c * N + j], modq_i128(X, prm.mq), Qm);
+          acc[c * N + j] = (W)addq(acc[c * N + j], modq_lift(X, prm.mq), Qm);
           continue;
         }
         W add = 0;
@@ -1264,7 +1270,7 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_q_kernel(const Pub
     uint32_t x[P];
 #pragma unroll
     for (int g = 0; g < P; ++g) x[g] = stage[g * 2 * N + idx];
-    uint64_t r = modq_i128(garner_exact<P>(x, prm.S), prm.mq);
+    uint64_t r = modq_lift(garner_exact<P>(x, prm.S), prm.mq);
     if (idx < N) {
       const int p0 = rotated(r1, idx);
       const uint64_t p0q = p0 >= 0 ? (uint64_t)p0 : Q - (uint64_t)(-p0);
@@ -1351,7 +1357,7 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) rlwe_encrypt_q_kernel(con
       uint32_t x[P];
 #pragma unroll
       for (int g = 0; g < P; ++g) x[g] = stage[g * N + j];
-      const uint64_t X = modq_i128(garner_exact<P>(x, prm.S), prm.mq);
+      const uint64_t X = modq_lift(garner_exact<P>(x, prm.S), prm.mq);
       out[j] = addq(out[j], mulq(X, w, prm.mq), Q);
     }
   }

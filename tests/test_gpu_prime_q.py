@@ -85,7 +85,7 @@ def test_every_variant_matches_the_oracle(F, torch_cuda, ctx, OQ, qz):
     cts = OQ.encrypt_messages(QZ, kr.s, mr)
     refs = [OQ.fdfb_bootstrap(QZ, K, rot[i][0], rot[i][1], c, debug=True) for c, i in zip(cts, ids)]
     cur, count, _ = ctx.variant_info(sid)
-    assert count == 3
+    assert count == 4
     for v in range(count):
         ctx.set_variant(sid, v)
         out, dbg = run_q(F, torch_cuda, ctx, sid, QZ, cts, ids)
