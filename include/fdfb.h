@@ -86,7 +86,7 @@ typedef struct {
    *   - the RLWE side (keys, accumulators, the extracted and key-switched
    *     LWE samples) lives mod Q in 64-bit words (log2q = 64);
    *   - the LWE side lives mod q = 2N: input and output ciphertexts are
-   *     [n+1] 64-bit words in [0, 2N), Delta_q = 2N / t, so the first
+   *     [n+1] 64-bit words in [0, 2N), Delta_q = round(2N / t), so the first
    *     ModSwitch (q -> 2N) is the identity and the last is ModSwitch(Q -> q),
    *     round(q x / Q) round half up;
    *   - every gadget decomposition is exact: lg, lks, lpk must equal
@@ -99,6 +99,10 @@ typedef struct {
    *     base-L_boot digits and returns [round(Q/t) rotP'_1, 0] + sum_i p[i]
    *     c_R,i; the function rotation, SampleExtract and KeySwitch(ksK) follow,
    *     then ModSwitch(Q -> q);
+   *   - t is any integer in [2, N] (the pairwise coprime moduli of a CRT
+   *     representation, Section "Extending the Arithmetic", need not divide
+   *     2N): Delta_q = round(2N / t), and fdfb_lwe_decrypt returns
+   *     round(t (b - <a, s>) / 2N) mod t;
    *   - N is 256, 2048 or 4096; signed_digits and t_out must be 0;
    *     fdfb_bootstrap_multi (k > 1), the TFHE bootstrap and fdfb_lwe_affine
    *     are not available (FDFB_EINVAL).

@@ -107,6 +107,7 @@ def lib():
                 "orq_sample_extract": ([i32, C.c_uint64, vp, vp], None),
                 "orq_keyswitch": ([i32, C.c_uint64, i32, i32, i32, vp, vp, vp], None),
                 "orq_modswitch": ([C.c_uint64, i32, i32, vp, vp], None),
+                "orq_decrypt_q2n": ([i32, i32, i32, vp, vp], C.c_uint64),
                 "orq_pubmux": ([vp, vp, vp, vp, vp], None),
                 "orq_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
                 "orq_fdfb_batch": ([vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32], None),

@@ -31,6 +31,10 @@
  *       s_F = Coefs(sk) is therefore a uniform vector mod Q.
  *   G28 PubMux keeps p = p_1 - p_0 in Z_Q (no reduction mod t) and splits it
  *       into l_boot = ceil(log_{L_boot} Q) digits: the literal algorithm.
+ *   G29 t need not divide q = 2N (the CRT moduli of Section "Extending the
+ *       Arithmetic" are pairwise coprime): inputs carry Delta_{q,t} m with
+ *       Delta_{q,t} = round(2N / t), and decryption is round(t phase / q)
+ *       mod t.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -281,6 +285,17 @@ void orq_keyswitch(int n_in, u64 Q, int log2B, int ell, int out_len, const u64* 
             for (int k = 0; k < out_len; ++k) out[k] = mq_sub(out[k], mq_mul(dig[j], row[k], Q), Q);
         }
     }
+}
+
+/* Decryption on the LWE side, q = 2^logq, any plaintext modulus t (the
+ * pairwise coprime moduli of the CRT representation, Section "Extending the
+ * Arithmetic"): round(t (b - <a, s>) / q) mod t, round half up (G6, G29). */
+u64 orq_decrypt_q2n(int n, int logq, int t, const u8* s, const u64* ct) {
+    const u64 q = (u64)1 << logq;
+    u64 ph = ct[0];
+    for (int i = 0; i < n; ++i) ph -= ct[1 + i] * (u64)s[i];
+    ph &= q - 1;
+    return (u64)((((u128)ph * (u64)t + q / 2) >> logq) % (u64)t);
 }
 
 /* ModSwitch (appendix figure "Modulus switching algorithm") from Q to

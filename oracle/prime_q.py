@@ -11,7 +11,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import _i64, _p, _u8, _u64, lib, lwe_decrypt, lwe_encrypt, setup_polynomial
+from . import _i64, _p, _u8, _u64, lib, lwe_encrypt, setup_polynomial
 
 
 class orq_params(C.Structure):
@@ -123,7 +123,9 @@ def encrypt_messages(ps, s, mr) -> np.ndarray:
 
 
 def decrypt(ps, s, ct) -> int:
-    return int(lwe_decrypt(ps.logq, ps.t, s, ct))
+    """round(t (b - <a, s>) / q) mod t on the LWE side (q = 2N, any t)."""
+    s, ct = _u8(s), _u64(ct)
+    return int(lib().orq_decrypt_q2n(len(s), ps.logq, ps.t, _p(s), _p(ct)))
 
 
 def extprod(ps, C_row, d) -> np.ndarray:

@@ -693,7 +693,7 @@ int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
   if (P.k != 1 || P.log2q != 64) return FDFB_EINVAL;
   if (P.N != 256 && P.N != 2048 && P.N != 4096) return FDFB_EINVAL;
   if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
-  if (!is_pow2(P.t) || P.t < 2 || P.t > P.N) return FDFB_EINVAL;
+  if (P.t < 2 || P.t > P.N) return FDFB_EINVAL;  // any t: CRT moduli need not divide q = 2N
   if (P.signed_digits || P.t_out) return FDFB_EINVAL;
   const uint64_t Q = P.Q;
   int kbits = 64;
@@ -1410,9 +1410,10 @@ int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a,
   if (count == 0) return FDFB_OK;
   if (!s || !a || !e || !m || !ct_out) return FDFB_EINVAL;
   DeviceGuard g(ctx->device);
-  // prime-modulus sets encrypt mod q = 2N
+  // prime-modulus sets encrypt mod q = 2N with Delta = round(2N / t)
   const int logq = st->mq.Q ? st->L + 1 : st->w;
-  const uint64_t delta = (uint64_t)1 << (logq - st->logt);
+  const uint64_t delta = st->mq.Q ? ((2ull << st->L) + st->prm.t / 2) / st->prm.t
+                                  : (uint64_t)1 << (logq - st->logt);
   const unsigned blocks = (unsigned)((count + 7) / 8);
   cudaStream_t cs = as_stream(cuda_stream);
   if (st->w == 32)
@@ -1436,10 +1437,11 @@ int fdfb_lwe_decrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* ct
   cudaStream_t cs = as_stream(cuda_stream);
   if (st->w == 32)
     lwe_decrypt_kernel<uint32_t><<<blocks, 256, 0, cs>>>(s, (const uint32_t*)ct, count,
-                                                         (int)st->prm.n, st->logtout, m_out, logq);
+                                                         (int)st->prm.n, st->logtout, m_out, logq, 0);
   else
     lwe_decrypt_kernel<uint64_t><<<blocks, 256, 0, cs>>>(s, (const uint64_t*)ct, count,
-                                                         (int)st->prm.n, st->logtout, m_out, logq);
+                                                         (int)st->prm.n, st->logtout, m_out, logq,
+                                                         st->mq.Q ? (int)st->prm.t : 0);
   return cuda_err(cudaGetLastError());
 }
 

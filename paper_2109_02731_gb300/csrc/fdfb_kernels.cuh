@@ -1064,10 +1064,12 @@ __global__ void lwe_encrypt_kernel(const uint8_t* s, const W* a, const int64_t* 
   }
 }
 
-// Decryption round(t * phase / q) mod t (power-of-two t, round half up).
+// Decryption round(t * phase / q) mod t (round half up): power-of-two t
+// (t = 2^logt) by shifts, or any t (t_any > 0, the prime-modulus sets' CRT
+// moduli) as ((phase t + q/2) >> logq) mod t.
 template <typename W>
 __global__ void lwe_decrypt_kernel(const uint8_t* s, const W* ct, int64_t count, int n, int logt,
-                                   int32_t* m, int logq) {
+                                   int32_t* m, int logq, int t_any) {
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (c >= count) return;
@@ -1078,8 +1080,13 @@ __global__ void lwe_decrypt_kernel(const uint8_t* s, const W* ct, int64_t count,
   if (lane == 0) {
     const W mask = logq >= Word<W>::bits ? (W)~(W)0 : (W)(((W)1 << logq) - 1);
     const W ph = (W)(ct[c * (n + 1)] - acc);
-    const W r = (W)((W)((W)(ph + ((W)1 << (logq - logt - 1))) & mask) >> (logq - logt));
-    m[c] = (int32_t)r;
+    if (t_any > 0) {  // logq <= 14 here: the product fits 64 bits
+      const uint64_t phq = (uint64_t)(ph & mask);
+      m[c] = (int32_t)(((phq * (uint64_t)t_any + (1ull << (logq - 1))) >> logq) % (uint64_t)t_any);
+    } else {
+      const W r = (W)((W)((W)(ph + ((W)1 << (logq - logt - 1))) & mask) >> (logq - logt));
+      m[c] = (int32_t)r;
+    }
   }
 }
 

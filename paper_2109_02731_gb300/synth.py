@@ -395,8 +395,8 @@ class QParamSet:
         return _ceil_div(self.k, self.log2Lboot)
 
     @property
-    def delta_q(self) -> int:    # Delta_{q,t} of the input and output ciphertexts
-        return self.q // self.t
+    def delta_q(self) -> int:    # Delta_{q,t} = round(q / t) of the input and output ciphertexts
+        return (self.q + self.t // 2) // self.t
 
 
 # Table 1 columns with N <= 4096 (ring degree 2^13 needs more shared memory
@@ -477,3 +477,11 @@ def q_lut_tables(ps: QParamSet, seed: int, count: int, group: int = 0) -> np.nda
 def param_set(name: str):
     """A power-of-two set (PARAM_SETS) or a prime-modulus set (Q_PARAM_SETS)."""
     return PARAM_SETS[name] if name in PARAM_SETS else Q_PARAM_SETS[name]
+
+
+def crt_sets(base: str, moduli) -> List[QParamSet]:
+    """One prime-modulus set per CRT modulus t_i (pairwise coprime), the
+    geometry of `base` (Section "Extending the Arithmetic": Z_t with
+    t = prod t_i is Z_t1 x ... x Z_tm, one bootstrap per residue)."""
+    ps = Q_PARAM_SETS[base]
+    return [dataclasses.replace(ps, name=f"{base}-t{t}", t=int(t)) for t in moduli]

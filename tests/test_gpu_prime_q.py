@@ -209,3 +209,82 @@ def test_full_size_decrypts_and_variants_agree(F, torch_cuda, ctx, OQ, name):
     ctx.autotune(sid, batch)
     out, _ = run_q(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
     assert np.array_equal(out, outs[0])
+
+
+# ------------------------------------------------- CRT plaintexts -----------
+
+def test_crt_residue_set_matches_the_oracle(F, torch_cuda, ctx, OQ):
+    """An odd plaintext modulus (t = 7, not dividing q = 2N): bootstraps bit
+    for bit equal to the oracle's, and the library's encryption and general-t
+    decryption equal the oracle's."""
+    torch = torch_cuda
+    ps = S.crt_sets("QZ", [7])[0]
+    kr = S.q_key_randomness(QZ, 51)
+    K = OQ.QKeys(QZ, kr)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    table = np.array([(m * m + 5 * m + 3) % 7 for m in range(7)])
+    ctx.lut_setup(sid, table)
+    rot = OQ.rotation_polys(ps, [table])
+    m = np.concatenate([np.arange(7), np.arange(7)])
+    mr = S.q_message_randomness(ps, 52, len(m), m=m)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    ct_d = torch.empty((len(m), ps.n + 1), dtype=torch.int64, device="cuda")
+    ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                    torch.tensor(mr.m, device="cuda"), ct_d)
+    ctx.sync()
+    assert np.array_equal(F.to_host_words(ps, ct_d).astype(np.uint64), cts)
+    ids = np.zeros(len(m), np.int32)
+    ref = OQ.fdfb_batch(ps, K, rot, ids, cts, threads=8)
+    for v in range(ctx.variant_info(sid)[1]):
+        ctx.set_variant(sid, v)
+        out, _ = run_q(F, torch, ctx, sid, ps, cts, ids, debug=False)
+        assert np.array_equal(out, ref), f"variant {v}"
+    m_d = torch.empty(len(m), dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, s_d, F.to_device_words(ps, out), m_d)
+    ctx.sync()
+    got = m_d.cpu().numpy()
+    assert list(got) == [OQ.decrypt(ps, kr.s, o) for o in out] == [int(table[x]) for x in m]
+
+
+def test_crt_polynomial_full_size(F, torch_cuda, ctx, OQ):
+    """Z_9009 = Z_7 x Z_9 x Z_11 x Z_13 on FDFB-80-6's geometry: P(x) =
+    x^2 + 5x + 3 for 300 random x, one bootstrap per residue (the four sets
+    in one fdfb_bootstrap_mixed call), recombined by the CRT after
+    decryption."""
+    torch = torch_cuda
+    moduli = (7, 9, 11, 13)
+    t = int(np.prod(moduli))
+    sets = S.crt_sets("FDFB-80-6", moduli)
+    kr = S.q_key_randomness(S.Q_PARAM_SETS["FDFB-80-6"], 53)  # one secret for every residue
+    rng = np.random.default_rng(54)
+    x = rng.integers(0, t, 300)
+    P = lambda v: (v * v + 5 * v + 3)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    groups, dec = [], []
+    for gi, ps in enumerate(sets):
+        sid = ctx.register(ps)
+        ctx.keys_generate(sid, kr)
+        ctx.lut_setup(sid, [P(m) % ps.t for m in range(ps.t)])
+        mr = S.q_message_randomness(ps, 55, len(x), m=x % ps.t)
+        ct = torch.empty((len(x), ps.n + 1), dtype=torch.int64, device="cuda")
+        ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                        torch.tensor(mr.m, device="cuda"), ct)
+        ids = torch.zeros(len(x), dtype=torch.int32, device="cuda")
+        groups.append((sid, ct, ids, torch.empty_like(ct)))
+    ctx.bootstrap_mixed(groups)
+    ctx.sync()
+    for (sid, _, _, out), ps in zip(groups, sets):
+        m_d = torch.empty(len(x), dtype=torch.int32, device="cuda")
+        ctx.lwe_decrypt(sid, s_d, out, m_d)
+        ctx.sync()
+        got = m_d.cpu().numpy()
+        assert np.array_equal(got, P(x) % ps.t), f"modulus {ps.t}"
+        dec.append(got)
+    # CRT recombination: y = sum r_i M_i (M_i^-1 mod t_i) mod t
+    y = np.zeros(len(x), dtype=object)
+    for r, mi in zip(dec, moduli):
+        Mi = t // mi
+        y = y + r.astype(object) * Mi * pow(Mi, -1, mi)
+    assert [int(v) % t for v in y] == [int(P(int(v)) % t) for v in x]

@@ -265,3 +265,73 @@ def test_single_digit_pubmux_decrypts_alike(keys):
     cts = OQ.encrypt_messages(PS, kr.s, mr)
     out = OQ.fdfb_batch(ps1, K, rot, np.zeros(PS.t, np.int32), cts, threads=oracle.max_threads())
     assert [OQ.decrypt(PS, kr.s, o) for o in out] == [int(v) for v in f]
+
+
+# ------------------------------------------------- CRT plaintexts (G29) -----
+
+def crt_combine(residues, moduli):
+    """The x in Z_t (t = prod moduli) with x = r_i mod t_i (brute force)."""
+    t = int(np.prod(moduli))
+    for x in range(t):
+        if all(x % m == r for r, m in zip(residues, moduli)):
+            return x
+    raise AssertionError("no CRT solution")
+
+
+def test_general_t_decryption_rounds_exactly():
+    import dataclasses
+    rng = np.random.default_rng(31)
+    s = rng.integers(0, 2, PS.n).astype(np.uint8)
+    for t in (3, 5, 7, 9, 64):
+        ps = dataclasses.replace(PS, t=t)
+        for _ in range(40):
+            ct = rng.integers(0, PS.q, PS.n + 1).astype(np.uint64)
+            ph = (int(ct[0]) - sum(int(a) * int(b) for a, b in zip(ct[1:], s))) % PS.q
+            want = int(Fraction(t * ph, PS.q) + Fraction(1, 2)) % t
+            assert OQ.decrypt(ps, s, ct) == want
+    assert S.crt_sets("QZ", [7])[0].delta_q == round(PS.q / 7)
+
+
+def test_crt_polynomial_on_every_residue():
+    """Section "Extending the Arithmetic": Z_105 = Z_3 x Z_5 x Z_7; the
+    polynomial P(x) = x^2 + 5x + 3 acts residue-wise, so each residue's
+    bootstrap maps x_i to P(x_i) mod t_i.  Every residue of every modulus is
+    bootstrapped; recombining the decrypted outputs gives P(x) mod 105 for
+    every x in Z_105."""
+    moduli = (3, 5, 7)
+    sets = S.crt_sets("QZ", moduli)
+    kr = S.q_key_randomness(PS, 41)
+    K = OQ.QKeys(PS, kr)  # the keys do not depend on t
+    P = lambda x: x * x + 5 * x + 3
+    dec = []
+    for ps in sets:
+        table = np.array([P(m) % ps.t for m in range(ps.t)])
+        rot = OQ.rotation_polys(ps, [table])
+        mr = S.q_message_randomness(ps, 42, ps.t, m=np.arange(ps.t))
+        cts = OQ.encrypt_messages(ps, kr.s, mr)
+        out = OQ.fdfb_batch(ps, K, rot, np.zeros(ps.t, np.int32), cts, threads=oracle.max_threads())
+        got = [OQ.decrypt(ps, kr.s, o) for o in out]
+        assert got == [int(v) for v in table]
+        dec.append(got)
+    t = int(np.prod(moduli))
+    for x in range(t):
+        y = crt_combine([dec[i][x % m] for i, m in enumerate(moduli)], moduli)
+        assert y == P(x) % t
+
+
+def test_crt_addition_wraps_before_bootstrapping():
+    """With t = 7 not dividing q = 2N, the sum of two encryptions still
+    decrypts (after an identity bootstrap) to (a + b) mod 7, wrap included:
+    Delta t = q + eps with |eps| < t/2 only adds eps to the noise (G29)."""
+    ps = S.crt_sets("QZ", [7])[0]
+    kr = S.q_key_randomness(PS, 43)
+    K = OQ.QKeys(PS, kr)
+    rot = OQ.rotation_polys(ps, [np.arange(7)])
+    pairs = [(3, 5), (6, 6), (4, 3), (0, 6), (2, 1)]
+    m = np.array([p for ab in pairs for p in ab])
+    mr = S.q_message_randomness(ps, 44, len(m), m=m)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    sums = np.array([(cts[2 * i].astype(object) + cts[2 * i + 1].astype(object)) % ps.q
+                     for i in range(len(pairs))], dtype=np.uint64)
+    out = OQ.fdfb_batch(ps, K, rot, np.zeros(len(pairs), np.int32), sums, threads=oracle.max_threads())
+    assert [OQ.decrypt(ps, kr.s, o) for o in out] == [(a + b) % 7 for a, b in pairs]
