@@ -62,7 +62,8 @@ def is_prime_set(ps) -> bool:
 # bootstrap, not parallelised, on a 60-core Xeon Cascade Lake VM with a
 # 64-bit prime-modulus NTT): context for the prime-modulus workloads.
 PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7": 9278.0,
-                          "FDFB-100-7": 13781.0}
+                          "FDFB-100-7": 13781.0, "TFHE-100-7": 7757.0, "TFHE-80-2": 306.0,
+                          "TFHE-100-2": 321.0}
 
 
 # DRAM bytes (read + write) of one blind-rotation launch over the whole batch,
@@ -158,7 +159,7 @@ def rank_messages(ps, seed: int, batch: int, rank: int, group: int = 0):
     return S.message_randomness(ps, seed, batch, group=1000 * rank + group)
 
 
-def q_oracle_sample(ps, seconds_target: float = 10.0):
+def q_oracle_sample(ps, seconds_target: float = 10.0, tfhe: bool = False):
     """The prime-modulus oracle's time per bootstrap, from a bounded sample:
     one bootstrap of these sets takes the schoolbook oracle hours (about
     (l_boot + 1) n CMux steps of 2 (2 l) N^2 products mod Q), so the sample
@@ -199,6 +200,12 @@ def q_oracle_sample(ps, seconds_target: float = 10.0):
     t0 = time.perf_counter()
     OQ.pubmux(ps, cR, p0, -p0)
     t_pm = time.perf_counter() - t0
+    if tfhe:  # the TFHE bootstrap: one rotation and the LWE key switch
+        sec = n * t_step + t_ks
+        desc = (f"{steps} full-size CMux step(s) ({t_step:.2f} s each, x {n} per TFHE bootstrap) and the "
+                f"LWE key switch ({t_ks:.2f} s) of the schoolbook oracle on one core, scaled to one "
+                f"bootstrap ({sec / 60:.1f} min)")
+        return sec, desc
     sec = (lb + 1) * n * t_step + lb * t_pk + t_pm + t_ks
     desc = (f"{steps} full-size CMux step(s) ({t_step:.2f} s each, x {(lb + 1) * n} per bootstrap), one "
             f"packing key switch ({t_pk:.2f} s, x {lb}), PubMux ({t_pm:.2f} s) and the LWE key switch "
@@ -223,12 +230,13 @@ def run_reference(args):
     import oracle as O
     wl, g, ps = workload_desc(args.workload)
     if is_prime_set(ps):
+        tf = g.mode == "tfhe"
         for _ in range(args.warmup):
-            q_oracle_sample(ps)
+            q_oracle_sample(ps, tfhe=tf)
         secs = []
         desc = ""
         for _ in range(args.steps):
-            sec, desc = q_oracle_sample(ps)
+            sec, desc = q_oracle_sample(ps, tfhe=tf)
             secs.append(sec)
         value = args.steps / sum(secs)
         line = {
@@ -291,7 +299,9 @@ def run_reference(args):
 
 def config_of(args, wl, g, ps):
     if is_prime_set(ps):
-        return {"workload": f"{wl.name}: FDFB, the paper's set {ps.name} (Table 1): n={ps.n} N={ps.N} "
+        kind = ("TFHE bootstrap (one blind rotation of a pre-rotation polynomial)" if g.mode == "tfhe"
+                else "FDFB")
+        return {"workload": f"{wl.name}: {kind}, the paper's set {ps.name} (Table 1): n={ps.n} N={ps.N} "
                             f"Q=2^{ps.k}-{(1 << ps.k) - ps.Q} q=2N={ps.q} t={ps.t} B_g=2^{ps.log2Bg} l_g={ps.lg} "
                             f"B_ks=2^{ps.log2Bks} l_ks={ps.lks} B_pk=2^{ps.log2Bpk} l_pk={ps.lpk} "
                             f"L_boot=2^{ps.log2Lboot} l_boot={ps.lboot} (exact decompositions, uniform RLWE "
@@ -312,7 +322,7 @@ def cpu_baseline(wl, g, ps, seconds_target=20.0):
     """The oracle timed on a bounded sample (rank 0, one GPU only)."""
     import oracle as O
     if is_prime_set(ps):
-        sec, desc = q_oracle_sample(ps)
+        sec, desc = q_oracle_sample(ps, tfhe=g.mode == "tfhe")
         return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     cores = O.max_threads()
     O.set_threads(cores)
@@ -373,7 +383,8 @@ class Job:
         for f in fs:
             ctx.lut_setup(sid, f)
         if g.mode == "tfhe":
-            for poly in S.tfhe_polynomials(ps, wl.seed, g.n_luts):
+            polys = (S.q_tfhe_polynomials if prime else S.tfhe_polynomials)(ps, wl.seed, g.n_luts)
+            for poly in polys:
                 ctx.tfhe_poly_setup(sid, poly)
         ids_np = S.lut_assignment(wl.seed, g.batch, g.n_luts, g.lut_assign, gi)
         mr = rank_messages(ps, wl.seed, g.batch, rank, gi)
@@ -491,7 +502,8 @@ class Job:
             g = self.groups[0]
             return sum(1 + 5 * pipelines(g, b) for b in self.mlp_batches)
         if any(g.get("mode") == "tfhe" for g in self.groups):
-            return 3 * len(self.groups)  # accumulator, blind rotation, key switch
+            # accumulator, blind rotation, key switch (+ its finalize kernel mod Q)
+            return sum(4 if is_prime_set(g["ps"]) else 3 for g in self.groups)
         # prime-modulus sets: each key switch is a sum kernel and a finalize kernel
         return sum((7 if is_prime_set(g["ps"]) else 5) * pipelines(g, g["batch"]) for g in self.groups)
 

@@ -80,9 +80,10 @@ typedef struct {
    * outputs encrypt Delta' f(m). */
   uint32_t t_out;
   /* Prime-modulus parameter sets (Table 1); 0 selects q = Q = 2^log2q
-   * (everything above).  Q = 2^k - c with 33 <= k <= 63 and odd c < 2^20
+   * (everything above).  Q = 2^k - c with 32 <= k <= 63 and odd c < 2^20
    * (the paper's Q_1 = 2^62 - 65535, Q_2 = 2^63 - 278527, Q_3 = 2^48 -
-   * 163839) runs the paper's Bootstrap figure literally:
+   * 163839, Q_4 = 2^32 - 139263) runs the paper's Bootstrap
+   * figure literally:
    *   - the RLWE side (keys, accumulators, the extracted and key-switched
    *     LWE samples) lives mod Q in 64-bit words (log2q = 64);
    *   - the LWE side lives mod q = 2N: input and output ciphertexts are
@@ -103,9 +104,12 @@ typedef struct {
    *     representation, Section "Extending the Arithmetic", need not divide
    *     2N): Delta_q = round(2N / t), and fdfb_lwe_decrypt returns
    *     round(t (b - <a, s>) / 2N) mod t;
-   *   - N is 256, 2048 or 4096; signed_digits and t_out must be 0;
-   *     fdfb_bootstrap_multi (k > 1), the TFHE bootstrap and fdfb_lwe_affine
-   *     are not available (FDFB_EINVAL).
+   *   - N is 256, 1024, 2048 or 4096; signed_digits and t_out must be 0;
+   *     fdfb_bootstrap_multi (k > 1) and fdfb_lwe_affine are not available
+   *     (FDFB_EINVAL);
+   *   - the TFHE bootstrap takes polynomials of residues mod Q and, like the
+   *     full-domain one, inputs mod 2N (ModSwitch the identity), returning
+   *     ModSwitch(Q -> 2N) of the key-switched sample.
    * Keys are uploaded in the canonical layouts as residues mod Q; the RLWE
    * key of fdfb_keys_generate is uniform in Z_Q^N (fdfb_keygen_inputs.sk_q). */
   uint64_t Q;

@@ -108,6 +108,8 @@ def lib():
                 "orq_keyswitch": ([i32, C.c_uint64, i32, i32, i32, vp, vp, vp], None),
                 "orq_modswitch": ([C.c_uint64, i32, i32, vp, vp], None),
                 "orq_decrypt_q2n": ([i32, i32, i32, vp, vp], C.c_uint64),
+                "orq_tfhe_bootstrap": ([vp, vp, vp, vp, vp, vp], None),
+                "orq_tfhe_batch": ([vp, vp, vp, vp, vp, i64, vp, vp, i32], None),
                 "orq_pubmux": ([vp, vp, vp, vp, vp], None),
                 "orq_fdfb_bootstrap": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], None),
                 "orq_fdfb_batch": ([vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32], None),

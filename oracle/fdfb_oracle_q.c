@@ -431,3 +431,39 @@ void orq_fdfb_batch(const orq_params* P, const u64* bsk, const u64* pk, const u6
                            ct + (size_t)b * (n + 1), out + (size_t)b * (n + 1), NULL);
     }
 }
+
+/* TFHE bootstrap (figure "TFHE Bootstrapping") on a prime-modulus set:
+ * ctN = ct (q = 2N, G25); acc = [poly X^{b_N}, 0]; BlindRotate;
+ * SampleExtract; KeySwitch(ksK); ModSwitch(Q -> q).  poly: [N] mod Q. */
+void orq_tfhe_bootstrap(const orq_params* P, const u64* bsk, const u64* ksk, const u64* poly,
+                        const u64* ct, u64* out) {
+    const int n = P->n, N = P->N;
+    const u64 Q = P->Q;
+    int logq = 0;
+    while ((1 << logq) < 2 * N) ++logq;
+    u64* ctN = (u64*)malloc((size_t)(n + 1) * sizeof(u64));
+    for (int i = 0; i <= n; ++i) ctN[i] = ct[i] & (u64)(2 * N - 1);
+    u64* acc = (u64*)malloc((size_t)2 * N * sizeof(u64));
+    orq_poly_mul_xk(N, Q, poly, (i64)ctN[0], acc);
+    for (int j = 0; j < N; ++j) acc[N + j] = 0;
+    orq_blind_rotate(P, bsk, acc, ctN);
+    u64* cQ = (u64*)malloc((size_t)(N + 1) * sizeof(u64));
+    orq_sample_extract(N, Q, acc, cQ);
+    u64* cKS = (u64*)malloc((size_t)(n + 1) * sizeof(u64));
+    orq_keyswitch(N, Q, P->log2Bks, P->lks, n + 1, ksk, cQ, cKS);
+    orq_modswitch(Q, logq, n + 1, cKS, out);
+    free(cKS);
+    free(cQ);
+    free(acc);
+    free(ctN);
+}
+
+/* Batch: item b uses polys[poly_ids[b]] ([n_polys][N]). */
+void orq_tfhe_batch(const orq_params* P, const u64* bsk, const u64* ksk, const u64* polys,
+                    const int32_t* poly_ids, int64_t batch, const u64* ct, u64* out, int threads) {
+    const int n = P->n, N = P->N;
+#pragma omp parallel for num_threads(threads > 0 ? threads : 1) schedule(dynamic, 1) if (threads > 1)
+    for (int64_t b = 0; b < batch; ++b)
+        orq_tfhe_bootstrap(P, bsk, ksk, polys + (size_t)poly_ids[b] * N, ct + (size_t)b * (n + 1),
+                           out + (size_t)b * (n + 1));
+}

@@ -214,3 +214,44 @@ def rotation_polys(ps, tables) -> np.ndarray:
         p0, p1 = setup_polynomial(ps.N, ps.t, f)
         out.append(np.stack([p0, p1]))
     return np.stack(out).astype(np.int64)
+
+
+def tfhe_bootstrap(ps, keys: QKeys, poly, ct) -> np.ndarray:
+    """The TFHE bootstrap of ct (mod q = 2N) with pre-rotation polynomial
+    poly ([N] mod Q); returns [n+1] mod q."""
+    P = params(ps)
+    poly, ct = _u64(poly), _u64(ct)
+    out = np.zeros(ps.n + 1, dtype=np.uint64)
+    lib().orq_tfhe_bootstrap(C.byref(P), _p(keys.bsk), _p(keys.ksk), _p(poly), _p(ct), _p(out))
+    return out
+
+
+def tfhe_batch(ps, keys: QKeys, polys, poly_ids, cts, threads: int = 1) -> np.ndarray:
+    P = params(ps)
+    polys, cts = _u64(polys), _u64(cts)
+    ids = np.ascontiguousarray(np.asarray(poly_ids, dtype=np.int32))
+    out = np.zeros_like(cts)
+    lib().orq_tfhe_batch(C.byref(P), _p(keys.bsk), _p(keys.ksk), _p(polys), _p(ids), len(ids),
+                         _p(cts), _p(out), int(threads))
+    return out
+
+
+def tfhe_test_polynomial(ps, f_half) -> np.ndarray:
+    """A pre-rotation polynomial mod Q mapping m in [0, t/2) to
+    Delta_Q f_half[m] and m + t/2 to -Delta_Q f_half[m] (the negacyclic
+    half): coefficient 0 of poly X^y must be Delta_Q f(m) for y within N/t of
+    round(2N/t) m in [0, N), and y rounding to t/2 gives -Delta_Q f(0).
+    Coefficient 0 of poly X^y is poly[0] for y = 0 and -poly[N - y] for
+    0 < y < N.  Test-side construction (the library takes any polynomial)."""
+    N, t, Q = ps.N, ps.t, ps.Q
+    D = delta(Q, t)
+    poly = np.zeros(N, dtype=np.uint64)
+    step = ps.delta_q
+    for y in range(N):
+        m = (y + step // 2) // step
+        v = D * int(f_half[m]) if m < t // 2 else -D * int(f_half[0])
+        if y == 0:
+            poly[0] = v % Q
+        else:
+            poly[N - y] = (-v) % Q
+    return poly

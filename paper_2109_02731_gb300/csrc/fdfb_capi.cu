@@ -24,12 +24,14 @@ const Ops* ops_n11(int w, int variant);
 const Ops* ops_n12(int w, int variant);
 
 const Ops* ops_q_n8(int variant);
+const Ops* ops_q_n10(int variant);
 const Ops* ops_q_n11(int variant);
 const Ops* ops_q_n12(int variant);
 
 const Ops* find_ops_q(int L, int variant) {
   switch (L) {
     case 8: return ops_q_n8(variant);
+    case 10: return ops_q_n10(variant);
     case 11: return ops_q_n11(variant);
     case 12: return ops_q_n12(variant);
     default: return nullptr;
@@ -691,14 +693,14 @@ int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
 // every lift with the primes of each variant, and builds the variants.
 int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
   if (P.k != 1 || P.log2q != 64) return FDFB_EINVAL;
-  if (P.N != 256 && P.N != 2048 && P.N != 4096) return FDFB_EINVAL;
+  if (P.N != 256 && P.N != 1024 && P.N != 2048 && P.N != 4096) return FDFB_EINVAL;
   if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
   if (P.t < 2 || P.t > P.N) return FDFB_EINVAL;  // any t: CRT moduli need not divide q = 2N
   if (P.signed_digits || P.t_out) return FDFB_EINVAL;
   const uint64_t Q = P.Q;
   int kbits = 64;
   while (kbits > 0 && !((Q >> (kbits - 1)) & 1)) --kbits;
-  if (kbits < 33 || kbits > 63) return FDFB_EINVAL;
+  if (kbits < 32 || kbits > 63) return FDFB_EINVAL;
   const uint64_t c = ((uint64_t)1 << kbits) - Q;
   if (!(Q & 1) || c == 0 || c >= ((uint64_t)1 << 20)) return FDFB_EINVAL;
   auto exact_l = [&](uint32_t log2B, uint32_t l) {
@@ -728,7 +730,7 @@ int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
   st->logt = ilog2(P.t);
   st->tout = (int)P.t;
   st->logtout = st->logt;
-  st->mq = ModQ{Q, c, kbits};
+  st->mq = ModQ{Q, c, kbits, modq_folds(Q, c, kbits)};
   st->lboot = (int)P.lboot;
   const uint64_t h = (uint64_t)(((unsigned __int128)Q + P.t) / (2 * (uint64_t)P.t));  // round(Q / 2t)
   st->delta_q = (uint64_t)(((unsigned __int128)Q + P.t / 2) / P.t);                // round(Q / t)
@@ -862,13 +864,13 @@ int keys_generate_q(fdfb_ctx* ctx, SetState* st, const fdfb_keygen_inputs* in, c
 // The TFHE bootstrap's accumulator kernel for ring degree 2^L.
 template <typename W>
 cudaError_t launch_tfhe_acc(int L, int64_t batch, cudaStream_t s, const W* ct, int n, const int32_t* ids,
-                            const W* polys, int n_polys, W* acc, int* err) {
+                            const W* polys, int n_polys, W* acc, int* err, uint64_t Q) {
   switch (L) {
-    case 8: tfhe_acc_kernel<W, 8><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
-    case 9: tfhe_acc_kernel<W, 9><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
-    case 10: tfhe_acc_kernel<W, 10><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
-    case 11: tfhe_acc_kernel<W, 11><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
-    case 12: tfhe_acc_kernel<W, 12><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err); break;
+    case 8: tfhe_acc_kernel<W, 8><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
+    case 9: tfhe_acc_kernel<W, 9><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
+    case 10: tfhe_acc_kernel<W, 10><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
+    case 11: tfhe_acc_kernel<W, 11><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
+    case 12: tfhe_acc_kernel<W, 12><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1187,8 +1189,11 @@ int fdfb_lut_setup(fdfb_ctx* ctx, int set_id, const uint32_t* f, int* lut_id_out
 
 int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_id_out) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || !poly || !poly_id_out || st->mq.Q) return FDFB_EINVAL;
+  if (!st || !poly || !poly_id_out) return FDFB_EINVAL;
   const size_t N = st->prm.N;
+  if (st->mq.Q)
+    for (size_t j = 0; j < N; ++j)
+      if (((const uint64_t*)poly)[j] >= st->mq.Q) return FDFB_EINVAL;  // residues mod Q
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
   const size_t off = st->tpolys_host.size();
@@ -1212,7 +1217,7 @@ int fdfb_tfhe_poly_setup(fdfb_ctx* ctx, int set_id, const void* poly, int* poly_
 int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* poly_ids,
                         int64_t batch, void* ct_out, void* cuda_stream) {
   SetState* st = get_set(ctx, set_id);
-  if (!st || batch < 0 || batch > 0x7fffffff || st->mq.Q) return FDFB_EINVAL;
+  if (!st || batch < 0 || batch > 0x7fffffff) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !poly_ids || !ct_out) return FDFB_EINVAL;
   if (!st->keys) return FDFB_ENOKEYS;
@@ -1230,11 +1235,11 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
     if (st->w == 32)
       FD_CUDA(launch_tfhe_acc<uint32_t>(st->L, batch, s, (const uint32_t*)ct_in, (int)P.n, poly_ids,
                                         (const uint32_t*)st->tpolys.p, st->n_tpolys, (uint32_t*)accF,
-                                        ctx->d_err));
+                                        ctx->d_err, 0));
     else
       FD_CUDA(launch_tfhe_acc<uint64_t>(st->L, batch, s, (const uint64_t*)ct_in, (int)P.n, poly_ids,
                                         (const uint64_t*)st->tpolys.p, st->n_tpolys, (uint64_t*)accF,
-                                        ctx->d_err));
+                                        ctx->d_err, st->mq.Q));
   }
   Variant& bv = st->br();
   BRParams br{};
@@ -1254,14 +1259,23 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
   br.rep = 1;
   br.signed_digits = (int)P.signed_digits;
   br.err = ctx->d_err;
+  if (st->mq.Q) fill_br_q(br, *st);
   {
     StageTimer tm(ctx, 3, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
   }
   {
     StageTimer tm(ctx, 4, s);
-    FD_TRY(launch_keyswitch(ctx, st->w, cQ, batch, (int)N, st->ksk.p, P.lks, P.log2Bks,
-                            trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
+    if (st->mq.Q) {
+      // exact half sums after cQ, then mod Q and ModSwitch(Q -> 2N)
+      uint64_t* sums = (uint64_t*)((unsigned char*)cQ + (size_t)batch * (N + 1) * wb);
+      FD_TRY(launch_keyswitch_q(ctx, *st, (const uint64_t*)cQ, batch, (int)N,
+                                (const uint32_t*)st->ksk_split.p, P.lks, P.log2Bks, (int)P.n + 1, sums,
+                                st->L + 1, (uint64_t*)ct_out, s));
+    } else {
+      FD_TRY(launch_keyswitch(ctx, st->w, cQ, batch, (int)N, st->ksk.p, P.lks, P.log2Bks,
+                              trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
+    }
   }
   return FDFB_OK;
 }

@@ -176,7 +176,21 @@ struct ModQ {
   uint64_t Q;  // 0: the set works modulo 2^w instead
   uint64_t c;  // Q = 2^k - c
   int k;
+  int folds;   // folds that bring any value below 2^98 under 2Q (modq_lift)
 };
+
+// The fold count of modq_lift: the smallest f with F^f(2^98 - 1) < 2Q for
+// the bound map F(u) = (u >> k) c + 2^k - 1 (1 for Q_1 and Q_2, 2 for Q_3,
+// 5 for Q_4).
+inline int modq_folds(uint64_t Q, uint64_t c, int k) {
+  unsigned __int128 ub = (((unsigned __int128)1) << 98) - 1;
+  int f = 0;
+  while (ub >= (unsigned __int128)2 * Q && f < 16) {
+    ub = (ub >> k) * c + ((((unsigned __int128)1) << k) - 1);
+    ++f;
+  }
+  return f;
+}
 
 // x mod Q for any x < 2^128: replace x by (x >> k) c + (x mod 2^k) while x
 // has bits at or above 2^k (each fold divides the excess by 2^k / c >= 2^12,
@@ -196,15 +210,14 @@ FD_HD uint64_t modq_i128(__int128 x, const ModQ& m) {
   const uint64_t r = modq_u128((unsigned __int128)(-x), m);
   return r ? m.Q - r : 0;
 }
-// Residue of a lifted product sum, |x| < 2^96.  For k >= 48 (Q_1, Q_2,
-// Q_3) branch-free: x + Q 2^(97-k) lies in (0, 2^98), and two folds bring it
-// below 2^k + 2^42 <= 2Q (the excess shrinks by 2^k / c >= 2^28 per fold).
+// Residue of a lifted product sum, |x| < 2^96, without data-dependent
+// branches: x + Q 2^(97-k) lies in (0, 2^98), m.folds folds (the same count
+// for every thread) bring it below 2Q, one conditional subtraction ends it.
 FD_HD uint64_t modq_lift(__int128 x, const ModQ& m) {
-  if (m.k < 48) return modq_i128(x, m);
   const unsigned __int128 lo_mask = (((unsigned __int128)1) << m.k) - 1;
   unsigned __int128 y = (unsigned __int128)(x + (__int128)((unsigned __int128)m.Q << (97 - m.k)));
-  y = (y >> m.k) * m.c + (y & lo_mask);
-  y = (y >> m.k) * m.c + (y & lo_mask);
+#pragma unroll 1
+  for (int f = 0; f < m.folds; ++f) y = (y >> m.k) * m.c + (y & lo_mask);
   const uint64_t r = (uint64_t)y;
   return r >= m.Q ? r - m.Q : r;
 }

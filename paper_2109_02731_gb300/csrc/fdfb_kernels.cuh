@@ -808,10 +808,11 @@ __global__ void __launch_bounds__(P * (1 << (L - EL))) pubmux_kernel(const PubMu
 template <typename W, int L>
 __global__ void __launch_bounds__(256)
 tfhe_acc_kernel(const W* __restrict__ ct, int n, const int32_t* __restrict__ ids,
-                const W* __restrict__ polys, int n_polys, W* __restrict__ acc, int* err) {
+                const W* __restrict__ polys, int n_polys, W* __restrict__ acc, int* err, uint64_t Q) {
   constexpr int N = 1 << L;
   const int64_t ci = blockIdx.x;
-  const int bN = (int)modswitch_2n<W, L>(ct[ci * (n + 1)]);
+  // prime-modulus sets (Q != 0): the input is already mod 2N, negation mod Q
+  const int bN = Q ? (int)((uint64_t)ct[ci * (n + 1)] & (2 * N - 1)) : (int)modswitch_2n<W, L>(ct[ci * (n + 1)]);
   int id = ids[ci];
   if (id < 0 || id >= n_polys) {
     if (threadIdx.x == 0) atomicExch(err, -6);
@@ -823,7 +824,7 @@ tfhe_acc_kernel(const W* __restrict__ ct, int n, const int32_t* __restrict__ ids
     bool neg;
     const int m = rot_src<L>(j, bN, neg);
     const W v = poly[m];
-    out[j] = neg ? (W)(0 - v) : v;
+    out[j] = neg ? (Q ? (W)negq((uint64_t)v, Q) : (W)(0 - v)) : v;
     out[N + j] = 0;
   }
 }

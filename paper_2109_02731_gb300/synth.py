@@ -140,6 +140,9 @@ WORKLOADS: Dict[str, Workload] = {
     # l_boot = 6 sign rotations and one function rotation per input
     "paper_80_6": Workload("paper_80_6", 5, [Group("FDFB-80-6", 1000, 4, "uniform")]),
     "paper_80_7": Workload("paper_80_7", 6, [Group("FDFB-80-7", 456, 4, "uniform")]),
+    # Table 1's TFHE:80:2 through the TFHE bootstrap (one rotation)
+    "paper_tfhe_80_2": Workload("paper_tfhe_80_2", 7, [Group("TFHE-80-2", 1024, 4, "round_robin",
+                                                             mode="tfhe")]),
 }
 
 # Sub-stream identifiers (xored into the master seed before mixing).
@@ -414,6 +417,18 @@ Q_PARAM_SETS: Dict[str, QParamSet] = {
                             log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
     "QZ": QParamSet("QZ", n=24, N=256, Q=Q1, t=8, log2Bg=11, log2Bks=6, log2Bpk=13, log2Lboot=11,
                     sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
+    # Table 1's TFHE columns (the paper's comparison point: one blind
+    # rotation of a pre-rotation polynomial, negacyclic functions); they give
+    # no packing key or L_boot, so the FDFB-only gadgets take B_RGSW.
+    "TFHE-80-2": QParamSet("TFHE-80-2", n=424, N=1024, Q=Q4, t=4, log2Bg=11, log2Bks=4,
+                           log2Bpk=11, log2Lboot=11, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
+    "TFHE-100-2": QParamSet("TFHE-100-2", n=525, N=1024, Q=Q4, t=4, log2Bg=11, log2Bks=4,
+                            log2Bpk=11, log2Lboot=11, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
+    "TFHE-100-7": QParamSet("TFHE-100-7", n=1500, N=4096, Q=Q3, t=128, log2Bg=16, log2Bks=1,
+                            log2Bpk=16, log2Lboot=16, sigma_lwe=2.0 ** 18, sigma_glwe=3.2),
+    # small set on Q_4 (k = 32) for the exhaustive checks
+    "QT": QParamSet("QT", n=24, N=256, Q=Q4, t=4, log2Bg=11, log2Bks=4, log2Bpk=11, log2Lboot=11,
+                    sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
 }
 
 
@@ -485,3 +500,10 @@ def crt_sets(base: str, moduli) -> List[QParamSet]:
     t = prod t_i is Z_t1 x ... x Z_tm, one bootstrap per residue)."""
     ps = Q_PARAM_SETS[base]
     return [dataclasses.replace(ps, name=f"{base}-t{t}", t=int(t)) for t in moduli]
+
+
+def q_tfhe_polynomials(ps: QParamSet, seed: int, count: int) -> np.ndarray:
+    """Pre-rotation polynomials for timing the TFHE bootstrap of a prime-modulus
+    set: [count][N] residues uniform mod Q (the cost does not depend on them)."""
+    st = Stream(seed, STREAM_LUTS, 100)
+    return np.stack([_below_big(st.sub(i), ps.N, ps.Q) for i in range(count)])

@@ -152,11 +152,11 @@ def test_registration_rules(F, ctx):
     def reg(ps):
         return ctx.register(ps)
     with pytest.raises(F.FDFBError):
-        reg(dataclasses.replace(QZ, N=1024))              # no layout at N = 1024
+        reg(dataclasses.replace(QZ, N=512))               # no layout at N = 512
     with pytest.raises(F.FDFBError):
         reg(dataclasses.replace(QZ, Q=S.Q1 + 1))          # even modulus
     with pytest.raises(F.FDFBError):
-        reg(dataclasses.replace(QZ, Q=S.Q4))              # k = 32 < 33
+        reg(dataclasses.replace(QZ, Q=(1 << 31) - 1))     # k = 31 < 32
     with pytest.raises(F.FDFBError):
         reg(dataclasses.replace(QZ, log2Lboot=7))         # l_boot = 9 > 8
     # a caller-given l that is not ceil(k / log2 B)
@@ -176,8 +176,8 @@ def test_unavailable_calls_refuse(F, torch_cuda, ctx, qz):
     out = torch.empty((2, 2, QZ.n + 1), dtype=torch.int64, device="cuda")
     with pytest.raises(F.FDFBError):
         ctx.bootstrap_multi(sid, ct, ids, out)
-    with pytest.raises(F.FDFBError):
-        ctx.tfhe_poly_setup(sid, np.zeros(QZ.N, np.uint64))
+    with pytest.raises(F.FDFBError):  # a coefficient not below Q
+        ctx.tfhe_poly_setup(sid, np.full(QZ.N, QZ.Q, np.uint64))
 
 
 @pytest.mark.parametrize("name", ["FDFB-80-6", "FDFB-80-7"])
@@ -288,3 +288,96 @@ def test_crt_polynomial_full_size(F, torch_cuda, ctx, OQ):
         Mi = t // mi
         y = y + r.astype(object) * Mi * pow(Mi, -1, mi)
     assert [int(v) % t for v in y] == [int(P(int(v)) % t) for v in x]
+
+
+# ----------------------------------- TFHE bootstrap and Q_4 (k = 32) --------
+
+@pytest.mark.parametrize("name", ["QZ", "QT"])
+def test_tfhe_matches_the_oracle(F, torch_cuda, ctx, OQ, name):
+    """The TFHE bootstrap on a prime modulus, every layout, bit for bit equal
+    to the oracle; outputs decrypt to the negacyclic function."""
+    torch = torch_cuda
+    ps = S.Q_PARAM_SETS[name]
+    kr = S.q_key_randomness(ps, 71)
+    K = OQ.QKeys(ps, kr)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    f_half = np.array([(3 * m + 1) % ps.t for m in range(ps.t // 2)])
+    polys = np.stack([OQ.tfhe_test_polynomial(ps, f_half),
+                      S.q_tfhe_polynomials(ps, 72, 1)[0]])
+    assert [ctx.tfhe_poly_setup(sid, p) for p in polys] == [0, 1]
+    m = np.concatenate([np.arange(ps.t), np.arange(ps.t), [1]])
+    ids = np.concatenate([np.zeros(ps.t), np.ones(ps.t), [0]]).astype(np.int32)
+    mr = S.q_message_randomness(ps, 73, len(m), m=m)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    ref = OQ.tfhe_batch(ps, K, polys, ids, cts, threads=8)
+    for v in range(ctx.variant_info(sid)[1]):
+        ctx.set_variant(sid, v)
+        ct_d = F.to_device_words(ps, cts)
+        out_d = torch.empty_like(ct_d)
+        ctx.tfhe_bootstrap(sid, ct_d, torch.tensor(ids, device="cuda"), out_d)
+        ctx.sync()
+        out = F.to_host_words(ps, out_d).astype(np.uint64)
+        assert np.array_equal(out, ref), f"variant {v}"
+    want = [int(f_half[x]) if x < ps.t // 2 else (-int(f_half[x - ps.t // 2])) % ps.t for x in m[:ps.t]]
+    assert [OQ.decrypt(ps, kr.s, o) for o in ref[:ps.t]] == want
+
+
+def test_fdfb_on_q4_matches_the_oracle(F, torch_cuda, ctx, OQ):
+    """The full-domain bootstrap's mod-Q arithmetic at k = 32 (noiseless, see
+    the oracle pin), every layout bit for bit equal to the oracle."""
+    ps = dataclasses.replace(S.Q_PARAM_SETS["QT"], sigma_lwe=0.0, sigma_glwe=0.0, sigma_in=0.0)
+    kr = S.q_key_randomness(ps, 74)
+    K = OQ.QKeys(ps, kr)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, K.bsk, K.pk, K.ksk)
+    f = np.array([3, 0, 2, 1])
+    ctx.lut_setup(sid, f)
+    rot = OQ.rotation_polys(ps, [f])
+    m = np.tile(np.arange(ps.t), 3)
+    mr = S.q_message_randomness(ps, 75, len(m), m=m)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    ids = np.zeros(len(m), np.int32)
+    refs = [OQ.fdfb_bootstrap(ps, K, rot[0][0], rot[0][1], c, debug=True) for c in cts]
+    for v in range(ctx.variant_info(sid)[1]):
+        ctx.set_variant(sid, v)
+        out, dbg = run_q(F, torch_cuda, ctx, sid, ps, cts, ids)
+        for c, (o, d) in enumerate(refs):
+            for key in ("sgn", "cR", "accF", "cQ", "cKS"):
+                assert np.array_equal(dbg[key][c].reshape(d[key].shape), d[key]), f"{key}, variant {v}, ct {c}"
+            assert np.array_equal(out[c], o), f"variant {v}, ct {c}"
+    assert [OQ.decrypt(ps, kr.s, o) for o in out] == [int(f[x]) for x in m]
+
+
+def test_tfhe_80_2_full_size(F, torch_cuda, ctx, OQ):
+    """Table 1's TFHE:80:2 (n = 424, N = 1024, Q_4) at full size, keys
+    generated on the GPU: every output decrypts to the negacyclic function,
+    every layout returns the same bits."""
+    torch = torch_cuda
+    ps = S.Q_PARAM_SETS["TFHE-80-2"]
+    kr = S.q_key_randomness(ps, 76)
+    sid = ctx.register(ps)
+    ctx.keys_generate(sid, kr)
+    f_half = np.array([1, 3])
+    ctx.tfhe_poly_setup(sid, OQ.tfhe_test_polynomial(ps, f_half))
+    batch = 512
+    mr = S.q_message_randomness(ps, 77, batch)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    ct = torch.empty((batch, ps.n + 1), dtype=torch.int64, device="cuda")
+    ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                    torch.tensor(mr.m, device="cuda"), ct)
+    ids = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    outs = []
+    for v in range(ctx.variant_info(sid)[1]):
+        ctx.set_variant(sid, v)
+        out = torch.empty_like(ct)
+        ctx.tfhe_bootstrap(sid, ct, ids, out)
+        ctx.sync()
+        outs.append(F.to_host_words(ps, out).astype(np.uint64))
+    for v in range(1, len(outs)):
+        assert np.array_equal(outs[v], outs[0]), f"variant {v}"
+    m_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, s_d, F.to_device_words(ps, outs[0]), m_d)
+    ctx.sync()
+    want = [int(f_half[x]) if x < 2 else (-int(f_half[x - 2])) % 4 for x in mr.m]
+    assert list(m_d.cpu().numpy()) == want

@@ -335,3 +335,43 @@ def test_crt_addition_wraps_before_bootstrapping():
                      for i in range(len(pairs))], dtype=np.uint64)
     out = OQ.fdfb_batch(ps, K, rot, np.zeros(len(pairs), np.int32), sums, threads=oracle.max_threads())
     assert [OQ.decrypt(ps, kr.s, o) for o in out] == [(a + b) % 7 for a, b in pairs]
+
+
+# ------------------------------- TFHE bootstrap, Q_4 (k = 32) ---------------
+
+@pytest.mark.parametrize("name", ["QZ", "QT"])
+def test_tfhe_bootstrap_decrypts_the_negacyclic_function(name):
+    """Figure "TFHE Bootstrapping" on a prime modulus: with the test
+    polynomial of f_half, m in [0, t/2) decrypts to f_half[m] and m + t/2 to
+    -f_half[m] mod t, for every m."""
+    ps = S.Q_PARAM_SETS[name]
+    kr = S.q_key_randomness(ps, 61)
+    K = OQ.QKeys(ps, kr)
+    f_half = np.array([(3 * m + 1) % ps.t for m in range(ps.t // 2)])
+    poly = OQ.tfhe_test_polynomial(ps, f_half)
+    mr = S.q_message_randomness(ps, 62, ps.t, m=np.arange(ps.t))
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    out = OQ.tfhe_batch(ps, K, poly[None, :], np.zeros(ps.t, np.int32), cts, threads=oracle.max_threads())
+    want = [int(f_half[m]) if m < ps.t // 2 else (-int(f_half[m - ps.t // 2])) % ps.t for m in range(ps.t)]
+    assert [OQ.decrypt(ps, kr.s, o) for o in out] == want
+    # one rotation: coefficient 0 of the key-switched sample before ModSwitch
+    # is Delta_Q f within the key switch's noise, so the output is exactly the
+    # ModSwitch of a value near Delta_Q f (checked through decryption above)
+
+
+def test_fdfb_on_q4_every_message():
+    """The full-domain bootstrap's arithmetic on Q_4 = 2^32 - 139263 (k = 32),
+    noiseless: with Delta_Q / 2 ~ 2^29 the literal PubMux over l_boot digits
+    of p in Z_Q multiplies the packed samples' noise by digits up to 2^11
+    (about 2^33 at these gadgets), which is why Table 1 uses Q_4 only for the
+    TFHE bootstrap."""
+    import dataclasses
+    ps = dataclasses.replace(S.Q_PARAM_SETS["QT"], sigma_lwe=0.0, sigma_glwe=0.0, sigma_in=0.0)
+    kr = S.q_key_randomness(ps, 63)
+    K = OQ.QKeys(ps, kr)
+    f = np.array([3, 0, 2, 1])
+    rot = OQ.rotation_polys(ps, [f])
+    mr = S.q_message_randomness(ps, 64, 2 * ps.t, m=np.tile(np.arange(ps.t), 2))
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    out = OQ.fdfb_batch(ps, K, rot, np.zeros(len(cts), np.int32), cts, threads=oracle.max_threads())
+    assert [OQ.decrypt(ps, kr.s, o) for o in out] == [int(f[m]) for m in mr.m]
