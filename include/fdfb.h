@@ -309,7 +309,9 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
 
 /* LWE key switching with the installed ksK (figure "Key switching algorithm
  * and its setup"): ct_in device [batch][N+1] words under s_F, ct_out device
- * [batch][n+1] words under s (prime-modulus sets: both mod Q). */
+ * [batch][n+1] words under s (prime-modulus sets: both mod Q; there the call
+ * allocates a temporary buffer for the exact half sums and synchronises the
+ * stream before returning). */
 int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, void* ct_out,
                    void* cuda_stream);
 
