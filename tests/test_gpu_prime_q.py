@@ -381,3 +381,63 @@ def test_tfhe_80_2_full_size(F, torch_cuda, ctx, OQ):
     ctx.sync()
     want = [int(f_half[x]) if x < 2 else (-int(f_half[x - 2])) % 4 for x in mr.m]
     assert list(m_d.cpu().numpy()) == want
+
+
+def test_fdfb_100_6_and_noalloc(F, torch_cuda, ctx, OQ):
+    """FDFB:100:6 (n = 1050, B_ks = 2: 62 key-switch digits per word) decrypts
+    correctly, and the no-allocation entry point returns the same bits as
+    fdfb_bootstrap on a prime-modulus set."""
+    torch = torch_cuda
+    ps = S.Q_PARAM_SETS["FDFB-100-6"]
+    kr = S.q_key_randomness(ps, 81)
+    sid = ctx.register(ps)
+    ctx.keys_generate(sid, kr)
+    f = S.q_lut_tables(ps, 81, 1)[0]
+    ctx.lut_setup(sid, f)
+    batch = 64
+    mr = S.q_message_randomness(ps, 82, batch)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    ct = torch.empty((batch, ps.n + 1), dtype=torch.int64, device="cuda")
+    ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                    torch.tensor(mr.m, device="cuda"), ct)
+    ids = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    out = torch.empty_like(ct)
+    ctx.bootstrap(sid, ct, ids, out)
+    m_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, s_d, out, m_d)
+    ctx.sync()
+    assert list(m_d.cpu().numpy()) == [int(f[m]) for m in mr.m]
+    cap = ctx.noalloc_max_batch(sid)
+    assert cap >= 1
+    k = min(cap, 8)
+    out2 = torch.empty_like(ct[:k])
+    ctx.bootstrap_noalloc(sid, ct[:k].contiguous(), ids[:k].contiguous(), out2)
+    ctx.sync()
+    assert torch.equal(out2, out[:k])
+
+
+def test_tfhe_100_7_full_size(F, torch_cuda, ctx, OQ):
+    """Table 1's TFHE:100:7 (n = 1500, N = 4096, Q_3 = 2^48 - 163839, 16-bit
+    blind-rotation digits, 48 key-switch digits): outputs decrypt to the
+    negacyclic function."""
+    torch = torch_cuda
+    ps = S.Q_PARAM_SETS["TFHE-100-7"]
+    kr = S.q_key_randomness(ps, 83)
+    sid = ctx.register(ps)
+    ctx.keys_generate(sid, kr)
+    f_half = np.array([(5 * m + 2) % ps.t for m in range(ps.t // 2)])
+    ctx.tfhe_poly_setup(sid, OQ.tfhe_test_polynomial(ps, f_half))
+    batch = 64
+    mr = S.q_message_randomness(ps, 84, batch)
+    s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+    ct = torch.empty((batch, ps.n + 1), dtype=torch.int64, device="cuda")
+    ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                    torch.tensor(mr.m, device="cuda"), ct)
+    out = torch.empty_like(ct)
+    ctx.tfhe_bootstrap(sid, ct, torch.zeros(batch, dtype=torch.int32, device="cuda"), out)
+    m_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    ctx.lwe_decrypt(sid, s_d, out, m_d)
+    ctx.sync()
+    h = ps.t // 2
+    want = [int(f_half[x]) if x < h else (-int(f_half[x - h])) % ps.t for x in mr.m]
+    assert list(m_d.cpu().numpy()) == want
