@@ -441,3 +441,37 @@ def test_tfhe_100_7_full_size(F, torch_cuda, ctx, OQ):
     h = ps.t // 2
     want = [int(f_half[x]) if x < h else (-int(f_half[x - h])) % ps.t for x in mr.m]
     assert list(m_d.cpu().numpy()) == want
+
+
+def test_fdfb_100_7_and_tfhe_100_2(F, torch_cuda, ctx, OQ):
+    """The remaining Table 1 columns with N <= 4096: FDFB:100:7 (n = 1100,
+    N = 4096, Q_2, 63 key-switch digits) decrypts to f(m); TFHE:100:2 (n =
+    525, N = 1024, Q_4) decrypts to the negacyclic function."""
+    torch = torch_cuda
+    for name in ("FDFB-100-7", "TFHE-100-2"):
+        ps = S.Q_PARAM_SETS[name]
+        kr = S.q_key_randomness(ps, 85)
+        sid = ctx.register(ps)
+        ctx.keys_generate(sid, kr)
+        batch = 32
+        mr = S.q_message_randomness(ps, 86, batch)
+        s_d = torch.tensor(kr.s.astype(np.uint8), device="cuda")
+        ct = torch.empty((batch, ps.n + 1), dtype=torch.int64, device="cuda")
+        ctx.lwe_encrypt(sid, s_d, F.to_device_words(ps, mr.a), torch.tensor(mr.e, device="cuda"),
+                        torch.tensor(mr.m, device="cuda"), ct)
+        ids = torch.zeros(batch, dtype=torch.int32, device="cuda")
+        out = torch.empty_like(ct)
+        if name.startswith("FDFB"):
+            f = S.q_lut_tables(ps, 85, 1)[0]
+            ctx.lut_setup(sid, f)
+            ctx.bootstrap(sid, ct, ids, out)
+            want = [int(f[m]) for m in mr.m]
+        else:
+            f_half = np.array([1, 2])
+            ctx.tfhe_poly_setup(sid, OQ.tfhe_test_polynomial(ps, f_half))
+            ctx.tfhe_bootstrap(sid, ct, ids, out)
+            want = [int(f_half[x]) if x < 2 else (-int(f_half[x - 2])) % 4 for x in mr.m]
+        m_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+        ctx.lwe_decrypt(sid, s_d, out, m_d)
+        ctx.sync()
+        assert list(m_d.cpu().numpy()) == want, name
