@@ -132,7 +132,8 @@ int fdfb_create(fdfb_ctx** out, int device);
 int fdfb_destroy(fdfb_ctx* ctx);
 
 /* Registers a parameter set; *set_id_out receives its id.  Fails with
- * FDFB_EINVAL for unsupported shapes: N not in {256, 512, 1024, 2048, 4096},
+ * FDFB_EINVAL for unsupported shapes (prime-modulus sets: the rules given
+ * with fdfb_params.Q, lg <= 7): N not in {256, 512, 1024, 2048, 4096},
  * n > 4096, lg > 4, signed_digits > 1, or a negacyclic product whose exact
  * value could exceed what the 30-bit primes lift exactly (2l N (B-1) q/2 for
  * the blind rotation, N (t-1) q for PubMux).  Registration also builds the
