@@ -375,3 +375,48 @@ def test_fdfb_on_q4_every_message():
     cts = OQ.encrypt_messages(ps, kr.s, mr)
     out = OQ.fdfb_batch(ps, K, rot, np.zeros(len(cts), np.int32), cts, threads=oracle.max_threads())
     assert [OQ.decrypt(ps, kr.s, o) for o in out] == [int(f[m]) for m in mr.m]
+
+
+def test_external_product_noise_matches_its_expectation(keys):
+    """The external product's noise (Definition "External Product", exact
+    decomposition) in closed form, conditional on the key: extProd(RGSW(s_i),
+    d) has phase s_i mu + sum_r D_r * e_r with e_r row r's key error and D_r
+    the digit polynomials of a uniform d.  Digits are independent with mean
+    mu_r and variance v_r ((B-1)/2 and (B^2-1)/12 for the l-1 full digits;
+    the exact distribution of floor(x / B^(l-1)) for the top digit of x
+    uniform mod Q), so coefficient j's mean square is
+        sum_r v_r ||e_r||^2 + (sum_r mu_r S_r(j))^2,
+    S_r(j) = sum_{m <= j} e_r[m] - sum_{m > j} e_r[m] (the negacyclic signs).
+    Averaged over 64 random d and all j, the oracle must be within 6 %."""
+    kr, K = keys
+    N, l = PS.N, PS.lg
+    B = 1 << PS.log2Bg
+    G = B ** (l - 1)
+    T = -(-Q // G)
+    probs = np.array([(min(Q, (v + 1) * G) - v * G) / Q for v in range(T)])
+    vals = np.arange(T, dtype=np.float64)
+    mu_T = float(probs @ vals)
+    var_T = float(probs @ vals ** 2) - mu_T ** 2
+    mus = [(B - 1) / 2] * (l - 1) + [mu_T]
+    vrs = [(B * B - 1) / 12] * (l - 1) + [var_T]
+    i = int(np.flatnonzero(kr.s)[0])
+    want_var = 0.0
+    mean_part = np.zeros(N)
+    for r in range(2 * l):
+        e = kr.bsk_e[i, r].astype(np.float64)
+        jd = r % l
+        want_var += vrs[jd] * float(e @ e)
+        pre = np.cumsum(e)
+        S_r = pre - (pre[-1] - pre)          # sum_{m<=j} e - sum_{m>j} e
+        mean_part += mus[jd] * S_r
+    want = want_var + float(np.mean(mean_part ** 2))
+    rng = np.random.default_rng(92)
+    acc = []
+    for _ in range(64):
+        mu = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+        a = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+        d = OQ.rlwe_encrypt(Q, kr.sk, a, np.zeros(N, np.int64), mu)
+        ph = OQ.rlwe_phase(Q, kr.sk, OQ.extprod(PS, K.bsk[i], d))
+        acc.append(np.array([centred(int(p) - int(m)) for p, m in zip(ph, mu)], dtype=np.float64))
+    got = float(np.mean(np.concatenate(acc) ** 2))
+    assert 0.94 * want <= got <= 1.06 * want, (got, want)
