@@ -57,11 +57,12 @@ enum {
 typedef struct fdfb_ctx fdfb_ctx;
 
 /* One parameter set (paper notation, Table 1).  k must be 1; log2q is 32 or
- * 64 (q = Q: the final ModSwitch Q -> q of the Bootstrap figure is the
- * identity).  t is a power of two with 2 <= t <= N.  log2Lboot / lboot
- * describe the PubMux decomposition of Bootstrap step "l_boot"; the library
- * implements L_boot = t, l_boot = 1 (log2Lboot = log2 t, lboot = 1): one sign
- * blind rotation, and the PubMux selector (p_1 - p_0) mod t is one digit. */
+ * 64.  With Q = 0 (power-of-two sets) q = Q = 2^log2q: the final ModSwitch
+ * Q -> q of the Bootstrap figure is the identity, t is a power of two with
+ * 2 <= t <= N, and log2Lboot / lboot, which describe the PubMux
+ * decomposition of Bootstrap step "l_boot", must be log2 t and 1 (L_boot =
+ * t, l_boot = 1: one sign blind rotation, the PubMux selector (p_1 - p_0)
+ * mod t one digit).  With Q != 0 the rules of the Q field below apply. */
 typedef struct {
   uint32_t n, N, k, log2q, t;
   uint32_t log2Bg, lg;     /* bootstrapping-key gadget: base 2^log2Bg, lg digits (lg <= 4) */

@@ -545,7 +545,8 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
     FD_CUDA(bv.ops->br(br, items, bv.br_smem, s));
   }
 
-  // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q).
+  // Step 14: KeySwitch with ksK (ModSwitch Q -> q is the identity, q = Q;
+  // the prime-modulus sets take run_pipeline_q).
   {
     StageTimer tm(tctx, 4, s);
     FD_TRY(launch_keyswitch(ctx, st.w, cQ, items, (int)N, st.ksk.p, P.lks, P.log2Bks,

@@ -22,7 +22,8 @@ Parameter sets follow the paper's notation (Table 1): n (LWE dimension),
 N (ring degree), q = 2^w (q = Q here), gadget bases B_g = 2^log2Bg with
 l_g digits for the bootstrapping key, B_ks/l_ks for the LWE key-switching
 key, B_pk/l_pk for the LWE-to-RLWE packing key, plaintext modulus t and the
-noise standard deviations.
+noise standard deviations.  QParamSet holds the paper's own sets, with a
+prime RLWE modulus Q and the LWE side mod q = 2N.
 """
 from __future__ import annotations
 
