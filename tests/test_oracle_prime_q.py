@@ -420,3 +420,59 @@ def test_external_product_noise_matches_its_expectation(keys):
         acc.append(np.array([centred(int(p) - int(m)) for p, m in zip(ph, mu)], dtype=np.float64))
     got = float(np.mean(np.concatenate(acc) ** 2))
     assert 0.94 * want <= got <= 1.06 * want, (got, want)
+
+
+def _noiseless(ps):
+    import dataclasses
+    return dataclasses.replace(ps, sigma_lwe=0.0, sigma_glwe=0.0, sigma_in=0.0)
+
+
+def test_tfhe_noiseless_phase_is_the_rotated_coefficient():
+    """Figure "TFHE Bootstrapping" at sigma = 0 with the exact decomposition:
+    the extracted sample's phase (under s_F) is exactly coefficient 0 of
+    poly X^{b_N - <a_N, s>}, the key switch keeps it exactly (under s), and
+    the bootstrap's output is the ModSwitch of that sample."""
+    ps = _noiseless(PS)
+    kr = S.q_key_randomness(ps, 93)
+    K = OQ.QKeys(ps, kr)
+    rng = np.random.default_rng(94)
+    N, n = ps.N, ps.n
+    for _ in range(3):
+        poly = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+        ct = rng.integers(0, 2 * N, n + 1).astype(np.uint64)
+        acc = np.zeros((2, N), dtype=np.uint64)
+        acc[0] = OQ.poly_mul_xk(Q, poly, int(ct[0]))
+        acc = OQ.blind_rotate(ps, K.bsk, acc, ct)
+        cQ = OQ.sample_extract(Q, acc)
+        k = int(ct[0]) - sum(int(a) * int(s) for a, s in zip(ct[1:], kr.s))
+        want = int(OQ.poly_mul_xk(Q, poly, k)[0])
+        assert OQ.lwe_phase_q(Q, kr.sk, cQ) == want
+        cks = OQ.keyswitch(Q, ps.log2Bks, ps.lks, K.ksk, cQ)
+        assert OQ.lwe_phase_q(Q, kr.s.astype(np.uint64), cks) == want
+        out = OQ.tfhe_bootstrap(ps, K, poly, ct)
+        assert np.array_equal(out, OQ.modswitch(Q, ps.logq, cks))
+
+
+def test_fdfb_noiseless_phase_within_the_rounding_of_delta():
+    """The full-domain bootstrap at sigma = 0 (inputs noiseless too): the key
+    switched sample's phase is Delta_Q f(m) up to the mismatch of G24 -- the
+    sign samples carry 2 round(Q/2t) where PubMux uses round(Q/t), which
+    differ by at most 1, times p_1 - p_0 (|.| < 2t) -- for every m and two
+    tables; where the two roundings agree (Q_1, t = 8) the phase is exactly
+    Delta_Q f(m)."""
+    ps = _noiseless(PS)
+    kr = S.q_key_randomness(ps, 95)
+    K = OQ.QKeys(ps, kr)
+    D = OQ.delta(Q, ps.t)
+    for f in S.q_lut_tables(ps, 95, 2):
+        rot = OQ.rotation_polys(ps, [f])[0]
+        mr = S.q_message_randomness(ps, 96, ps.t, m=np.arange(ps.t))
+        for m, ct in zip(range(ps.t), OQ.encrypt_messages(ps, kr.s, mr)):
+            out, dbg = OQ.fdfb_bootstrap(ps, K, rot[0], rot[1], ct, debug=True)
+            ph = OQ.lwe_phase_q(Q, kr.s.astype(np.uint64), dbg["cKS"])
+            dev = centred(ph - D * int(f[m]))
+            if 2 * OQ.delta_half(Q, ps.t) == D:
+                assert dev == 0      # Q_1 with t = 8: the two roundings agree
+            else:
+                assert abs(dev) <= 2 * ps.t
+            assert OQ.decrypt(ps, kr.s, out) == int(f[m])
