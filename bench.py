@@ -72,7 +72,12 @@ PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7"
 KERNEL_TRAFFIC = {
     ("B", 7, 1024): 86.26e6,    # tfhe_scale workload
     ("D", 6, 1000): 3.19754e9,  # n2048 workload
+    # paper_80_6: the sign rotation (6000 items) scaled from a 384-item capture
+    # (1.2074 GB): the 413 MB key streams from DRAM once per wave of 152 items
+    ("FDFB-80-6", 3, 1000): 1.2074e9 * 6000 / 384,
 }
+KERNEL_TRAFFIC_SCALED = {("FDFB-80-6", 3, 1000): "sign-rotation launch (batch x l_boot = 6000 items), "
+                                                  "scaled by items from an ncu capture of 384 items"}
 
 
 def br_algorithmic_slots(ps, batch: int) -> float:
@@ -692,6 +697,8 @@ def main():
             traffic = KERNEL_TRAFFIC[key]
             traffic_src = ("dram bytes per unchunked blind-rotation launch over the batch, "
                            f"ncu capture of set {key[0]} variant {key[1]}, {key[2]} ciphertexts")
+            if key in KERNEL_TRAFFIC_SCALED:
+                traffic_src = "dram bytes per " + KERNEL_TRAFFIC_SCALED[key] + f", set {key[0]} variant {key[1]}"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
