@@ -76,6 +76,31 @@ int main() {
       bad += got != X;
     }
   }
+  // NTT constants of both prime families (fdfb_host.hpp make_prime_set):
+  // p = 1 mod 2N, psi^N = -1 (psi = the twiddle at bit-reversed index 1),
+  // Shoup companions floor(w 2^32 / p), -p^-1 mod 2^32, N^-1 2^32 mod p,
+  // Garner's p_i^-1 mod p_j and the prefix products
+  for (int family = 0; family <= 1; ++family)
+    for (int L = 8; L <= 12; ++L) {
+      const uint32_t N = 1u << L;
+      const int EL = L == 8 ? 3 : 4;
+      PrimeSet S{};
+      std::vector<uint2> fwd, inv;
+      host::make_prime_set(family ? 2 : 3, L, EL, S, fwd, inv, family);
+      for (int i = 0; i < S.P; ++i) {
+        const uint64_t p = S.p[i];
+        bad += (p - 1) % (2 * N) != 0;
+        bad += fwd[(size_t)i * N].x != 1;
+        const uint64_t w1 = fwd[(size_t)i * N + 1].x;  // psi^(N/2)
+        bad += host::mulmod(w1, w1, p) != p - 1;     // psi^N = -1
+        bad += host::mulmod(w1, inv[(size_t)i * N + 1].x, p) != 1;
+        bad += fwd[(size_t)i * N + 1].y != (uint32_t)((w1 << 32) / p);
+        bad += (uint32_t)(S.pneg[i] * (uint32_t)p) != 0xffffffffu;
+        bad += host::mulmod(S.ninv_m[i], N, p) != ((uint64_t)1 << 32) % p;
+        for (int j = i + 1; j < S.P; ++j) bad += host::mulmod(S.gc[i][j], p % S.p[j], S.p[j]) != 1;
+        bad += S.M[i + 1] != S.M[i] * p;
+      }
+    }
   if (bad) {
     printf("%ld mismatches\n", bad);
     return 1;

@@ -1,7 +1,9 @@
 """Host check of the CUDA library's modular helpers for the prime-modulus
 sets (csrc/fdfb_core.cuh compiled as plain C++ with g++, no GPU): the lift
 reduction and its fold counts, and Garner's exact lift, against 128-bit
-integer division and the integer the residues came from."""
+integer division and the integer the residues came from; and the NTT
+constants of both prime families (roots of unity, Shoup and Montgomery
+companions, Garner constants) for N = 2^8 .. 2^12."""
 import os
 import subprocess
 
