@@ -278,12 +278,30 @@ def keygen_pk_row(ps, kr, i: int, j: int) -> np.ndarray:
     return out.reshape(2, ps.N)
 
 
+def delta(w: int, t: int) -> int:
+    """Delta_{q,t} = round(q / t) (Section 2, notation) for q = 2^w and a
+    power-of-two t, where the quotient is exact."""
+    return (1 << w) // t
+
+
+def t_out(ps) -> int:
+    """Output plaintext modulus t' of f: Z_t -> Z_t' (Section 1.1, footnote);
+    a set with t_out = 0 maps into Z_t."""
+    return ps.t_out or ps.t
+
+
+def delta_out(ps) -> int:
+    """Delta_{q,t'}: the scale of the bootstrap's outputs."""
+    return delta(ps.w, t_out(ps))
+
+
 def encrypt_messages(ps, s, mr) -> np.ndarray:
     """Fresh LWE ciphertexts [count][n+1] of Delta*m with the given randomness."""
     count = len(mr.m)
     out = np.zeros((count, ps.n + 1), dtype=np.uint64)
+    D = delta(ps.w, ps.t)
     for i in range(count):
-        out[i] = lwe_encrypt(ps.w, s, mr.a[i], int(mr.e[i]), (ps.delta * int(mr.m[i])) % (1 << ps.w))
+        out[i] = lwe_encrypt(ps.w, s, mr.a[i], int(mr.e[i]), (D * int(mr.m[i])) % (1 << ps.w))
     return out
 
 
@@ -446,9 +464,10 @@ def tfhe_test_polynomial(ps, f_half) -> np.ndarray:
     mask = (1 << ps.w) - 1
     poly = np.zeros(N, dtype=np.uint64)
     step = 2 * N // t
+    D = delta(ps.w, t)
     for y in range(N):
         m = (y + step // 2) // step               # nearest message, 0 .. t/2
-        v = ps.delta * int(f_half[m]) if m < t // 2 else -ps.delta * int(f_half[0])
+        v = D * int(f_half[m]) if m < t // 2 else -D * int(f_half[0])
         if y == 0:
             poly[0] = v & mask
         else:

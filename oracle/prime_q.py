@@ -114,11 +114,27 @@ class QKeys:
         lib().orq_keygen_ksk(C.byref(P), _p(self.sk), _p(self.s), _p(ka), _p(ke), _p(self.ksk))
 
 
+def exact_digits(Q: int, log2B: int) -> int:
+    """Digits of the exact decomposition of Z_Q in base B = 2^log2B
+    (Definition "Decomposition": l = ceil(log_B Q)); for 2^(k-1) < Q < 2^k
+    that is ceil(k / log2B).  Also l_boot = ceil(log_{L_boot} Q) (Bootstrap
+    figure, step "for i in [l_boot]")."""
+    k = int(Q).bit_length()
+    return -(-k // log2B)
+
+
+def delta_in(ps) -> int:
+    """Delta_{q,t} = round(q / t), round half up, on the LWE side q = 2N
+    (Section 2's rounding; G29's reading for t not dividing 2N)."""
+    return (ps.q + ps.t // 2) // ps.t
+
+
 def encrypt_messages(ps, s, mr) -> np.ndarray:
     """Fresh LWE ciphertexts mod q = 2N of Delta_q m, [count][n+1] uint64."""
     out = np.zeros((len(mr.m), ps.n + 1), dtype=np.uint64)
+    D = delta_in(ps)
     for i in range(len(mr.m)):
-        out[i] = lwe_encrypt(ps.logq, s, mr.a[i], int(mr.e[i]), (ps.delta_q * int(mr.m[i])) % ps.q)
+        out[i] = lwe_encrypt(ps.logq, s, mr.a[i], int(mr.e[i]), (D * int(mr.m[i])) % ps.q)
     return out
 
 
@@ -246,7 +262,7 @@ def tfhe_test_polynomial(ps, f_half) -> np.ndarray:
     N, t, Q = ps.N, ps.t, ps.Q
     D = delta(Q, t)
     poly = np.zeros(N, dtype=np.uint64)
-    step = ps.delta_q
+    step = delta_in(ps)
     for y in range(N):
         m = (y + step // 2) // step
         v = D * int(f_half[m]) if m < t // 2 else -D * int(f_half[0])

@@ -66,19 +66,6 @@ class ParamSet:
     def word_dtype(self):
         return np.uint32 if self.w == 32 else np.uint64
 
-    @property
-    def delta(self) -> int:
-        return (1 << self.w) // self.t
-
-    @property
-    def tout(self) -> int:
-        """Output plaintext modulus t' (f: Z_t -> Z_t')."""
-        return self.t_out or self.t
-
-    @property
-    def delta_out(self) -> int:
-        return (1 << self.w) // self.tout
-
 
 # Sets A-C are the parameters of the toy, TFHE-scale and large-plaintext
 # workloads.  Set D (N = 2048), the packing-key gadgets and the noise levels of
@@ -338,16 +325,14 @@ Q3 = (1 << 48) - 163839
 Q4 = (1 << 32) - 139263
 
 
-def _ceil_div(a: int, b: int) -> int:
-    return -(-a // b)
-
-
 @dataclasses.dataclass(frozen=True)
 class QParamSet:
     """A parameter set of Table 1: RLWE side modulo a prime Q, LWE side
-    modulo q = 2N, exact gadget decompositions with l = ceil(log_B Q)
-    digits, l_boot = ceil(log_{L_boot} Q) sign rotations, uniform RLWE key
-    in Z_Q^N, binary LWE key.
+    modulo q = 2N, exact gadget decompositions, uniform RLWE key in Z_Q^N,
+    binary LWE key.  The digit counts lg, lks, lpk (gadget digits) and lboot
+    (sign rotations) are stated with each set; the oracle's tests check them
+    against the exact decomposition's count and the library re-checks them at
+    registration.
 
     sigma_lwe  : the key-switching key (LWE samples mod Q)
     sigma_glwe : the bootstrapping and packing keys (RLWE samples mod Q)
@@ -359,9 +344,13 @@ class QParamSet:
     Q: int
     t: int
     log2Bg: int
+    lg: int
     log2Bks: int
+    lks: int
     log2Bpk: int
+    lpk: int
     log2Lboot: int
+    lboot: int
     sigma_lwe: float
     sigma_glwe: float
     sigma_in: float = 3.2
@@ -382,53 +371,35 @@ class QParamSet:
     def q(self) -> int:
         return 2 * self.N
 
-    @property
-    def lg(self) -> int:
-        return _ceil_div(self.k, self.log2Bg)
-
-    @property
-    def lks(self) -> int:
-        return _ceil_div(self.k, self.log2Bks)
-
-    @property
-    def lpk(self) -> int:
-        return _ceil_div(self.k, self.log2Bpk)
-
-    @property
-    def lboot(self) -> int:
-        return _ceil_div(self.k, self.log2Lboot)
-
-    @property
-    def delta_q(self) -> int:    # Delta_{q,t} = round(q / t) of the input and output ciphertexts
-        return (self.q + self.t // 2) // self.t
-
 
 # Table 1 columns with N <= 4096 (ring degree 2^13 needs more shared memory
 # per ciphertext than one SM has), and QZ, a small set of the same shape for
 # the exhaustive checks.  t is the largest plaintext modulus the paper's
 # correctness table gives a negligible error probability for.
 Q_PARAM_SETS: Dict[str, QParamSet] = {
-    "FDFB-80-6": QParamSet("FDFB-80-6", n=700, N=2048, Q=Q1, t=64, log2Bg=11, log2Bks=6,
-                           log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
-    "FDFB-100-6": QParamSet("FDFB-100-6", n=1050, N=2048, Q=Q1, t=64, log2Bg=11, log2Bks=1,
-                            log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
-    "FDFB-80-7": QParamSet("FDFB-80-7", n=700, N=4096, Q=Q2, t=128, log2Bg=9, log2Bks=4,
-                           log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 39, sigma_glwe=3.2),
-    "FDFB-100-7": QParamSet("FDFB-100-7", n=1100, N=4096, Q=Q2, t=128, log2Bg=9, log2Bks=1,
-                            log2Bpk=13, log2Lboot=11, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
-    "QZ": QParamSet("QZ", n=24, N=256, Q=Q1, t=8, log2Bg=11, log2Bks=6, log2Bpk=13, log2Lboot=11,
+    "FDFB-80-6": QParamSet("FDFB-80-6", n=700, N=2048, Q=Q1, t=64, log2Bg=11, lg=6, log2Bks=6, lks=11,
+                           log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
+    "FDFB-100-6": QParamSet("FDFB-100-6", n=1050, N=2048, Q=Q1, t=64, log2Bg=11, lg=6, log2Bks=1, lks=62,
+                            log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
+    "FDFB-80-7": QParamSet("FDFB-80-7", n=700, N=4096, Q=Q2, t=128, log2Bg=9, lg=7, log2Bks=4, lks=16,
+                           log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 39, sigma_glwe=3.2),
+    "FDFB-100-7": QParamSet("FDFB-100-7", n=1100, N=4096, Q=Q2, t=128, log2Bg=9, lg=7, log2Bks=1, lks=63,
+                            log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
+    "QZ": QParamSet("QZ", n=24, N=256, Q=Q1, t=8, log2Bg=11, lg=6, log2Bks=6, lks=11, log2Bpk=13, lpk=5,
+                    log2Lboot=11, lboot=6,
                     sigma_lwe=2.0 ** 38, sigma_glwe=3.2),
     # Table 1's TFHE columns (the paper's comparison point: one blind
     # rotation of a pre-rotation polynomial, negacyclic functions); they give
     # no packing key or L_boot, so the FDFB-only gadgets take B_RGSW.
-    "TFHE-80-2": QParamSet("TFHE-80-2", n=424, N=1024, Q=Q4, t=4, log2Bg=11, log2Bks=4,
-                           log2Bpk=11, log2Lboot=11, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
-    "TFHE-100-2": QParamSet("TFHE-100-2", n=525, N=1024, Q=Q4, t=4, log2Bg=11, log2Bks=4,
-                            log2Bpk=11, log2Lboot=11, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
-    "TFHE-100-7": QParamSet("TFHE-100-7", n=1500, N=4096, Q=Q3, t=128, log2Bg=16, log2Bks=1,
-                            log2Bpk=16, log2Lboot=16, sigma_lwe=2.0 ** 18, sigma_glwe=3.2),
+    "TFHE-80-2": QParamSet("TFHE-80-2", n=424, N=1024, Q=Q4, t=4, log2Bg=11, lg=3, log2Bks=4, lks=8,
+                           log2Bpk=11, lpk=3, log2Lboot=11, lboot=3, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
+    "TFHE-100-2": QParamSet("TFHE-100-2", n=525, N=1024, Q=Q4, t=4, log2Bg=11, lg=3, log2Bks=4, lks=8,
+                            log2Bpk=11, lpk=3, log2Lboot=11, lboot=3, sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
+    "TFHE-100-7": QParamSet("TFHE-100-7", n=1500, N=4096, Q=Q3, t=128, log2Bg=16, lg=3, log2Bks=1, lks=48,
+                            log2Bpk=16, lpk=3, log2Lboot=16, lboot=3, sigma_lwe=2.0 ** 18, sigma_glwe=3.2),
     # small set on Q_4 (k = 32) for the exhaustive checks
-    "QT": QParamSet("QT", n=24, N=256, Q=Q4, t=4, log2Bg=11, log2Bks=4, log2Bpk=11, log2Lboot=11,
+    "QT": QParamSet("QT", n=24, N=256, Q=Q4, t=4, log2Bg=11, lg=3, log2Bks=4, lks=8, log2Bpk=11, lpk=3,
+                    log2Lboot=11, lboot=3,
                     sigma_lwe=2.0 ** 16, sigma_glwe=3.2),
 }
 

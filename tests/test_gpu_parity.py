@@ -152,7 +152,7 @@ def test_fdfb_noiseless_all_functions(F, torch_cuda, ctx, oracle):
     out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
     check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, range(0, len(ms), 7))
     for c in range(len(ms)):
-        assert oracle.lwe_phase(ps.w, K.s, out[c]) == ps.delta * int(fs[ids[c], ms[c]])
+        assert oracle.lwe_phase(ps.w, K.s, out[c]) == oracle.delta(ps.w, ps.t) * int(fs[ids[c], ms[c]])
 
 
 def test_lut_polys_match_oracle(ctx, oracle):
@@ -608,7 +608,7 @@ def test_degenerate_tables_and_t2(F, torch_cuda, ctx, oracle):
     out, dbg = run_gpu(F, torch_cuda, ctx, sid, ps, cts, ids)
     check_against_oracle(oracle, ps, K, rot, cts, ids, out, dbg, range(len(ms)))
     for c in range(len(ms)):
-        assert oracle.lwe_phase(ps.w, K.s, out[c]) == ps.delta * tables[ids[c]][ms[c]]
+        assert oracle.lwe_phase(ps.w, K.s, out[c]) == oracle.delta(ps.w, ps.t) * tables[ids[c]][ms[c]]
 
 
 def test_bootstrap_captured_in_cuda_graph(F, torch_cuda, ctx, oracle):

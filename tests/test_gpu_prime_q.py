@@ -158,7 +158,7 @@ def test_registration_rules(F, ctx):
     with pytest.raises(F.FDFBError):
         reg(dataclasses.replace(QZ, Q=(1 << 31) - 1))     # k = 31 < 32
     with pytest.raises(F.FDFBError):
-        reg(dataclasses.replace(QZ, log2Lboot=7))         # l_boot = 9 > 8
+        reg(dataclasses.replace(QZ, log2Lboot=7, lboot=9))  # l_boot = 9 > 8
     # a caller-given l that is not ceil(k / log2 B)
     from paper_2109_02731_gb300.fdfb import fdfb_params
     import ctypes as C

@@ -230,7 +230,7 @@ def test_keyswitch_noise_within_lemma(oracle):
     r = rng(4)
     errs = []
     for _ in range(60):
-        mu = int(r.integers(0, ps.t)) * ps.delta
+        mu = int(r.integers(0, ps.t)) * oracle.delta(ps.w, ps.t)
         ct = oracle.lwe_encrypt(ps.w, k.sk, rand_words(r, ps.w, ps.N), 0, mu)
         out = oracle.keyswitch(ps.w, ps.log2Bks, ps.lks, k.ksk, ct)
         e = (oracle.lwe_phase(ps.w, k.s, out) - mu) % (1 << ps.w)
@@ -471,7 +471,7 @@ def test_fdfb_noiseless_exhaustive(oracle):
     cts = oracle.encrypt_messages(ps, k.s, mr)
     outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
     for c in range(len(ms)):
-        want = (ps.delta * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        want = (oracle.delta(ps.w, ps.t) * int(fs[ids[c], ms[c]])) % (1 << ps.w)
         assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
 
 
@@ -493,7 +493,7 @@ def test_fdfb_signed_digits_noiseless(oracle):
     cts = oracle.encrypt_messages(ps, k.s, mr)
     outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
     for c in range(len(ms)):
-        want = (ps.delta * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        want = (oracle.delta(ps.w, ps.t) * int(fs[ids[c], ms[c]])) % (1 << ps.w)
         assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
 
 
@@ -520,7 +520,7 @@ def test_fdfb_other_output_modulus_noiseless(oracle, t_out):
     cts = oracle.encrypt_messages(ps, k.s, mr)
     outs = oracle.fdfb_batch(ps, k, rot, ids, cts)
     for c in range(len(ms)):
-        want = (ps.delta_out * int(fs[ids[c], ms[c]])) % (1 << ps.w)
+        want = (oracle.delta_out(ps) * int(fs[ids[c], ms[c]])) % (1 << ps.w)
         assert oracle.lwe_phase(ps.w, k.s, outs[c]) == want, (ids[c], ms[c])
 
 
@@ -544,7 +544,7 @@ def test_fdfb_multi_noiseless_exhaustive(oracle):
     assert outs.shape == (t, len(fs), ps.n + 1)
     for m in range(t):
         for i in range(len(fs)):
-            want = (ps.delta * int(fs[i, m])) % (1 << ps.w)
+            want = (oracle.delta(ps.w, ps.t) * int(fs[i, m])) % (1 << ps.w)
             assert oracle.lwe_phase(ps.w, k.s, outs[m, i]) == want, (m, i)
 
 
@@ -622,3 +622,66 @@ def test_fdfb_toy_decrypts(oracle):
     got = [oracle.lwe_decrypt(ps.w, ps.t, k.s, o) for o in outs]
     want = [int(fs[i][m]) for i, m in zip(ids, mr.m)]
     assert got == want
+
+
+# ------------------------------------------------------- LWE affine layer ---
+
+@pytest.mark.parametrize("w", [W32, W64])
+def test_lwe_affine_matches_big_integer_sum(oracle, w):
+    """The affine layer (Lemma 'Linear Homomorphism of GLWE samples'):
+    y[j][k] = sum_i W[j][i] x[i][k] mod 2^w, recomputed with Python's exact
+    integers.  Non-square weights (a transposed W cannot even be applied),
+    weights of both signs including the int32 extremes, and every LWE
+    component k, so a dropped sign, a swapped index or a truncated product
+    fails."""
+    r = rng(40 + w)
+    n_in, n_out, length = 7, 5, 11
+    W = r.integers(-8, 8, size=(n_out, n_in), dtype=np.int64)
+    W[0, 0], W[1, 2], W[4, 6] = -(1 << 31), (1 << 31) - 1, -1
+    x = rand_words(r, w, (n_in, length))
+    y = oracle.lwe_affine(w, W, x)
+    assert y.shape == (n_out, length)
+    for j in range(n_out):
+        for k in range(length):
+            want = sum(int(W[j, i]) * int(x[i, k]) for i in range(n_in)) % (1 << w)
+            assert int(y[j, k]) == want, (j, k)
+
+
+@pytest.mark.parametrize("name", ["A", "D"])
+def test_lwe_affine_is_homomorphic(oracle, name):
+    """The linear homomorphism itself: for noiseless LWE samples of Delta m_i
+    under one key, row j of the layer's output has phase exactly
+    Delta * sum_i W[j][i] m_i mod q, so it decrypts to sum_i W[j][i] m_i
+    mod t; with fresh noise it still decrypts to that sum mod t while the
+    accumulated noise sum_i W[j][i] e_i stays below Delta/2."""
+    ps = S.PARAM_SETS[name]
+    w, t, n = ps.w, ps.t, ps.n
+    D = oracle.delta(w, t)
+    r = rng(50)
+    s = r.integers(0, 2, size=n, dtype=np.uint8)
+    n_in, n_out = 9, 4
+    m = r.integers(0, t, size=n_in)
+    W = r.integers(-8, 8, size=(n_out, n_in), dtype=np.int64)
+    for sigma in (0.0, 2.0 ** (w - 20)):
+        x = np.stack([oracle.lwe_encrypt(w, s, rand_words(r, w, n), int(round(sigma * r.standard_normal())),
+                                         (D * int(m[i])) % (1 << w)) for i in range(n_in)])
+        y = oracle.lwe_affine(w, W, x)
+        for j in range(n_out):
+            want = sum(int(W[j, i]) * int(m[i]) for i in range(n_in)) % t
+            if sigma == 0.0:
+                assert oracle.lwe_phase(w, s, y[j]) == (D * want) % (1 << w)
+            assert oracle.lwe_decrypt(w, t, s, y[j]) == want
+
+
+def test_prime_set_digit_counts(oracle):
+    """Every prime-modulus set states l_g, l_ks, l_pk and l_boot equal to the
+    exact decomposition's digit count ceil(log_B Q) (Definition
+    'Decomposition'; Bootstrap figure, l_boot = ceil(log_{L_boot} Q)), and
+    that count is the smallest l with B^l > Q -- checked here with exact
+    integers, independently of the oracle's helper."""
+    import oracle.prime_q as OQ
+    for ps in S.Q_PARAM_SETS.values():
+        for log2B, ell in ((ps.log2Bg, ps.lg), (ps.log2Bks, ps.lks), (ps.log2Bpk, ps.lpk),
+                           (ps.log2Lboot, ps.lboot)):
+            assert OQ.exact_digits(ps.Q, log2B) == ell, (ps.name, log2B)
+            assert (1 << (log2B * ell)) > ps.Q and (1 << (log2B * (ell - 1))) <= ps.Q, (ps.name, log2B)

@@ -257,7 +257,7 @@ def test_single_digit_pubmux_decrypts_alike(keys):
     # of 62 bits; the outputs differ in their noise but decrypt alike
     import dataclasses
     kr, K = keys
-    ps1 = dataclasses.replace(PS, log2Lboot=62)
+    ps1 = dataclasses.replace(PS, log2Lboot=62, lboot=1)
     assert ps1.lboot == 1
     f = S.q_lut_tables(PS, 11, 1)[0]
     rot = OQ.rotation_polys(PS, [f])
@@ -289,7 +289,7 @@ def test_general_t_decryption_rounds_exactly():
             ph = (int(ct[0]) - sum(int(a) * int(b) for a, b in zip(ct[1:], s))) % PS.q
             want = int(Fraction(t * ph, PS.q) + Fraction(1, 2)) % t
             assert OQ.decrypt(ps, s, ct) == want
-    assert S.crt_sets("QZ", [7])[0].delta_q == round(PS.q / 7)
+    assert OQ.delta_in(S.crt_sets("QZ", [7])[0]) == round(PS.q / 7)
 
 
 def test_crt_polynomial_on_every_residue():
