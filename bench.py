@@ -8,6 +8,11 @@ ciphertext.  Keys, tables and ciphertexts are made on the GPU from seeded
 synthetic randomness before timing (inputs resident in HBM); L2 is flushed
 by a 512 MB write before every timed step and the flush is not timed.
 
+The default workload is large_t: n = 744, N = 4096, q = 2^64, t = 64, 4096
+ciphertexts with 16 tables, the largest single-GPU configuration.  Its line
+also carries `target_n2048`: the N = 2048, q = 2^64 set on 1000 ciphertexts,
+batched and one ciphertext per call (the plain path), with its own roofline.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
@@ -66,18 +71,16 @@ PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7"
                           "TFHE-100-2": 321.0}
 
 
-# DRAM bytes (read + write) of one blind-rotation launch over the whole batch,
-# measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the current
-# kernel for (set, variant, batch); reported only for that configuration.
+# DRAM bytes (read + write) of one blind-rotation launch, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the current kernel, keyed
+# by (set, variant): (bytes per wave of resident CTAs, CTAs per wave, what was
+# captured).  The transform-domain key streams from DRAM about once per wave,
+# so a launch over `items` CTAs moves bytes_per_wave * ceil(items / per_wave).
 KERNEL_TRAFFIC = {
-    ("B", 7, 1024): 86.26e6,    # tfhe_scale workload
-    ("D", 6, 1000): 3.19754e9,  # n2048 workload
-    # paper_80_6: the sign rotation (6000 items) scaled from a 384-item capture
-    # (1.2074 GB): the 413 MB key streams from DRAM once per wave of 152 items
-    ("FDFB-80-6", 3, 1000): 1.2074e9 * 6000 / 384,
+    # FDFB-80-6 sign rotation (variant 3, one CTA per SM): a 384-item capture
+    # (three waves) read 1.2074 GB
+    ("FDFB-80-6", 3): (1.2074e9 / 3, 152, "ncu capture of a 384-item sign rotation (3 waves), FDFB-80-6"),
 }
-KERNEL_TRAFFIC_SCALED = {("FDFB-80-6", 3, 1000): "sign-rotation launch (batch x l_boot = 6000 items), "
-                                                  "scaled by items from an ncu capture of 384 items"}
 
 
 def br_algorithmic_slots(ps, batch: int) -> float:
@@ -91,6 +94,56 @@ def br_algorithmic_slots(ps, batch: int) -> float:
     bfly = (2 * ps.lg + 2) * P * (ps.N // 2) * ps.logN
     mac = 4 * ps.lg * ps.N * P
     return float(batch) * ps.n * (4.0 * bfly + 2.0 * mac)
+
+
+def br_algorithmic_ops(ps, batch: int):
+    """The blind rotation's modular operations per launch over `batch` items
+    (n CMux steps each, figure "Blind Rotation and its setup"; extProd of
+    Definition "External Product" as exact NTT products over P primes):
+    forward butterflies of the 2l digit polynomials, inverse butterflies of
+    the 2 output columns, and the 4 l N P pointwise key products.  P = 2
+    30-bit primes lift a q = 2^32 product exactly, P = 3 a q = 2^64 or
+    prime-Q one."""
+    P = 2 if getattr(ps, "w", 64) == 32 else 3
+    per_tf = (ps.N // 2) * ps.logN * P
+    f = float(batch) * ps.n
+    return {"fwd_butterflies": f * 2 * ps.lg * per_tf, "inv_butterflies": f * 2 * per_tf,
+            "key_products": f * 4 * ps.lg * ps.N * P}
+
+
+def opmix_roofline(ps, batch_items: int, br_ms: float, probe):
+    """Roofline of the blind rotation against the measured rates of its own
+    operations (probe): the time the method's butterflies and products need at
+    the GPU's rate for each, T_alg = F / R_fwd + I / R_inv + M / R_mac, over
+    the measured time.  Forward butterflies take the faster of the two
+    forward forms the kernels use (Harvey's, and for q = 2^32 the lazy
+    family's), so the peak is the higher one."""
+    ops = br_algorithmic_ops(ps, 1)
+    F, I, M = (ops[k] * batch_items for k in ("fwd_butterflies", "inv_butterflies", "key_products"))
+    r_fwd = probe["fwd_butterfly"]
+    if getattr(ps, "w", 64) == 32:
+        r_fwd = max(r_fwd, probe["lazy_fwd_butterfly"])
+    t_alg = F / (r_fwd * 1e12) + I / (probe["inv_butterfly"] * 1e12) + M / (probe["mac64"] * 1e12)
+    total = F + I + M
+    peak = total / t_alg / 1e12
+    achieved = total / (br_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
+            "unit": "T modular ops/s (butterflies + key products)", "frac": achieved / peak,
+            "peak_source": "measured in this run: probe of the kernels' own forward and inverse butterflies "
+                           "and 32x32->64 key products at full occupancy (probe/int_pipe.cu), combined in the "
+                           "method's proportions",
+            "ops_per_launch_set": {"fwd_butterflies": F, "inv_butterflies": I, "key_products": M}}
+
+
+def slot_roofline(ps, slots: float, br_ms: float):
+    """The stricter derived roofline: the method's multiplier slots (every
+    Shoup product 4 slots, every key product 2) against 152 SMs x 64 integer
+    multiply lanes x 2.07 GHz, which leaves out the additions and minimums of
+    each butterfly (they issue on the separate ALU pipe)."""
+    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    achieved = slots / (br_ms / 1e3) / 1e12
+    return {"achieved": achieved, "peak": peak, "unit": "T IMAD slots/s", "frac": achieved / peak,
+            "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz"}
 
 
 def sample_clocks(path: str):
@@ -130,18 +183,27 @@ def read_clocks(path: str, gpu_index: int):
             "samples": len(sm)}
 
 
+PROBE_KEYS = ("imad", "imad_hi", "lop", "fwd_butterfly", "inv_butterfly", "lazy_fwd_butterfly", "mac64",
+              "fp64_flops", "int8_tensor_ops")
+
+
 def probe_rates(dev_index: int):
-    """Measured integer-pipe rates of this GPU (T ops/s): IMAD, IMAD.HI, LOP
-    and Harvey butterflies, from paper_2109_02731_gb300/probe/int_pipe.cu."""
+    """Measured rates of this GPU's pipes (T ops/s) from
+    paper_2109_02731_gb300/probe/int_pipe.cu: single integer instructions,
+    the blind rotation's butterflies and key products, FP64 fused
+    multiply-adds and 8-bit integer tensor products."""
     import ctypes
     from paper_2109_02731_gb300 import build as B
     try:
         lib = ctypes.CDLL(B.build_probe())
-        rates = (ctypes.c_double * 4)()
-        if lib.probe_int_rates(dev_index, rates) != 0:
-            return None
-        return {"imad": rates[0] / 1e12, "imad_hi": rates[1] / 1e12, "lop": rates[2] / 1e12,
-                "butterfly": rates[3] / 1e12, "unit": "T/s"}
+        n = lib.probe_pipe_count()
+        rates = (ctypes.c_double * n)()
+        rc = lib.probe_pipe_rates(dev_index, rates)
+        if rc != 0:
+            return {"error": f"probe returned {rc}"}
+        out = {k: rates[i] / 1e12 for i, k in enumerate(PROBE_KEYS)}
+        out["unit"] = "T/s (fp64_flops: T flop/s; int8_tensor_ops: T op/s, mma.sync m16n8k32)"
+        return out
     except Exception as e:  # the probe is evidence, not the measurement
         return {"error": str(e)[:200]}
 
@@ -173,7 +235,8 @@ def q_oracle_sample(ps, seconds_target: float = 10.0, tfhe: bool = False):
     switch, PubMux and the LWE key switch, at full size, and scales each by
     its count per bootstrap.  Key material of the right shapes is drawn
     uniformly mod Q without key generation: the products cost the same for
-    any values.  Returns (seconds per bootstrap, description)."""
+    any values.  Returns (seconds per bootstrap, description, seconds the
+    sample itself took)."""
     import oracle.prime_q as OQ
     rng = np.random.default_rng(0)
     Q, N, n, lg, lb = ps.Q, ps.N, ps.n, ps.lg, ps.lboot
@@ -190,6 +253,7 @@ def q_oracle_sample(ps, seconds_target: float = 10.0, tfhe: bool = False):
     t1 = cmux_steps(1)
     steps = int(min(16, max(1, seconds_target * 0.6 / max(t1, 1e-3))))
     t_step = cmux_steps(steps) if steps > 1 else t1
+    measured = t1 + (t_step * steps if steps > 1 else 0.0)
     lwe = uni(N + 1)
     pk = uni(N, ps.lpk, 2, N)
     t0 = time.perf_counter()
@@ -205,18 +269,93 @@ def q_oracle_sample(ps, seconds_target: float = 10.0, tfhe: bool = False):
     t0 = time.perf_counter()
     OQ.pubmux(ps, cR, p0, -p0)
     t_pm = time.perf_counter() - t0
+    measured += t_pk + t_ks + t_pm
     if tfhe:  # the TFHE bootstrap: one rotation and the LWE key switch
         sec = n * t_step + t_ks
         desc = (f"{steps} full-size CMux step(s) ({t_step:.2f} s each, x {n} per TFHE bootstrap) and the "
                 f"LWE key switch ({t_ks:.2f} s) of the schoolbook oracle on one core, scaled to one "
                 f"bootstrap ({sec / 60:.1f} min)")
-        return sec, desc
+        return sec, desc, measured
     sec = (lb + 1) * n * t_step + lb * t_pk + t_pm + t_ks
     desc = (f"{steps} full-size CMux step(s) ({t_step:.2f} s each, x {(lb + 1) * n} per bootstrap), one "
             f"packing key switch ({t_pk:.2f} s, x {lb}), PubMux ({t_pm:.2f} s) and the LWE key switch "
             f"({t_ks:.2f} s) of the schoolbook oracle on one core, scaled to one bootstrap "
             f"({sec / 3600:.2f} h)")
-    return sec, desc
+    return sec, desc, measured
+
+
+def p2_oracle_sample(ps, seconds_target: float = 10.0):
+    """The power-of-two oracle's time per bootstrap from a bounded sample, for
+    sets whose single bootstrap takes the schoolbook oracle longer than a
+    benchmark step should (2 n CMux steps of 2 (2 l) N^2 word products each):
+    whole full-size CMux steps of the blind rotation (the oracle's ring
+    products spread over every host core), one packing key switch, PubMux and
+    the LWE key switch, each scaled by its count per bootstrap.  Key material
+    of the right shapes is drawn uniformly without key generation: the
+    products cost the same for any values.  Returns (seconds per bootstrap,
+    description, cores, seconds the sample itself took)."""
+    import oracle as O
+    cores = O.max_threads()
+    O.set_threads(cores)
+    rng = np.random.default_rng(0)
+    N, n, lg, w = ps.N, ps.n, ps.lg, ps.w
+    uni = lambda *shape: (rng.integers(0, 2 ** 63, shape, dtype=np.uint64) * np.uint64(2)
+                          + rng.integers(0, 2, shape, dtype=np.uint64)) >> np.uint64(64 - w)
+
+    measured = [0.0]
+
+    def cmux_steps(steps):
+        pset = dataclasses.replace(ps, n=steps)
+        ctN = np.zeros(steps + 1, dtype=np.uint64)
+        ctN[1:] = 1 + np.arange(steps)  # nonzero masks: no step is skipped
+        bsk, acc = uni(steps, 2 * lg, 2, N), uni(2, N)
+        t0 = time.perf_counter()
+        O.blind_rotate(pset, bsk, acc, ctN)
+        dt = time.perf_counter() - t0
+        measured[0] += dt
+        return dt / steps
+
+    t1 = cmux_steps(1)
+    steps = int(min(16, max(1, seconds_target * 0.6 / max(t1, 1e-3))))
+    t_step = cmux_steps(steps) if steps > 1 else t1
+    # the key switches' cost is linear in the input dimension: time them on
+    # the first N / 8 input words and scale by 8 (keeps the key material small)
+    sub = max(1, N // 8)
+    lwe = uni(sub + 1)
+    pk = uni(sub, ps.lpk, 2, N)
+    t0 = time.perf_counter()
+    O.keyswitch(w, ps.log2Bpk, ps.lpk, pk, lwe)
+    t_pk = time.perf_counter() - t0
+    del pk
+    ksk = uni(sub, ps.lks, n + 1)
+    t0 = time.perf_counter()
+    O.keyswitch(w, ps.log2Bks, ps.lks, ksk, lwe)
+    t_ks = time.perf_counter() - t0
+    cR = uni(2, N)
+    p0 = rng.integers(0, ps.t, N)
+    t0 = time.perf_counter()
+    O.pubmux(w, ps.t, cR, p0, (p0 + 1) % ps.t)
+    t_pm = time.perf_counter() - t0
+    measured[0] += t_pk + t_ks + t_pm
+    t_pk, t_ks = t_pk * N / sub, t_ks * N / sub
+    sec = 2 * n * t_step + t_pk + t_pm + t_ks
+    desc = (f"{steps} full-size CMux step(s) ({t_step * 1e3:.1f} ms each, x {2 * n} per bootstrap), the "
+            f"packing key switch ({t_pk:.2f} s) and the LWE key switch ({t_ks:.2f} s) timed on {sub} of the "
+            f"{N} input words and scaled by {N // sub}, and PubMux ({t_pm:.3f} s), of the schoolbook oracle "
+            f"with its ring products spread over {cores} threads, scaled to one bootstrap ({sec:.1f} s)")
+    return sec, desc, cores, measured[0]
+
+
+def oracle_bootstrap_macs(ps) -> float:
+    """Schoolbook word products of one bootstrap: 2 n CMux steps of 2 (2 l)
+    N^2, plus the packing key switch's N l_pk 2N."""
+    return 2.0 * ps.n * 2 * (2 * ps.lg) * ps.N ** 2 + ps.N * ps.lpk * 2.0 * ps.N
+
+
+# Above this many word products a whole bootstrap takes the oracle longer than
+# a benchmark step should (set B, 1.6e10, takes about half a second on 16
+# cores); larger sets are timed by p2_oracle_sample.
+ORACLE_WHOLE_LIMIT = 3e10
 
 
 def dist_setup():
@@ -238,20 +377,47 @@ def run_reference(args):
         tf = g.mode == "tfhe"
         for _ in range(args.warmup):
             q_oracle_sample(ps, tfhe=tf)
-        secs = []
+        units, walls = [], []
         desc = ""
         for _ in range(args.steps):
-            sec, desc = q_oracle_sample(ps, tfhe=tf)
-            secs.append(sec)
-        value = args.steps / sum(secs)
+            sec, desc, wall = q_oracle_sample(ps, tfhe=tf)
+            units.append(wall / sec)  # the fraction of one bootstrap the sample did
+            walls.append(wall)
+        value = sum(units) / sum(walls)
         line = {
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps,
+            "units_per_step": sum(units) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded key-shaped words, no key generation: the oracle's cost does not "
                     "depend on the values)",
             "config": config_of(args, wl, g, ps),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return 0
+    if g.mode == "fdfb" and g.tables_per_input == 1 and oracle_bootstrap_macs(ps) > ORACLE_WHOLE_LIMIT:
+        for _ in range(args.warmup):
+            p2_oracle_sample(ps, seconds_target=3.0)
+        units, walls = [], []
+        desc, cores = "", 1
+        for _ in range(args.steps):
+            sec, desc, cores, wall = p2_oracle_sample(ps, seconds_target=3.0)
+            units.append(wall / sec)  # the fraction of one bootstrap the sample did
+            walls.append(wall)
+        value = sum(units) / sum(walls)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps,
+            "units_per_step": sum(units) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32" if ps.w == 32 else "u64",
+            "data": "synthetic (seeded key-shaped words, no key generation: the oracle's cost does not "
+                    "depend on the values)",
+            "config": config_of(args, wl, g, ps),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "per step: " + desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
@@ -327,8 +493,11 @@ def cpu_baseline(wl, g, ps, seconds_target=20.0):
     """The oracle timed on a bounded sample (rank 0, one GPU only)."""
     import oracle as O
     if is_prime_set(ps):
-        sec, desc = q_oracle_sample(ps, tfhe=g.mode == "tfhe")
+        sec, desc, _ = q_oracle_sample(ps, tfhe=g.mode == "tfhe")
         return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if g.mode == "fdfb" and g.tables_per_input == 1 and oracle_bootstrap_macs(ps) > ORACLE_WHOLE_LIMIT:
+        sec, desc, cores, _ = p2_oracle_sample(ps, seconds_target=seconds_target)
+        return {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     cores = O.max_threads()
     O.set_threads(cores)
     K = O.Keys(ps, S.key_randomness(ps, wl.seed))
@@ -362,18 +531,20 @@ class Job:
     """The timed work of one workload on this rank: `step()` queues one step on
     the current stream; `units` bootstraps per step."""
 
-    def __init__(self, torch, F, ctx, dev, args, rank):
+    def __init__(self, torch, F, ctx, dev, args, rank, workload=None, batch=None):
         self.torch, self.F, self.ctx, self.dev = torch, F, ctx, dev
-        wl = S.WORKLOADS[args.workload]
+        wl = S.WORKLOADS[workload or args.workload]
         self.wl = wl
         self.groups = []
         self.tuned = {}
+        if batch is None and workload is None:
+            batch = args.batch
         if wl.mlp_layers:
             self._prepare_mlp(args, rank)
         else:
             for gi, g in enumerate(wl.groups):
-                if args.batch is not None and len(wl.groups) == 1:
-                    g = dataclasses.replace(g, batch=args.batch)  # smaller case, e.g. for ncu
+                if batch is not None and len(wl.groups) == 1:
+                    g = dataclasses.replace(g, batch=batch)  # smaller case, e.g. for ncu
                 self.groups.append(self._prepare_group(gi, g, args, rank))
             self.units = sum(x["batch"] * x["k"] for x in self.groups)
 
@@ -487,6 +658,13 @@ class Job:
         return sum((0 if g.get("mode") == "tfhe" else br_algorithmic_slots(g["ps"], g["batch"] * g.get("lboot", 1)))
                    + br_algorithmic_slots(g["ps"], g["batch"] * g["k"]) for g in self.groups)
 
+    def br_items_per_step(self):
+        """Blind rotations per step (sign and function), each n CMux steps."""
+        if self.wl.mlp_layers:
+            return 2 * sum(self.mlp_batches)
+        return sum((0 if g.get("mode") == "tfhe" else g["batch"] * g.get("lboot", 1)) + g["batch"] * g["k"]
+                   for g in self.groups)
+
     def io_bytes(self):
         if self.wl.mlp_layers:
             g = self.groups[0]
@@ -535,13 +713,82 @@ def config_for(job, args):
             "l2": "flushed before every timed step (512 MB write, not timed)"}
 
 
+def timed_steps(torch, ctx, job, stream, flush, steps, barrier):
+    """Times `steps` steps of `job` with CUDA events on the launching stream,
+    L2 flushed (not timed) before each; returns (total ms, profile)."""
+    ctx.profile_enable(True)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        job.step()
+        ev[k][1].record(stream)
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    return float(sum(a.elapsed_time(b) for a, b in ev)), prof
+
+
+def time_plain(torch, ctx, job, stream, reps=8):
+    """The plain path: one ciphertext per bootstrap call, the same kernels."""
+    g = job.groups[0]
+    one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()
+    ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(reps):
+        ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
+    p1.record(stream)
+    p1.synchronize()
+    return {"value": reps / (p0.elapsed_time(p1) / 1e3), "unit": UNIT,
+            "what": f"one ciphertext per bootstrap call, set {g['ps'].name}, same kernels ({reps} calls)"}
+
+
+def rooflines(job, prof, steps, probe):
+    """The op-mix roofline (measured peak) and the slot roofline (derived) of
+    the blind rotation launches of `steps` steps of `job`."""
+    br_ms = prof["blind_rotate_union"][0]
+    items = job.br_items_per_step() * steps
+    ps0 = job.groups[0]["ps"]
+    out = None
+    if probe and "error" not in probe and len(set(g["ps"].name for g in job.groups)) == 1:
+        out = opmix_roofline(ps0, items, br_ms, probe)
+    slots = slot_roofline(ps0, job.slots_per_step() * steps, br_ms)
+    if out is None:
+        out = {"bound": "alu", "kernel": "blind_rotate_kernel", **slots}
+        slots = None
+    out["br_ms_per_step"] = br_ms / steps
+    out["launches"] = prof["blind_rotate_sign"][1] + prof["blind_rotate_func"][1]
+    if slots is not None:
+        out["slot_model"] = slots
+    return out
+
+
+def kernel_traffic(job, ctx):
+    """DRAM bytes of one blind-rotation launch over the workload (sign
+    rotation), from the ncu capture of the autotuned variant, or None."""
+    if len(job.groups) != 1 or job.wl.mlp_layers or job.groups[0]["k"] != 1:
+        return None, None
+    g0 = job.groups[0]
+    key = (g0["ps"].name, ctx.variant_info(g0["sid"])[0])
+    if key not in KERNEL_TRAFFIC:
+        return None, None
+    per_wave, ctas, src = KERNEL_TRAFFIC[key]
+    items = g0["batch"] * g0.get("lboot", 1)
+    waves = -(-items // ctas)
+    return per_wave * waves, (f"{src}: {per_wave / 1e6:.1f} MB per wave of {ctas} CTAs, x {waves} waves for "
+                              f"the {items}-item launch, set {key[0]} variant {key[1]}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tfhe_scale", choices=sorted(S.WORKLOADS))
+    ap.add_argument("--workload", default="large_t", choices=sorted(S.WORKLOADS))
     ap.add_argument("--batch", type=int, default=None,
                     help="override the batch of a single-group workload (a smaller case for profiling; "
                          "not the workload's benchmark configuration)")
@@ -553,7 +800,9 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false",
                     help="skip timing the plain path (one ciphertext per bootstrap call, rank 0)")
     ap.add_argument("--plain", dest="plain", action="store_true", help=argparse.SUPPRESS)
-    ap.set_defaults(plain=True)
+    ap.add_argument("--no-target", dest="target", action="store_false",
+                    help="skip the N = 2048 target measurement that the large_t line carries")
+    ap.set_defaults(plain=True, target=True)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -587,21 +836,12 @@ def main():
     clk_path = os.path.join(tempfile.gettempdir(), f"fdfb_clocks_{os.getpid()}.csv")
     proc, fh = sample_clocks(clk_path)
     time.sleep(0.3)
-    ctx.profile_enable(True)
-    barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        job.step()
-        ev[k][1].record(stream)
-    barrier()
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    ms_total = float(sum(a.elapsed_time(b) for a, b in ev))
+    ms_total, prof = timed_steps(torch, ctx, job, stream, flush, args.steps, barrier)
 
     # End to end through the public API with host buffers: the step's inputs
-    # go host -> device from pinned memory, the outputs come back.
+    # go host -> device from pinned memory, the outputs come back.  Steps
+    # longer than half a second are timed five times at most.
+    e2e_steps = max(1, min(args.steps, 5 if ms_total / args.steps > 500 else args.steps))
     host_in = [(g["ct"].cpu().pin_memory(), g["ids"].cpu().pin_memory() if "ids" in g else None)
                for g in job.groups]
     dev_in = [(torch.empty_like(g["ct"]), torch.empty_like(g["ids"]) if "ids" in g else None)
@@ -619,7 +859,7 @@ def main():
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
-    for k in range(max(1, args.steps)):
+    for k in range(e2e_steps):
         flush.zero_()
         e0.record(stream)
         for (hc, hi), (dc, di) in zip(host_in, dev_in):
@@ -650,22 +890,32 @@ def main():
     if world > 1:
         ms_total, e2e_ms = slowest_rank([ms_total, e2e_ms], dev)
 
-    plain = None
-    if (args.plain and rank == 0 and not job.wl.mlp_layers and len(job.groups) == 1
-            and job.groups[0]["k"] == 1 and job.groups[0].get("mode") != "tfhe"):
-        reps = 8
-        g = job.groups[0]
-        one_ct, one_id, one_out = g["ct"][:1].clone(), g["ids"][:1].clone(), g["out"][:1].clone()
-        ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
-        torch.cuda.synchronize()  # rank 0 only: no collective here
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(reps):
-            ctx.bootstrap(g["sid"], one_ct, one_id, one_out)
-        p1.record(stream)
-        p1.synchronize()
-        plain = {"value": reps / (p0.elapsed_time(p1) / 1e3), "unit": UNIT,
-                 "what": f"one ciphertext per bootstrap call, set {g['ps'].name}, same kernels"}
+    single = (not job.wl.mlp_layers and len(job.groups) == 1 and job.groups[0]["k"] == 1
+              and job.groups[0].get("mode") != "tfhe")
+    plain = time_plain(torch, ctx, job, stream) if (args.plain and rank == 0 and single) else None
+    launches = job.launches_per_step() * args.steps
+    probe = probe_rates(dev.index) if rank == 0 else None
+
+    # The N = 2048 target (rank 0): batched and plain on the same GPU.
+    target = None
+    if rank == 0 and args.target and args.workload == "large_t" and args.batch is None:
+        tjob = Job(torch, F, ctx, dev, args, rank, workload="n2048")
+        for _ in range(3):
+            tjob.step()
+        ctx.sync()
+        t_ok = tjob.decrypt_ok()
+        t_steps = max(3, min(args.steps, 10))
+        t_ms, t_prof = timed_steps(torch, ctx, tjob, stream, flush, t_steps, lambda: torch.cuda.synchronize())
+        t_value = tjob.units * t_steps / (t_ms / 1e3)
+        t_plain = time_plain(torch, ctx, tjob, stream)
+        t_traffic, t_src = kernel_traffic(tjob, ctx)
+        t_roof = rooflines(tjob, t_prof, t_steps, probe)
+        t_roof["traffic"], t_roof["traffic_source"] = t_traffic, t_src
+        target = {"workload": config_for(tjob, args)["workload"], "value": t_value, "unit": UNIT,
+                  "steps": t_steps, "ms_per_step": t_ms / t_steps, "decrypt_ok": t_ok,
+                  "plain_path": t_plain, "batched_over_plain": t_value / t_plain["value"],
+                  "roofline": t_roof, "autotune": tjob.tuned,
+                  "goal": "batched >= 10x plain and >= 0.5 of the roofline"}
 
     if rank != 0:
         if world > 1:
@@ -674,13 +924,6 @@ def main():
 
     units = job.units * args.steps * world
     value = units / (ms_total / 1e3)
-    # wall time with at least one blind-rotation launch in flight (the
-    # launches of the chunks of one call overlap on different streams)
-    br_ms = prof["blind_rotate_union"][0]
-    br_n = prof["blind_rotate_sign"][1] + prof["blind_rotate_func"][1]
-    slots = job.slots_per_step() * args.steps
-    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12  # T slots/s
-    achieved = slots / (br_ms / 1e3) / 1e12
     stages = {k: v for k, v in prof.items() if k != "blind_rotate_union"}
     chunked = any(ctx.get_chunks(g["sid"]) > 1 for g in job.groups) and len(job.groups) == 1
     # launches of different stages overlap when a call is chunked, so their
@@ -689,16 +932,8 @@ def main():
         k: round(v[0] / max(1e-9, sum(x[0] for x in stages.values())), 4) for k, v in stages.items()}
     h2d, d2h = job.io_bytes()
     ps0 = job.groups[0]["ps"]
-    traffic, traffic_src = None, None
-    if len(job.groups) == 1 and not job.wl.mlp_layers and job.groups[0]["k"] == 1:
-        g0 = job.groups[0]
-        key = (ps0.name, ctx.variant_info(g0["sid"])[0], g0["batch"])
-        if key in KERNEL_TRAFFIC:
-            traffic = KERNEL_TRAFFIC[key]
-            traffic_src = ("dram bytes per unchunked blind-rotation launch over the batch, "
-                           f"ncu capture of set {key[0]} variant {key[1]}, {key[2]} ciphertexts")
-            if key in KERNEL_TRAFFIC_SCALED:
-                traffic_src = "dram bytes per " + KERNEL_TRAFFIC_SCALED[key] + f", set {key[0]} variant {key[1]}"
+    roof = rooflines(job, prof, args.steps, probe)
+    roof["traffic"], roof["traffic_source"] = kernel_traffic(job, ctx)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -707,25 +942,21 @@ def main():
         "data": "synthetic (seeded SplitMix64 keys, messages and tables; keys generated on the GPU)",
         "config": config_for(job, args),
         "decrypt_ok": decrypt_ok,
-        "roofline": {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "T IMAD slots/s", "frac": achieved / peak,
-                     "traffic": traffic, "traffic_source": traffic_src,
-                     "peak_source": "derived: 152 SMs x 64 IMAD lanes/clock x 2.07 GHz",
-                     "br_ms_per_step": br_ms / args.steps, "launches": br_n,
-                     "slots_per_step": job.slots_per_step()},
+        "roofline": roof,
         "stage_share": stage_share,
         "autotune": job.tuned,
-        "gpu_launches": job.launches_per_step() * args.steps,
-        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "e2e": {"value": job.units * e2e_steps * world / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "clocks": clocks,
     }
-    probe = probe_rates(dev.index)
     if probe:
-        line["roofline"]["probe"] = probe
+        line["probe"] = probe
     if plain:
         line["plain_path"] = plain
         line["batched_over_plain"] = value / plain["value"]
+    if target:
+        line["target_n2048"] = target
     if is_prime_set(ps0) and ps0.name in PAPER_MS_PER_BOOTSTRAP:
         ms = PAPER_MS_PER_BOOTSTRAP[ps0.name]
         line["paper_context"] = {"ms_per_bootstrap": ms, "bootstraps_per_s": 1e3 / ms,

@@ -266,25 +266,34 @@ int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
                          int64_t batch, void* ct_out, const fdfb_debug_bufs* dbg,
                          void* cuda_stream);
 
-/* fdfb_bootstrap for callers that cannot allocate GPU memory -- code that
- * runs where cudaMalloc is not allowed or not safe (inside a stream capture,
- * in a real-time or memory-budgeted service loop, in a host callback) -- and
- * so cannot let fdfb_bootstrap grow its scratch on first use.  The paper has
- * no counterpart; this is a library convenience.
+/* fdfb_bootstrap for callers that cannot allocate GPU memory at call time
+ * and so cannot let fdfb_bootstrap grow its scratch on first use: code in a
+ * host callback enqueued on a stream (CUDA calls are not allowed there),
+ * services whose device memory is all handed to a caching allocator up front
+ * or capped by a budget, and latency-bound loops that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree may imply.  The paper
+ * has no counterpart; this is a library convenience.
  *
  * Same arguments, results and errors as fdfb_bootstrap, bit for bit.  The
  * intermediates live in one fixed 32 MiB device array compiled into the
  * library (every GPU that loads the library holds it until the process
  * exits); this call performs no cudaMalloc, cudaFree or other allocation.
- *   - batch may be at most fdfb_noalloc_max_batch(ctx, set_id): 32 MiB /
- *     ((6N + 2) words), e.g. 1365 ciphertexts at N = 1024, q = 2^32 and 170
- *     at N = 4096, q = 2^64.  Larger batches return FDFB_EINVAL.
+ *   - batch may be at most fdfb_noalloc_max_batch(ctx, set_id), which is
+ *     32 MiB divided by the intermediates of one input:
+ *       power-of-two sets: (6N + 2) words, e.g. 1364 ciphertexts at N = 1024,
+ *       q = 2^32 and 170 at N = 4096, q = 2^64;
+ *       prime-modulus sets: l_boot (7N + 1) + 3N + 1 + 2(n + 1) 64-bit
+ *       words, e.g. 44 ciphertexts for FDFB-80-6 (n = 700, N = 2048,
+ *       l_boot = 6).
+ *     Larger batches return FDFB_EINVAL.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
  *   - All calls, from any context on the device, share the one array: calls
  *     that can overlap on the GPU (different streams, no ordering) race and
  *     corrupt each other's results.  Every intermediate is fully rewritten by
- *     each call, so nothing left by an earlier call is read.
+ *     each call (sums that accumulate are zeroed first), so nothing left by
+ *     an earlier call is read.
  *   - Keys and tables must be installed beforehand (those calls allocate). */
 int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
                            int64_t batch, void* ct_out, void* cuda_stream);
@@ -385,6 +394,16 @@ int fdfb_variant_info(fdfb_ctx* ctx, int set_id, int* current, int* count, int* 
  * enable.  Disabled by default. */
 int fdfb_profile_enable(fdfb_ctx* ctx, int enable);
 int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launches);
+
+/* Test hook; the paper has no counterpart.  flags = 0 (the default) is
+ * normal operation.  Bit 0: the blind rotations of fdfb_bootstrap issue none
+ * of the bulk copies that stage key rows in shared memory (the staged-key
+ * layout of N = 2048, q = 2^64) and bound the wait for them to 2^12 polls,
+ * so the wait expires with no copy in flight: the call then latches
+ * FDFB_ETIMEOUT (reported by fdfb_sync), computes garbage for the batch and
+ * leaves the context usable.  It exists to exercise that error path without
+ * any fault.  FDFB_EINVAL for unknown bits. */
+int fdfb_test_hooks(fdfb_ctx* ctx, int flags);
 
 /* Waits for the stream and reports latched device-side errors (e.g.
  * FDFB_ETIMEOUT) and CUDA errors; clears the latch. */

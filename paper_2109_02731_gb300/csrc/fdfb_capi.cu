@@ -138,6 +138,8 @@ struct fdfb_ctx {
   // side streams and fork/join events of the chunked single-set pipeline
   std::vector<cudaStream_t> chunk_side;
   std::vector<cudaEvent_t> chunk_events;
+  // fdfb_test_hooks flags (0 in normal use)
+  int test_flags = 0;
 };
 
 namespace {
@@ -504,6 +506,10 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   br.rep = 1;
   br.signed_digits = (int)P.signed_digits;
   br.err = ctx->d_err;
+  if (ctx->test_flags & 1) {  // fdfb_test_hooks: no staged-key copies, a short bounded wait
+    br.test_skip_key_copy = 1;
+    br.key_wait_polls = 1u << 12;
+  }
   {
     StageTimer tm(tctx, 0, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -1636,6 +1642,13 @@ int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launc
   ctx->marks.clear();
   *total_ms = ctx->prof_ms[stage];
   *launches = ctx->prof_n[stage];
+  return FDFB_OK;
+}
+
+int fdfb_test_hooks(fdfb_ctx* ctx, int flags) {
+  if (!ctx || (flags & ~1)) return FDFB_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->test_flags = flags;
   return FDFB_OK;
 }
 

@@ -238,6 +238,10 @@ struct BRParams {
   int rep;                      // items per input ciphertext: item i rotates by ct[i / rep]
   int signed_digits;            // balanced digits: the launcher picks the kernel built with SG
   int* err;                     // device error latch (FDFB_ETIMEOUT if a key copy never lands)
+  // test hook (fdfb_test_hooks): TK issues no key copies, so its bounded wait
+  // expires with nothing in flight; key_wait_polls bounds that wait (0: 2^20)
+  int test_skip_key_copy;
+  uint32_t key_wait_polls;
   // prime-modulus sets (the kernel built with MQ): words are residues mod
   // Q, the input LWE words already lie in [0, 2N) (q = 2N), and sign item i
   // starts from (and adds after extraction) sgn_scale[i % rep] instead of
@@ -436,9 +440,11 @@ blind_rotate_kernel(const BRParams prm) {
   // kfail latches an expired wait (no further copies or waits after it)
   uint32_t kph = 0, kfph = 0;
   bool kfail = false;
-  constexpr uint32_t kWaitLimit = 1u << 20;
+  const uint32_t kWaitLimit = prm.key_wait_polls ? prm.key_wait_polls : (1u << 20);
+  const bool kcopy = !prm.test_skip_key_copy;
   if constexpr (TK) {
-    if (t == 0 && n > 0) bulk_copy_g2s(kst, prm.bsk + (size_t)grp * R * 2 * KH * N, kPairWords * 4, kmb);
+    if (t == 0 && n > 0 && kcopy)
+      bulk_copy_g2s(kst, prm.bsk + (size_t)grp * R * 2 * KH * N, kPairWords * 4, kmb);
   }
   for (int i = 0; i < n; ++i) {
     const int a = aN[i];
@@ -565,7 +571,7 @@ blind_rotate_kernel(const BRParams prm) {
         // the group is done with the staged rows: stage the next pair (this
         // step's, else the next step's first)
         named_bar(bar, G);
-        if (t == 0 && !kfail) {
+        if (t == 0 && !kfail && kcopy) {
           const bool more = r0 + M < R;
           if (more || i + 1 < n) {
             const uint32_t* src = more ? krow + (size_t)(r0 + M) * 2 * KH * N

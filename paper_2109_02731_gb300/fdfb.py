@@ -29,7 +29,7 @@ SYMBOLS = [
     "fdfb_tfhe_poly_setup", "fdfb_tfhe_bootstrap",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
     "fdfb_set_variant", "fdfb_variant_info", "fdfb_set_chunks", "fdfb_get_chunks", "fdfb_profile_enable",
-    "fdfb_profile_read", "fdfb_sync", "fdfb_strerror",
+    "fdfb_profile_read", "fdfb_test_hooks", "fdfb_sync", "fdfb_strerror",
 ]
 
 
@@ -108,6 +108,7 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_variant_info": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
                 "fdfb_profile_enable": ([vp, i32], i32),
                 "fdfb_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], i32),
+                "fdfb_test_hooks": ([vp, i32], i32),
                 "fdfb_sync": ([vp, vp], i32),
                 "fdfb_strerror": ([i32], C.c_char_p),
             }
@@ -379,6 +380,11 @@ class Context:
             _check(self.L.fdfb_profile_read(self.h, i, C.byref(ms), C.byref(n)), "fdfb_profile_read")
             out[name] = (ms.value, n.value)
         return out
+
+    def test_hooks(self, flags: int) -> None:
+        """fdfb_test_hooks: bit 0 makes the staged-key blind rotation skip
+        its key copies so that its bounded wait expires (error-path tests)."""
+        _check(self.L.fdfb_test_hooks(self.h, int(flags)), "fdfb_test_hooks")
 
     def sync(self, stream=None) -> None:
         _check(self.L.fdfb_sync(self.h, _stream(stream)), "fdfb_sync")

@@ -1,7 +1,10 @@
 """fdfb_bootstrap_noalloc: the bootstrap for callers that cannot allocate GPU
-memory (code under stream capture, real-time or memory-budgeted service
-loops).  It must give exactly what fdfb_bootstrap gives, call after call, on
-its fixed scratch.  Runs last so a failure here leaves every other test run."""
+memory at call time (host callbacks on a stream, services whose device memory
+belongs to a caching allocator or a budget, latency-bound loops).  It must give
+exactly what fdfb_bootstrap gives, call after call, on its fixed scratch, for
+the power-of-two sets and for the prime-modulus sets (whose pipeline lays the
+scratch out differently).  Runs last so a failure here leaves every other test
+run."""
 import numpy as np
 import pytest
 
@@ -23,7 +26,8 @@ def env():
 
 def _inputs(torch, F, ctx, sid, ps, kr, seed, count, n_luts):
     dev = "cuda"
-    mr = S.message_randomness(ps, seed, count)
+    prime = isinstance(ps, S.QParamSet)
+    mr = (S.q_message_randomness if prime else S.message_randomness)(ps, seed, count)
     ct = torch.empty((count, ps.n + 1), dtype=F.word_torch(ps), device=dev)
     ctx.lwe_encrypt(sid, torch.tensor(kr.s, device=dev), F.to_device_words(ps, mr.a),
                     torch.tensor(mr.e, device=dev), torch.tensor(mr.m, device=dev), ct)
@@ -31,14 +35,15 @@ def _inputs(torch, F, ctx, sid, ps, kr, seed, count, n_luts):
     return ct, ids
 
 
-@pytest.mark.parametrize("name,count", [("A", 40), ("B", 300)])
+@pytest.mark.parametrize("name,count", [("A", 40), ("B", 300), ("QZ", 40)])
 def test_noalloc_matches_bootstrap_twice(env, name, count):
     torch, F, ctx = env
-    ps = S.PARAM_SETS[name]
+    ps = S.param_set(name)
+    prime = isinstance(ps, S.QParamSet)
     sid = ctx.register(ps)
-    kr = S.key_randomness(ps, 21)
+    kr = (S.q_key_randomness if prime else S.key_randomness)(ps, 21)
     ctx.keys_generate(sid, kr)
-    for f in S.lut_tables(ps, 21, 3):
+    for f in (S.q_lut_tables if prime else S.lut_tables)(ps, 21, 3):
         ctx.lut_setup(sid, f)
     assert ctx.noalloc_max_batch(sid) >= count
     for call, seed in enumerate((31, 32)):  # two calls in a row, different inputs
@@ -62,3 +67,14 @@ def test_noalloc_rejects_batches_beyond_its_scratch(env):
     with pytest.raises(F.FDFBError) as e:
         ctx.bootstrap_noalloc(sid, ct, ids, torch.empty_like(ct))
     assert e.value.code == -1
+
+
+def test_noalloc_cap_of_a_prime_set(env):
+    """The prime-modulus pipeline keeps l_boot sign LWEs, their packing sums
+    and packed RLWEs per input: l_boot (7N + 1) + 3N + 1 + 2(n + 1) words,
+    44 inputs for FDFB-80-6."""
+    torch, F, ctx = env
+    ps = S.Q_PARAM_SETS["FDFB-80-6"]
+    sid = ctx.register(ps)
+    per_input = ps.lboot * (7 * ps.N + 1) + 3 * ps.N + 1 + 2 * (ps.n + 1)
+    assert ctx.noalloc_max_batch(sid) == (32 << 20) // (per_input * 8) == 44
