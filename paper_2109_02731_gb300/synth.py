@@ -444,6 +444,20 @@ def q_key_randomness(ps: QParamSet, seed: int) -> QKeyRandomness:
     return QKeyRandomness(s, sk, bsk_a, bsk_e, pk_a, pk_e, ksk_a, ksk_e)
 
 
+def q_uniform_key_words(ps: QParamSet, seed: int):
+    """Key-shaped words uniform mod Q in the canonical layouts -- bsk
+    [n][2lg][2][N], pK [N][lpk][2][N], ksK [N][lks][n+1] -- that are no
+    encryptions at all: the bootstrap's arithmetic is defined for any words,
+    so they exercise it at full ring degree and digit counts without the cost
+    of key generation (outputs do not decrypt)."""
+    st = Stream(seed, STREAM_KEYS, hash_name(ps.name), 99)
+    n, N, Q = ps.n, ps.N, ps.Q
+    bsk = _below_big(st.sub(1), n * 2 * ps.lg * 2 * N, Q).reshape(n, 2 * ps.lg, 2, N)
+    pk = _below_big(st.sub(2), N * ps.lpk * 2 * N, Q).reshape(N, ps.lpk, 2, N)
+    ksk = _below_big(st.sub(3), N * ps.lks * (n + 1), Q).reshape(N, ps.lks, n + 1)
+    return bsk, pk, ksk
+
+
 def q_message_randomness(ps: QParamSet, seed: int, count: int, group: int = 0,
                          m: Optional[np.ndarray] = None) -> MessageRandomness:
     """Messages in Z_t, masks uniform mod q = 2N, noise sigma_in."""

@@ -249,7 +249,8 @@ def test_fdfb_set_D_full_batch(F, torch_cuda, ctx, oracle):
     1000, in the autotuned layout and chunking the benchmark times: sampled
     bit-exact parity of every stage, chunked call = single pipeline, every
     output decrypts correctly."""
-    _big_workload(F, torch_cuda, ctx, oracle, "D", 1000, 4, 3, [0, 999])
+    # eight ciphertexts: both ends, across the seven waves of 152 CTAs, every table
+    _big_workload(F, torch_cuda, ctx, oracle, "D", 1000, 4, 3, [0, 151, 152, 333, 500, 761, 998, 999])
 
 
 @pytest.mark.slow
@@ -259,7 +260,8 @@ def test_fdfb_large_t_full_batch(F, torch_cuda, ctx, oracle):
     every output decrypts correctly."""
     wl = S.WORKLOADS["large_t"]
     g = wl.groups[0]
-    _big_workload(F, torch_cuda, ctx, oracle, "C", g.batch, g.n_luts, wl.seed, [g.batch - 1])
+    # four ciphertexts: first, last and two from inner waves
+    _big_workload(F, torch_cuda, ctx, oracle, "C", g.batch, g.n_luts, wl.seed, [0, 1517, 3040, g.batch - 1])
 
 
 def test_keygen_then_bootstrap_matches_upload(F, torch_cuda, ctx, oracle):
@@ -398,6 +400,43 @@ def test_mixed_groups_match_separate_calls(F, torch_cuda, ctx, oracle):
         if ps.w == 64:
             dec = [oracle.lwe_decrypt(ps.w, ps.t, K.s, c) for c in got]
             assert dec == [int(fs[i][m]) for i, m in zip(ids, mr.m)]
+
+
+@pytest.mark.slow
+def test_mixed_workload_full_size_matches_oracle(F, torch_cuda, ctx, oracle):
+    """The mixed workload's shape in one fdfb_bootstrap_mixed call: set B x 37,
+    set D x 1000 and set C x 2900 with uniform table choices, each set's
+    autotuned layout and chunking as the benchmark uses them.  Sampled
+    outputs of every group equal the oracle's bit for bit, and every output of
+    the q = 2^64 groups decrypts to f(m)."""
+    spec = [("B", 1, 4, 37, [0, 18, 36]), ("D", 3, 4, 1000, [7, 999]), ("C", 2, 16, 2900, [0, 2899])]
+    groups, checks = [], []
+    for gi, (name, seed, nl, batch, sample) in enumerate(spec):
+        ps = S.PARAM_SETS[name]
+        K = oracle_keys(name, seed)
+        sid = install(ctx, oracle, name, seed, nl)
+        ctx.autotune(sid, batch)
+        fs, rot = luts(name, seed, nl)
+        ids = S.lut_assignment(seed, batch, nl, "uniform", group=30 + gi)
+        mr, cts = fresh_cts(name, seed, batch, K, group=30 + gi)
+        ct_d = F.to_device_words(ps, cts)
+        out_d = torch_cuda.empty_like(ct_d)
+        groups.append((sid, ct_d, torch_cuda.tensor(ids, device="cuda"), out_d))
+        checks.append((ps, K, fs, rot, ids, mr, cts, sample))
+    ctx.bootstrap_mixed(groups)
+    ctx.sync()
+    for (sid, _, _, out_d), (ps, K, fs, rot, ids, mr, cts, sample) in zip(groups, checks):
+        got = F.to_host_words(ps, out_d).astype(np.uint64)
+        for c in sample:
+            ref = oracle.fdfb_bootstrap(ps, K, rot[ids[c]][0], rot[ids[c]][1], cts[c])
+            assert np.array_equal(got[c], ref), f"set {ps.name}, ct {c}"
+        if ps.w == 64:
+            dev_s = torch_cuda.tensor(K.s, device="cuda")
+            m_d = torch_cuda.empty(len(cts), dtype=torch_cuda.int32, device="cuda")
+            ctx.lwe_decrypt(sid, dev_s, out_d, m_d)
+            ctx.sync()
+            want = np.array([fs[i][m] for i, m in zip(ids, mr.m)])
+            assert np.array_equal(m_d.cpu().numpy(), want), ps.name
 
 
 # ------------------------------------------------------------- MLP layers --

@@ -475,3 +475,45 @@ def test_fdfb_100_7_and_tfhe_100_2(F, torch_cuda, ctx, OQ):
         ctx.lwe_decrypt(sid, s_d, out, m_d)
         ctx.sync()
         assert list(m_d.cpu().numpy()) == want, name
+
+
+class _Words:
+    """Key material for the oracle given as words (no key generation)."""
+
+    def __init__(self, bsk, pk, ksk):
+        self.bsk, self.pk, self.ksk = bsk, pk, ksk
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("base,n,count", [("FDFB-80-6", 3, 2), ("FDFB-80-7", 3, 1)])
+def test_full_geometry_matches_the_oracle(F, torch_cuda, ctx, OQ, base, n, count):
+    """The paper's sets at their full ring degree and digit counts (N = 2048,
+    l_g = 6 and N = 4096, l_g = 7 with its 14-row sums; l_pk = 5, l_boot = 6
+    sign rotations), with n reduced to 3 so that the schoolbook oracle finishes
+    in about a minute, and key words drawn uniformly mod Q (the algorithm is
+    defined for any words; the outputs do not decrypt).  Every layout variant
+    must give every intermediate (six sign LWEs, six packed RLWEs, PubMux, the
+    function rotation, the key switch mod Q) and the output bit for bit as the
+    oracle does."""
+    ps = dataclasses.replace(S.Q_PARAM_SETS[base], name=f"{base}-n{n}", n=n)
+    bsk, pk, ksk = S.q_uniform_key_words(ps, 31)
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, bsk, pk, ksk)
+    tables = S.q_lut_tables(ps, 31, 2)
+    assert [ctx.lut_setup(sid, f) for f in tables] == [0, 1]
+    rot = OQ.rotation_polys(ps, tables)
+    s = S.Stream(31, 7).bits(n)
+    mr = S.q_message_randomness(ps, 32, count)
+    cts = OQ.encrypt_messages(ps, s, mr)
+    ids = np.arange(count, dtype=np.int32) % 2
+    K = _Words(bsk, pk, ksk)
+    refs = [OQ.fdfb_bootstrap(ps, K, rot[i][0], rot[i][1], c, debug=True) for c, i in zip(cts, ids)]
+    cur, nvar, _ = ctx.variant_info(sid)
+    for v in range(nvar):
+        ctx.set_variant(sid, v)
+        out, dbg = run_q(F, torch_cuda, ctx, sid, ps, cts, ids)
+        for c, (o, d) in enumerate(refs):
+            for key in ("sgn", "cR", "accF", "cQ", "cKS"):
+                assert np.array_equal(dbg[key][c].reshape(d[key].shape), d[key]), f"{key}, variant {v}, ct {c}"
+            assert np.array_equal(out[c], o), f"output, variant {v}, ct {c}"
+    ctx.set_variant(sid, cur)
