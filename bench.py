@@ -77,6 +77,10 @@ PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7"
 # captured).  The transform-domain key streams from DRAM about once per wave,
 # so a launch over `items` CTAs moves bytes_per_wave * ceil(items / per_wave).
 KERNEL_TRAFFIC = {
+    # set C (large_t), variant 4, one CTA per SM: a 152-item capture (one wave)
+    ("C", 4): (785.489e6 + 3.880e6, 152, "ncu capture of a 152-item sign rotation (one wave), set C"),
+    # set D (target_n2048), variant 9, one CTA per SM: a 152-item capture
+    ("D", 9): (294.640e6 + 3.286e6, 152, "ncu capture of a 152-item sign rotation (one wave), set D"),
     # FDFB-80-6 sign rotation (variant 3, one CTA per SM): a 384-item capture
     # (three waves) read 1.2074 GB
     ("FDFB-80-6", 3): (1.2074e9 / 3, 152, "ncu capture of a 384-item sign rotation (3 waves), FDFB-80-6"),
