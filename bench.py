@@ -115,19 +115,23 @@ def br_algorithmic_ops(ps, batch: int):
             "key_products": f * 4 * ps.lg * ps.N * P}
 
 
-def opmix_roofline(ps, batch_items: int, br_ms: float, probe):
+def opmix_roofline(parts, br_ms: float, probe):
     """Roofline of the blind rotation against the measured rates of its own
     operations (probe): the time the method's butterflies and products need at
     the GPU's rate for each, T_alg = F / R_fwd + I / R_inv + M / R_mac, over
-    the measured time.  Forward butterflies take the faster of the two
+    the measured time.  `parts` lists (parameter set, rotations) -- several
+    sets for a mixed call.  Forward butterflies take the faster of the two
     forward forms the kernels use (Harvey's, and for q = 2^32 the lazy
     family's), so the peak is the higher one."""
-    ops = br_algorithmic_ops(ps, 1)
-    F, I, M = (ops[k] * batch_items for k in ("fwd_butterflies", "inv_butterflies", "key_products"))
-    r_fwd = probe["fwd_butterfly"]
-    if getattr(ps, "w", 64) == 32:
-        r_fwd = max(r_fwd, probe["lazy_fwd_butterfly"])
-    t_alg = F / (r_fwd * 1e12) + I / (probe["inv_butterfly"] * 1e12) + M / (probe["mac64"] * 1e12)
+    F = I = M = t_alg = 0.0
+    for ps, batch_items in parts:
+        ops = br_algorithmic_ops(ps, 1)
+        f, i, m = (ops[k] * batch_items for k in ("fwd_butterflies", "inv_butterflies", "key_products"))
+        r_fwd = probe["fwd_butterfly"]
+        if getattr(ps, "w", 64) == 32:
+            r_fwd = max(r_fwd, probe["lazy_fwd_butterfly"])
+        t_alg += f / (r_fwd * 1e12) + i / (probe["inv_butterfly"] * 1e12) + m / (probe["mac64"] * 1e12)
+        F, I, M = F + f, I + i, M + m
     total = F + I + M
     peak = total / t_alg / 1e12
     achieved = total / (br_ms / 1e3) / 1e12
@@ -139,7 +143,7 @@ def opmix_roofline(ps, batch_items: int, br_ms: float, probe):
             "ops_per_launch_set": {"fwd_butterflies": F, "inv_butterflies": I, "key_products": M}}
 
 
-def slot_roofline(ps, slots: float, br_ms: float):
+def slot_roofline(slots: float, br_ms: float):
     """The stricter derived roofline: the method's multiplier slots (every
     Shoup product 4 slots, every key product 2) against 152 SMs x 64 integer
     multiply lanes x 2.07 GHz, which leaves out the additions and minimums of
@@ -583,6 +587,11 @@ class Job:
             self.tuned[ps.name] = {"variant": v, "of": cnt, "coeffs_per_thread": cpt,
                                    "trial_blind_rotation_ms": [round(x, 3) for x in each],
                                    "chunks": ctx.get_chunks(sid)}
+        if ps.name in self.tuned:
+            pk_path, ksk_path = ctx.keyswitch_path(sid)
+            self.tuned[ps.name]["keyswitch"] = {
+                "packing": "tensor cores (tcgen05)" if pk_path else "CUDA cores",
+                "lwe": "tensor cores (tcgen05)" if ksk_path else "CUDA cores"}
         k = g.tables_per_input
         if k > 1:
             want = np.array([[fs[i][m] for i in row] for row, m in zip(ids_np, mr.m)]).reshape(-1)
@@ -662,12 +671,13 @@ class Job:
         return sum((0 if g.get("mode") == "tfhe" else br_algorithmic_slots(g["ps"], g["batch"] * g.get("lboot", 1)))
                    + br_algorithmic_slots(g["ps"], g["batch"] * g["k"]) for g in self.groups)
 
-    def br_items_per_step(self):
-        """Blind rotations per step (sign and function), each n CMux steps."""
+    def br_items_by_set(self):
+        """[(parameter set, blind rotations per step)]: sign and function
+        rotations, each n CMux steps."""
         if self.wl.mlp_layers:
-            return 2 * sum(self.mlp_batches)
-        return sum((0 if g.get("mode") == "tfhe" else g["batch"] * g.get("lboot", 1)) + g["batch"] * g["k"]
-                   for g in self.groups)
+            return [(self.groups[0]["ps"], 2 * sum(self.mlp_batches))]
+        return [(g["ps"], (0 if g.get("mode") == "tfhe" else g["batch"] * g.get("lboot", 1)) + g["batch"] * g["k"])
+                for g in self.groups]
 
     def io_bytes(self):
         if self.wl.mlp_layers:
@@ -754,12 +764,10 @@ def rooflines(job, prof, steps, probe):
     """The op-mix roofline (measured peak) and the slot roofline (derived) of
     the blind rotation launches of `steps` steps of `job`."""
     br_ms = prof["blind_rotate_union"][0]
-    items = job.br_items_per_step() * steps
-    ps0 = job.groups[0]["ps"]
     out = None
-    if probe and "error" not in probe and len(set(g["ps"].name for g in job.groups)) == 1:
-        out = opmix_roofline(ps0, items, br_ms, probe)
-    slots = slot_roofline(ps0, job.slots_per_step() * steps, br_ms)
+    if probe and "error" not in probe:
+        out = opmix_roofline([(ps, n * steps) for ps, n in job.br_items_by_set()], br_ms, probe)
+    slots = slot_roofline(job.slots_per_step() * steps, br_ms)
     if out is None:
         out = {"bound": "alu", "kernel": "blind_rotate_kernel", **slots}
         slots = None
@@ -921,6 +929,20 @@ def main():
                   "roofline": t_roof, "autotune": tjob.tuned,
                   "goal": "batched >= 10x plain and >= 0.5 of the roofline"}
 
+    # The mixed workload (rank 0): three parameter sets in one call per step.
+    mixed = None
+    if rank == 0 and args.target and args.workload == "large_t" and args.batch is None:
+        mjob = Job(torch, F, ctx, dev, args, rank, workload="mixed")
+        for _ in range(2):
+            mjob.step()
+        ctx.sync()
+        m_ok = mjob.decrypt_ok()
+        m_steps = 3
+        m_ms, m_prof = timed_steps(torch, ctx, mjob, stream, flush, m_steps, lambda: torch.cuda.synchronize())
+        mixed = {"workload": config_for(mjob, args)["workload"], "value": mjob.units * m_steps / (m_ms / 1e3),
+                 "unit": UNIT, "steps": m_steps, "ms_per_step": m_ms / m_steps, "decrypt_ok": m_ok,
+                 "roofline": rooflines(mjob, m_prof, m_steps, probe), "autotune": mjob.tuned}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -961,6 +983,8 @@ def main():
         line["batched_over_plain"] = value / plain["value"]
     if target:
         line["target_n2048"] = target
+    if mixed:
+        line["mixed"] = mixed
     if is_prime_set(ps0) and ps0.name in PAPER_MS_PER_BOOTSTRAP:
         ms = PAPER_MS_PER_BOOTSTRAP[ps0.name]
         line["paper_context"] = {"ms_per_bootstrap": ms, "bootstraps_per_s": 1e3 / ms,

@@ -402,8 +402,23 @@ int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launc
  * so the wait expires with no copy in flight: the call then latches
  * FDFB_ETIMEOUT (reported by fdfb_sync), computes garbage for the batch and
  * leaves the context usable.  It exists to exercise that error path without
- * any fault.  FDFB_EINVAL for unknown bits. */
+ * any fault.  Bit 1: every key switch runs as the CUDA-core contraction
+ * instead of on the tensor cores (same results; for comparisons).
+ * FDFB_EINVAL for unknown bits. */
 int fdfb_test_hooks(fdfb_ctx* ctx, int flags);
+
+/* Which contraction the set's key switches use (the paper has no
+ * counterpart): *pk_path for the packing key (BuildAcc), *ksk_path for the
+ * LWE key switch; 1 = fifth-generation tensor cores, 0 = CUDA cores (either
+ * pointer may be NULL).  Key switching (figure "Key switching algorithm and
+ * its setup") is the dense contraction out = [b, 0] - D K mod 2^w of the
+ * digit matrix D and the key K.  On the tensor cores it is computed exactly:
+ * the key words are split into balanced limbs of b bits and the digits are
+ * summed in chunks short enough that every fp32 partial sum is an integer
+ * below 2^24 in magnitude.  The limb form is built when keys are installed,
+ * for power-of-two sets whose gadget bases are at most 2^11 (wider digits,
+ * the prime-modulus sets and fdfb_bootstrap_noalloc use the CUDA cores). */
+int fdfb_keyswitch_path(fdfb_ctx* ctx, int set_id, int* pk_path, int* ksk_path);
 
 /* Waits for the stream and reports latched device-side errors (e.g.
  * FDFB_ETIMEOUT) and CUDA errors; clears the latch. */

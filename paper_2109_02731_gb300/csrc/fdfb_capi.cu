@@ -14,6 +14,7 @@
 
 #include "../../include/fdfb.h"
 #include "fdfb_host.hpp"
+#include "fdfb_ks_tc.hpp"
 #include "fdfb_ops.hpp"
 
 namespace fdfb {
@@ -111,6 +112,14 @@ struct SetState {
   uint64_t sgn_scale[8] = {0};  // L_boot^i round(Q / 2t) mod Q
   uint64_t delta_q = 0;      // round(Q / t)
   DevBuf pk_split, ksk_split;  // key-switch layouts: 32-bit halves as columns
+  // power-of-two sets: the key-switching keys in tensor-core limb form, and
+  // the f16 digit matrices of the key switches (rows of the largest batch)
+  TcKsKey tc_pk, tc_ksk;
+  DevBuf tc_digits;
+  ~SetState() {
+    tc_ks_release(tc_pk);
+    tc_ks_release(tc_ksk);
+  }
   size_t wbytes() const { return (size_t)w / 8; }
   Variant& base() { return *var[0]; }
   Variant& br() { return *var[cur]; }
@@ -237,6 +246,35 @@ int install_split_keys(SetState& st, cudaStream_t s) {
   return cuda_err(cudaGetLastError());
 }
 
+// Power-of-two sets: both key-switching keys in the tensor-core form (limbs
+// of f16, see fdfb_ks_tc.hpp).  A key whose digits are too wide for f16
+// (log2 B > 11) keeps the CUDA-core contraction.
+int install_tc_keys(SetState& st, cudaStream_t s) {
+  const fdfb_params& P = st.prm;
+  if (st.mq.Q) return FDFB_OK;
+  const int N = (int)P.N;
+  int rc = tc_ks_prepare(st.tc_pk, st.pk.p, st.w, N, (int)P.lpk, (int)P.log2Bpk, 2 * N, s);
+  if (rc != FDFB_OK && rc != FDFB_EINVAL) return rc;
+  rc = tc_ks_prepare(st.tc_ksk, st.ksk.p, st.w, N, (int)P.lks, (int)P.log2Bks, (int)P.n + 1, s);
+  if (rc != FDFB_OK && rc != FDFB_EINVAL) return rc;
+  return FDFB_OK;
+}
+
+// Bytes of one input row of the key switches' digit matrix (0 without a
+// tensor-core key).
+size_t tc_digit_row_bytes(const SetState& st) {
+  size_t r = 0;
+  if (st.tc_pk.ready) r = std::max(r, tc_ks_digits_bytes(st.tc_pk, 1));
+  if (st.tc_ksk.ready) r = std::max(r, tc_ks_digits_bytes(st.tc_ksk, 1));
+  return r;
+}
+
+int ensure_tc_digits(SetState& st, int64_t rows) {
+  const size_t rb = tc_digit_row_bytes(st);
+  if (rb == 0) return FDFB_OK;
+  return st.tc_digits.ensure((size_t)rows * rb);
+}
+
 // Pipeline intermediates for `batch` inputs with k tables each: per input the
 // sign LWE [N+1] and the packed RLWE [2N], per (input, table) the function
 // accumulator [2N] and the extracted LWE [N+1].
@@ -264,8 +302,12 @@ int ensure_scratch(SetState& st, int64_t batch, int k = 1) {
 // added atomically into a zeroed output.
 int launch_keyswitch(const fdfb_ctx* ctx, int w, const void* in, int64_t batch, int n_in,
                      const void* key, int ell, int log2B, int rt, int out_len, void* out,
-                     cudaStream_t s) {
+                     cudaStream_t s, const TcKsKey* tk = nullptr, void* digits = nullptr) {
   if (batch <= 0) return FDFB_OK;
+  // the tensor-core contraction when the key has a limb form and the caller
+  // gave digit scratch (fdfb_test_hooks bit 1 forces the CUDA cores)
+  if (tk && tk->ready && digits && !(ctx->test_flags & 2))
+    return tc_keyswitch(*tk, in, batch, rt, out, digits, ctx->d_err, s);
   const int64_t tiles = (int64_t)((out_len + KS_BN - 1) / KS_BN) * ((batch + KS_BM - 1) / KS_BM);
   const int kt = (n_in * ell + KS_BK - 1) / KS_BK;
   int64_t split = (2 * (int64_t)ctx->sms + tiles - 1) / tiles;
@@ -457,7 +499,8 @@ int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t
 // functions with the same input).  lut_ids and ct_out are [batch][k].
 int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
                  int64_t batch, int k, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
-                 void* fixed_scratch = nullptr, bool timed = true) {
+                 void* fixed_scratch = nullptr, bool timed = true, unsigned char* tc_digits = nullptr,
+                 bool use_tc = true) {
   if (batch < 0 || k < 1) return FDFB_EINVAL;
   if (batch == 0) return FDFB_OK;
   if (!ct_in || !lut_ids || !ct_out) return FDFB_EINVAL;
@@ -470,6 +513,16 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   const int64_t items = batch * k;
   if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, k));
   unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
+  // Digit matrices of the tensor-core key switches (a slice given by a
+  // chunked caller, else the set's buffer grown to this call's rows).
+  void* dig = nullptr;
+  if (use_tc && tc_digit_row_bytes(st) && !(ctx->test_flags & 2)) {
+    if (!tc_digits) {
+      FD_TRY(ensure_tc_digits(st, batch * k));
+      tc_digits = (unsigned char*)st.tc_digits.p;
+    }
+    dig = tc_digits;
+  }
   // The measurement hook creates CUDA events; the no-allocation path stays
   // free of any runtime object creation.
   fdfb_ctx* tctx = timed ? ctx : nullptr;
@@ -519,7 +572,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   {
     StageTimer tm(tctx, 1, s);
     FD_TRY(launch_keyswitch(ctx, st.w, sgn, batch, (int)N, st.pk.p, P.lpk, P.log2Bpk,
-                            trunc_bits(st.w, P.log2Bpk, P.lpk), (int)(2 * N), cR, s));
+                            trunc_bits(st.w, P.log2Bpk, P.lpk), (int)(2 * N), cR, s, &st.tc_pk, dig));
   }
   PubMuxParams pm{};
   pm.S = st.base().S;
@@ -556,7 +609,7 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   {
     StageTimer tm(tctx, 4, s);
     FD_TRY(launch_keyswitch(ctx, st.w, cQ, items, (int)N, st.ksk.p, P.lks, P.log2Bks,
-                            trunc_bits(st.w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
+                            trunc_bits(st.w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s, &st.tc_ksk, dig));
   }
   return FDFB_OK;
 }
@@ -595,6 +648,9 @@ int run_chunked(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* l
   if (batch * (int64_t)k > 0x7fffffff) return FDFB_EINVAL;
   FD_TRY(ensure_scratch(st, batch, k));
   FD_TRY(ensure_chunk_streams(ctx, chunks));
+  const bool tc = tc_digit_row_bytes(st) && !(ctx->test_flags & 2);
+  if (tc) FD_TRY(ensure_tc_digits(st, batch * k));
+  const size_t drow = tc_digit_row_bytes(st);
   const size_t wb = st.wbytes(), row = (size_t)(st.prm.n + 1) * wb;
   unsigned char* base = (unsigned char*)st.scratch.p;
   FD_CUDA(cudaEventRecord(ctx->chunk_events[0], s));
@@ -604,7 +660,8 @@ int run_chunked(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* l
     const int64_t b0 = batch * c / chunks, b1 = batch * (c + 1) / chunks;
     rc = run_pipeline(ctx, st, (const unsigned char*)ct_in + b0 * row, lut_ids + b0 * k, b1 - b0, k,
                       (unsigned char*)ct_out + b0 * k * row, nullptr, ctx->chunk_side[c],
-                      base + scratch_bytes(st, b0, k));
+                      base + scratch_bytes(st, b0, k), true,
+                      tc ? (unsigned char*)st.tc_digits.p + (size_t)b0 * k * drow : nullptr, tc);
   }
   // Join even after an error, so the caller's stream never runs ahead of
   // work already queued on the side streams.
@@ -1048,6 +1105,7 @@ int fdfb_keys_upload(fdfb_ctx* ctx, int set_id, const void* bsk, const void* pk,
   FD_CUDA(cudaMemcpyAsync(st->ksk.p, ksk, wk_ * wb, cudaMemcpyHostToDevice, s));
   FD_TRY(install_bsk_ntt(*st, s));
   if (st->mq.Q) FD_TRY(install_split_keys(*st, s));
+  FD_TRY(install_tc_keys(*st, s));
   FD_CUDA(cudaStreamSynchronize(s));
   st->keys = true;
   return FDFB_OK;
@@ -1149,6 +1207,7 @@ int fdfb_keys_generate(fdfb_ctx* ctx, int set_id, const fdfb_keygen_inputs* in, 
     FD_CUDA(cudaGetLastError());
   }
   FD_TRY(install_bsk_ntt(*st, s));
+  FD_TRY(install_tc_keys(*st, s));
   FD_CUDA(cudaStreamSynchronize(s));
   st->keys = true;
   return FDFB_OK;
@@ -1280,8 +1339,13 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
                                 (const uint32_t*)st->ksk_split.p, P.lks, P.log2Bks, (int)P.n + 1, sums,
                                 st->L + 1, (uint64_t*)ct_out, s));
     } else {
+      void* dig = nullptr;
+      if (tc_digit_row_bytes(*st) && !(ctx->test_flags & 2)) {
+        FD_TRY(ensure_tc_digits(*st, batch));
+        dig = st->tc_digits.p;
+      }
       FD_TRY(launch_keyswitch(ctx, st->w, cQ, batch, (int)N, st->ksk.p, P.lks, P.log2Bks,
-                              trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s));
+                              trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s, &st->tc_ksk, dig));
     }
   }
   return FDFB_OK;
@@ -1334,7 +1398,7 @@ int fdfb_bootstrap_noalloc(fdfb_ctx* ctx, int set_id, const void* ct_in, const i
   void* scratch = nullptr;
   FD_TRY(noalloc_scratch(ctx->device, &scratch));
   return run_pipeline(ctx, *st, ct_in, lut_ids, batch, 1, ct_out, nullptr, as_stream(cuda_stream),
-                      scratch, false);
+                      scratch, false, nullptr, false);
 }
 
 int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int32_t* lut_ids,
@@ -1368,6 +1432,7 @@ int fdfb_bootstrap_mixed(fdfb_ctx* ctx, int n_groups, const fdfb_group* groups, 
     for (int i = 0; i < n_groups; ++i)
       if (lane[i] == k && groups[i].batch > mx) mx = groups[i].batch;
     FD_TRY(ensure_scratch(*get_set(ctx, sets[k]), mx));
+    FD_TRY(ensure_tc_digits(*get_set(ctx, sets[k]), mx));
   }
   if (sets.size() == 1) {
     for (int i = 0; i < n_groups; ++i)
@@ -1420,8 +1485,22 @@ int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, 
     FD_CUDA(cudaStreamSynchronize(s));  // the sums buffer is released on return
     return FDFB_OK;
   }
+  void* dig = nullptr;
+  if (tc_digit_row_bytes(*st) && !(ctx->test_flags & 2)) {
+    FD_TRY(ensure_tc_digits(*st, batch));
+    dig = st->tc_digits.p;
+  }
   return launch_keyswitch(ctx, st->w, ct_in, batch, (int)P.N, st->ksk.p, P.lks, P.log2Bks,
-                          trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s);
+                          trunc_bits(st->w, P.log2Bks, P.lks), (int)P.n + 1, ct_out, s, &st->tc_ksk, dig);
+}
+
+int fdfb_keyswitch_path(fdfb_ctx* ctx, int set_id, int* pk_path, int* ksk_path) {
+  SetState* st = get_set(ctx, set_id);
+  if (!st) return FDFB_EINVAL;
+  const bool on = !(ctx->test_flags & 2);
+  if (pk_path) *pk_path = (on && st->tc_pk.ready) ? 1 : 0;
+  if (ksk_path) *ksk_path = (on && st->tc_ksk.ready) ? 1 : 0;
+  return FDFB_OK;
 }
 
 int fdfb_lwe_encrypt(fdfb_ctx* ctx, int set_id, const uint8_t* s, const void* a, const int64_t* e,
@@ -1646,7 +1725,7 @@ int fdfb_profile_read(fdfb_ctx* ctx, int stage, double* total_ms, int64_t* launc
 }
 
 int fdfb_test_hooks(fdfb_ctx* ctx, int flags) {
-  if (!ctx || (flags & ~1)) return FDFB_EINVAL;
+  if (!ctx || (flags & ~3)) return FDFB_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->test_flags = flags;
   return FDFB_OK;

@@ -29,7 +29,7 @@ SYMBOLS = [
     "fdfb_tfhe_poly_setup", "fdfb_tfhe_bootstrap",
     "fdfb_lwe_encrypt", "fdfb_lwe_decrypt", "fdfb_lwe_affine", "fdfb_autotune",
     "fdfb_set_variant", "fdfb_variant_info", "fdfb_set_chunks", "fdfb_get_chunks", "fdfb_profile_enable",
-    "fdfb_profile_read", "fdfb_test_hooks", "fdfb_sync", "fdfb_strerror",
+    "fdfb_profile_read", "fdfb_test_hooks", "fdfb_keyswitch_path", "fdfb_sync", "fdfb_strerror",
 ]
 
 
@@ -109,6 +109,7 @@ def load(build: bool = True) -> C.CDLL:
                 "fdfb_profile_enable": ([vp, i32], i32),
                 "fdfb_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], i32),
                 "fdfb_test_hooks": ([vp, i32], i32),
+                "fdfb_keyswitch_path": ([vp, i32, C.POINTER(i32), C.POINTER(i32)], i32),
                 "fdfb_sync": ([vp, vp], i32),
                 "fdfb_strerror": ([i32], C.c_char_p),
             }
@@ -383,8 +384,16 @@ class Context:
 
     def test_hooks(self, flags: int) -> None:
         """fdfb_test_hooks: bit 0 makes the staged-key blind rotation skip
-        its key copies so that its bounded wait expires (error-path tests)."""
+        its key copies so that its bounded wait expires (error-path tests);
+        bit 1 runs the key switches on the CUDA cores instead of the tensor
+        cores (comparisons)."""
         _check(self.L.fdfb_test_hooks(self.h, int(flags)), "fdfb_test_hooks")
+
+    def keyswitch_path(self, set_id: int):
+        """(packing key, LWE key): 1 = tensor cores, 0 = CUDA cores."""
+        a, b = C.c_int(), C.c_int()
+        _check(self.L.fdfb_keyswitch_path(self.h, set_id, C.byref(a), C.byref(b)), "fdfb_keyswitch_path")
+        return a.value, b.value
 
     def sync(self, stream=None) -> None:
         _check(self.L.fdfb_sync(self.h, _stream(stream)), "fdfb_sync")

@@ -55,6 +55,6 @@ def test_staged_key_wait_expires_and_context_recovers():
             assert torch.equal(again, ref), f"variant {v} after the hook"
         assert len(expired) == 1, f"variants whose staged-key wait expired: {expired}"
         with pytest.raises(F.FDFBError):
-            ctx.test_hooks(2)  # unknown bit
+            ctx.test_hooks(4)  # unknown bit
     finally:
         ctx.close()
