@@ -81,6 +81,9 @@ KERNEL_TRAFFIC = {
     ("C", 4): (785.489e6 + 3.880e6, 152, "ncu capture of a 152-item sign rotation (one wave), set C"),
     # set D (target_n2048), variant 9, one CTA per SM: a 152-item capture
     ("D", 9): (294.640e6 + 3.286e6, 152, "ncu capture of a 152-item sign rotation (one wave), set D"),
+    # set D, variant 6 (the autotuner's other near-tie): a 1000-item capture
+    # (seven waves) read 3.198 GB
+    ("D", 6): (3.19754e9 / 7, 152, "ncu capture of a 1000-item sign rotation (7 waves), set D"),
     # FDFB-80-6 sign rotation (variant 3, one CTA per SM): a 384-item capture
     # (three waves) read 1.2074 GB
     ("FDFB-80-6", 3): (1.2074e9 / 3, 152, "ncu capture of a 384-item sign rotation (3 waves), FDFB-80-6"),
