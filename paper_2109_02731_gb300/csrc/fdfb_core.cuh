@@ -398,32 +398,12 @@ FD_HD void inv_pass(uint32_t (&v)[1 << EL], int t, const uint2* tw, uint32_t p, 
 // The same passes on M polynomials held by the same threads at once: every
 // twiddle is loaded once for the M butterflies that use it, and the M
 // independent butterfly chains give the scheduler M times the parallelism.
-// T0: the inputs are gadget digits below the table's size and the first
-// stage's products w d mod p come from `tab` (tab[d] = w d mod p in [0, p),
-// w the stage's single twiddle): X + T and X - T + 2p stay below 4p (and
-// within the lazy family's bound), with no multiplication.
-template <int L, int EL, int PASS, int M, bool LZ = false, bool T0 = false>
-FD_HD void fwd_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z,
-                      const uint32_t* tab = nullptr) {
+template <int L, int EL, int PASS, int M, bool LZ = false>
+FD_HD void fwd_pass_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p, uint32_t z) {
   using Y = Layout<L, EL>;
   constexpr int F = Y::first(PASS), LEN = Y::len(PASS);
 #pragma unroll
   for (int s = F; s < F + LEN; ++s) {
-    if constexpr (T0 && PASS == 0) {
-      if (s == 0) {
-        constexpr int H = Y::E / 2;  // stage 0 pairs register r with r + E/2 (twiddle index 1)
-#pragma unroll
-        for (int r = 0; r < H; ++r)
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const uint32_t x = v[m][r];
-            const uint32_t tt = tab[v[m][r + H]];
-            v[m][r] = x + tt + z;
-            v[m][r + H] = x - tt + 2 * p;
-          }
-        continue;
-      }
-    }
     const int rb = Y::rbit(PASS, s);
 #pragma unroll
     for (int r = 0; r < Y::E; ++r) {

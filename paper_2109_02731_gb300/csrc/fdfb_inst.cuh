@@ -6,15 +6,13 @@ namespace fdfb {
 
 template <int L, int EL, int P, typename W, typename DT = uint16_t, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1, bool SGV = false, bool TK = false, bool MQ = false, bool T0 = false>
+          int KH = 1, bool SGV = false, bool TK = false, bool MQ = false>
 struct Inst {
   // SGV: also build the blind rotation with balanced digits (parameter sets
   // with signed_digits only use variants that have it)
   template <bool SG>
-  static constexpr auto kernel() {
-    return blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH, SG, TK, MQ, T0 && !SG>;
-  }
-  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ, T0>;
+  static constexpr auto kernel() { return blind_rotate_kernel<L, EL, P, W, DT, WIDE, MINB, M, LZ, PP, KH, SG, TK, MQ>; }
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ>;
   static constexpr int THREADS = Sh::THREADS;
   static size_t br_smem(int n, int lg, uint32_t* r1, uint32_t* ex) { return Sh::smem_bytes(n, lg, r1, ex); }
   static cudaError_t br_prepare(size_t smem) {
@@ -106,7 +104,7 @@ struct Inst {
     }
   }
   static Ops ops() {
-    return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, T0 ? kT0Log2 : (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
+    return Ops{L, EL, P, (int)(sizeof(W) * 8), THREADS, (int)(sizeof(DT) * 8), &br_smem, &br_prepare, &br,
                &pubmux, &rlwe_enc, &bsk_ntt, LZ ? 1 : 0, &br_blocks_per_sm, KH, SGV ? 1 : 0,
                MQ ? 1 : 0, MQ ? &pubmux_q : nullptr, MQ ? &rlwe_enc_q : nullptr};
   }

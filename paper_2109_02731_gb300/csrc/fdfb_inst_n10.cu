@@ -17,17 +17,15 @@ const Ops* ops_n10(int w, int variant) {
   static const Ops a5 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, false, 1, true>::ops();
   static const Ops a6 = Inst<10, 4, 2, uint32_t, uint8_t, false, br_blocks_for_regs(2 << (10 - 4), 128), 2, true>::ops();
   static const Ops a7 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, true, 1, true>::ops();
-  // a7 with the first forward stage's products from a table (digits below 2^10)
-  static const Ops a8 = Inst<10, 4, 2, uint32_t, uint16_t, true, br_blocks_for_regs(2 << (10 - 4), 168), 2, true, true, 1, false, false, false, true>::ops();
   static const Ops b0 = Inst<10, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (10 - 4)), 1, false, false, 1, true>::ops();
   static const Ops b1 = Inst<10, 5, 3, uint64_t, uint16_t>::ops();
   static const Ops b2 = Inst<10, 4, 3, uint64_t, uint16_t, true>::ops();
   static const Ops b3 = Inst<10, 4, 3, uint64_t, uint16_t, false, br_min_blocks(3 << (10 - 4)), 2>::ops();
   static const Ops b4 = Inst<10, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (10 - 4)), 2>::ops();
-  static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
+  static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
   static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4};
   if (variant < 0) return nullptr;
-  if (w == 32) return variant < 9 ? v32[variant] : nullptr;
+  if (w == 32) return variant < 8 ? v32[variant] : nullptr;
   if (w == 64) return variant < 5 ? v64[variant] : nullptr;
   return nullptr;
 }

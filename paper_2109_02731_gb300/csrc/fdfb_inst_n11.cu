@@ -27,14 +27,11 @@ const Ops* ops_n11(int w, int variant) {
   static const Ops b8 = Inst<11, 4, 2, uint64_t, uint16_t, false, 2, 1, false, false, 2>::ops();
   // b4 with each pair's key rows staged in shared memory by bulk copies
   static const Ops b9 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, false, 1, false, true>::ops();
-  // b9 and b6 with the first forward stage's products from a table (digits below 2^10)
-  static const Ops b10 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, false, 1, false, true, false, true>::ops();
-  static const Ops b11 = Inst<11, 4, 3, uint64_t, uint16_t, true, br_min_blocks(3 << (11 - 4)), 2, false, true, 1, false, false, false, true>::ops();
   static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4, &b5, &b6, &b7, &b8, &b9, &b10, &b11};
+  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4, &b5, &b6, &b7, &b8, &b9};
   if (variant < 0) return nullptr;
   if (w == 32) return variant < 6 ? v32[variant] : nullptr;
-  if (w == 64) return variant < 12 ? v64[variant] : nullptr;
+  if (w == 64) return variant < 10 ? v64[variant] : nullptr;
   return nullptr;
 }
 }  // namespace fdfb

@@ -23,14 +23,11 @@ const Ops* ops_n12(int w, int variant) {
   static const Ops b5 = Inst<12, 4, 2, uint64_t, uint16_t, false, 1, 2, false, false, 2, true>::ops();
   // split keys with single forward transforms (fewer live registers at 128 per thread)
   static const Ops b6 = Inst<12, 4, 2, uint64_t, uint16_t, false, 1, 1, false, false, 2>::ops();
-  // b6 and b5 with the first forward stage's products from a table (digits below 2^10)
-  static const Ops b7 = Inst<12, 4, 2, uint64_t, uint16_t, false, 1, 1, false, false, 2, false, false, false, true>::ops();
-  static const Ops b8 = Inst<12, 4, 2, uint64_t, uint16_t, false, 1, 2, false, false, 2, false, false, false, true>::ops();
   static const Ops* const v32[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4, &b5, &b6, &b7, &b8};
+  static const Ops* const v64[] = {&b0, &b1, &b2, &b3, &b4, &b5, &b6};
   if (variant < 0) return nullptr;
   if (w == 32) return variant < 6 ? v32[variant] : nullptr;
-  if (w == 64) return variant < 9 ? v64[variant] : nullptr;
+  if (w == 64) return variant < 7 ? v64[variant] : nullptr;
   return nullptr;
 }
 }  // namespace fdfb

@@ -143,14 +143,14 @@ __device__ __forceinline__ void exchange_m(uint32_t (&v)[M][1 << EL], int t, uin
   }
 }
 
-template <int L, int EL, int PASS, int M, int XW, bool LZ = false, bool PP = false, bool T0 = false>
+template <int L, int EL, int PASS, int M, int XW, bool LZ = false, bool PP = false>
 __device__ __forceinline__ void ntt_fwd_m(uint32_t (&v)[M][1 << EL], int t, const uint2* tw, uint32_t p,
-                                          uint32_t* xb, int bar, uint32_t z, const uint32_t* tab = nullptr) {
+                                          uint32_t* xb, int bar, uint32_t z) {
   using Y = Layout<L, EL>;
   if constexpr (PASS < Y::K) {
     if constexpr (PASS > 0) exchange_m<L, EL, PASS - 1, PASS, M, XW, PP>(v, t, xb, bar);
-    fwd_pass_m<L, EL, PASS, M, LZ, T0>(v, t, tw, p, z, tab);
-    ntt_fwd_m<L, EL, PASS + 1, M, XW, LZ, PP, T0>(v, t, tw, p, xb, bar, z, tab);
+    fwd_pass_m<L, EL, PASS, M, LZ>(v, t, tw, p, z);
+    ntt_fwd_m<L, EL, PASS + 1, M, XW, LZ, PP>(v, t, tw, p, xb, bar, z);
   }
 }
 
@@ -250,12 +250,8 @@ struct BRParams {
   uint64_t sgn_scale[8];
 };
 
-// Digits below 2^kT0Log2 have a first-stage product table (variants built
-// with T0).
-constexpr int kT0Log2 = 10;
-
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1,
-          bool TK = false, bool MQ = false, bool T0 = false>
+          bool TK = false, bool MQ = false>
 struct BRShape {
   using Y = Layout<L, EL>;
   static constexpr int N = Y::N, E = Y::E, G = Y::G, THREADS = P * G;
@@ -269,10 +265,8 @@ struct BRShape {
     size_t r1 = dig > stage ? dig : stage;
     *r1_off = (uint32_t)(acc + an);
     *exch_off = (uint32_t)(acc + an + r1);
-    return acc + an + r1 + (size_t)P * group_words() * 4 + kstage_bytes() + tab_bytes();
+    return acc + an + r1 + (size_t)P * group_words() * 4 + kstage_bytes();
   }
-  // T0: per group the first forward stage's products w d mod p, d < 2^kT0Log2
-  static constexpr size_t tab_bytes() { return T0 ? (size_t)P * ((size_t)1 << kT0Log2) * 4 : 0; }
   // TK: per group, the key rows of one pair (2M rows x N words), then one
   // mbarrier per group
   static constexpr size_t kpair_words() { return (size_t)2 * M * KH * N; }
@@ -345,11 +339,9 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // MQ: prime modulus Q (Table 1): d = acc X^{-a} - acc mod Q, exact digits
 // (l log2 B >= log2 Q), the products lifted to the exact integer and reduced
 // mod Q; the input ciphertext is already modulo 2N.
-// T0: the digit polynomials' first forward stage reads its products from a
-// per-group table in shared memory (digits below 2^kT0Log2, unsigned).
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
-          int KH = 1, bool SG = false, bool TK = false, bool MQ = false, bool T0 = false>
+          int KH = 1, bool SG = false, bool TK = false, bool MQ = false>
 __global__ void __launch_bounds__(P * (1 << (L - EL)), MINB)
 blind_rotate_kernel(const BRParams prm) {
   using Y = Layout<L, EL>;
@@ -359,7 +351,6 @@ blind_rotate_kernel(const BRParams prm) {
   static_assert(KH == 1 || (KH == 2 && P == 2 && !WIDE && sizeof(W) == 8),
                 "split keys: q = 2^64, two primes, per-product reduction");
   static_assert(!MQ || (sizeof(W) == 8 && !SG && !LZ), "prime modulus: 64-bit words, unsigned digits");
-  static_assert(!T0 || !SG, "the product table is indexed by unsigned digits");
   extern __shared__ __align__(16) unsigned char smem[];
   W* acc = reinterpret_cast<W*>(smem);                                     // [2][N]
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * N * sizeof(W));     // [n]
@@ -406,8 +397,8 @@ blind_rotate_kernel(const BRParams prm) {
   }
   // TK: the staged pair of key rows of each group, and its mbarrier
   constexpr uint32_t kPairWords = (uint32_t)(2 * M * KH * N);
-  using ShT = BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ, T0>;
-  uint32_t* kst = reinterpret_cast<uint32_t*>(smem + prm.smem_exch + (size_t)P * ShT::group_words() * 4);
+  uint32_t* kst = reinterpret_cast<uint32_t*>(
+      smem + prm.smem_exch + (size_t)P * BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ>::group_words() * 4);
   uint64_t* kmb = reinterpret_cast<uint64_t*>(kst + (size_t)P * kPairWords) + (tid / G);
   kst += (size_t)(tid / G) * kPairWords;
   if constexpr (TK) {
@@ -424,16 +415,8 @@ blind_rotate_kernel(const BRParams prm) {
   const uint32_t z = prm.S.zero;
   const uint2* twf = prm.S.tw_fwd + (size_t)grp * N;
   const uint2* twi = prm.S.tw_inv + (size_t)grp * N;
-  // T0: this group's table of w d mod p (w = the first stage's twiddle), after
-  // the staged key rows; read only after the digit step's barrier
-  uint32_t* t0tab = reinterpret_cast<uint32_t*>(smem + prm.smem_exch + (size_t)P * ShT::group_words() * 4 +
-                                                ShT::kstage_bytes()) + (size_t)grp * ((size_t)1 << kT0Log2);
-  if constexpr (T0) {
-    const uint2 w1 = twf[1];
-    for (int d = t; d < (1 << kT0Log2); d += G) t0tab[d] = csub(mul_shoup((uint32_t)d, w1.x, w1.y, p), p);
-  }
   static_assert(!PP || M == 2, "ping-pong buffers are for paired transforms");
-  using Sh = ShT;
+  using Sh = BRShape<L, EL, P, W, DT, M, PP, KH, TK, MQ>;
   // forward transforms: M polynomials per pass; inverse transforms: both
   // columns together whenever the forward is paired or the key is split
   constexpr int MI = (M == 2 || KH == 2) ? 2 : 1;
@@ -540,7 +523,7 @@ blind_rotate_kernel(const BRParams prm) {
             v[m][k] = dv;
           }
         }
-      ntt_fwd_m<L, EL, 0, M, XW, LZ, PP, T0>(v, t, twf, p, xb, bar, z, t0tab);
+      ntt_fwd_m<L, EL, 0, M, XW, LZ, PP>(v, t, twf, p, xb, bar, z);
       if constexpr (WIDE && !LZ) {
 #pragma unroll
         for (int m = 0; m < M; ++m)
