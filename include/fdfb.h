@@ -415,9 +415,12 @@ int fdfb_test_hooks(fdfb_ctx* ctx, int flags);
  * digit matrix D and the key K.  On the tensor cores it is computed exactly:
  * the key words are split into balanced limbs of b bits and the digits are
  * summed in chunks short enough that every fp32 partial sum is an integer
- * below 2^24 in magnitude.  The limb form is built when keys are installed,
- * for power-of-two sets whose gadget bases are at most 2^11 (wider digits,
- * the prime-modulus sets and fdfb_bootstrap_noalloc use the CUDA cores). */
+ * below 2^24 in magnitude.  On the prime-modulus sets the tensor cores
+ * compute the exact integer sums (key residues as limbs covering 65 bits,
+ * digits above 11 bits in two halves), reduced mod Q afterwards.  The limb
+ * form is built when keys are installed, for gadget bases up to 2^11 (2^22
+ * on the prime-modulus sets); wider digits and fdfb_bootstrap_noalloc use
+ * the CUDA cores. */
 int fdfb_keyswitch_path(fdfb_ctx* ctx, int set_id, int* pk_path, int* ksk_path);
 
 /* Waits for the stream and reports latched device-side errors (e.g.

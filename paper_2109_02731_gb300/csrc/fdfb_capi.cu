@@ -251,20 +251,21 @@ int install_split_keys(SetState& st, cudaStream_t s) {
 // (log2 B > 11) keeps the CUDA-core contraction.
 int install_tc_keys(SetState& st, cudaStream_t s) {
   const fdfb_params& P = st.prm;
-  if (st.mq.Q) return FDFB_OK;
   const int N = (int)P.N;
-  int rc = tc_ks_prepare(st.tc_pk, st.pk.p, st.w, N, (int)P.lpk, (int)P.log2Bpk, 2 * N, s);
+  const bool exact = st.mq.Q != 0;  // prime-modulus sets: exact integer sums, reduced mod Q afterwards
+  int rc = tc_ks_prepare(st.tc_pk, st.pk.p, st.w, N, (int)P.lpk, (int)P.log2Bpk, 2 * N, s, exact);
   if (rc != FDFB_OK && rc != FDFB_EINVAL) return rc;
-  rc = tc_ks_prepare(st.tc_ksk, st.ksk.p, st.w, N, (int)P.lks, (int)P.log2Bks, (int)P.n + 1, s);
+  rc = tc_ks_prepare(st.tc_ksk, st.ksk.p, st.w, N, (int)P.lks, (int)P.log2Bks, (int)P.n + 1, s, exact);
   if (rc != FDFB_OK && rc != FDFB_EINVAL) return rc;
   return FDFB_OK;
 }
 
-// Bytes of one input row of the key switches' digit matrix (0 without a
-// tensor-core key).
+// Bytes of the key switches' digit matrices per input of a pipeline (0
+// without a tensor-core key): the packing key switch reads l_boot sign LWEs
+// per input on the prime-modulus sets, one on the others.
 size_t tc_digit_row_bytes(const SetState& st) {
   size_t r = 0;
-  if (st.tc_pk.ready) r = std::max(r, tc_ks_digits_bytes(st.tc_pk, 1));
+  if (st.tc_pk.ready) r = std::max(r, (size_t)st.lboot * tc_ks_digits_bytes(st.tc_pk, 1));
   if (st.tc_ksk.ready) r = std::max(r, tc_ks_digits_bytes(st.tc_ksk, 1));
   return r;
 }
@@ -334,8 +335,17 @@ int launch_keyswitch(const fdfb_ctx* ctx, int w, const void* in, int64_t batch, 
 // out = ([b, 0..] - sums) mod Q, and with logq > 0 ModSwitch(Q -> 2^logq).
 int launch_keyswitch_q(const fdfb_ctx* ctx, const SetState& st, const uint64_t* in, int64_t batch,
                        int n_in, const uint32_t* key_split, int ell, int log2B, int out_len,
-                       uint64_t* sums, int logq, uint64_t* out, cudaStream_t s) {
+                       uint64_t* sums, int logq, uint64_t* out, cudaStream_t s, const TcKsKey* tk = nullptr,
+                       void* digits = nullptr) {
   if (batch <= 0) return FDFB_OK;
+  if (tk && tk->ready && digits && !(ctx->test_flags & 2)) {
+    // the exact sums on the tensor cores, in the layout the reduction reads
+    FD_TRY(tc_keyswitch(*tk, in, batch, 0, sums, digits, ctx->d_err, s));
+    const int64_t total = batch * out_len;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->sms);
+    ks_finalize_q_kernel<<<blocks, 256, 0, s>>>(in, n_in, batch, sums, out_len, st.mq, logq, out);
+    return cuda_err(cudaGetLastError());
+  }
   const int cols = 2 * out_len;
   const int64_t tiles = (int64_t)((cols + KS_BN - 1) / KS_BN) * ((batch + KS_BM - 1) / KS_BM);
   const int kt = (n_in * ell + KS_BK - 1) / KS_BK;
@@ -398,7 +408,7 @@ struct StageTimer {
 // rotation, SampleExtract, KeySwitch(ksK) and ModSwitch(Q -> q = 2N).
 int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* lut_ids,
                    int64_t batch, int k, void* ct_out, const fdfb_debug_bufs* dbg, cudaStream_t s,
-                   void* fixed_scratch, bool timed) {
+                   void* fixed_scratch, bool timed, void* dig) {
   if (k != 1) return FDFB_EINVAL;
   const fdfb_params& P = st.prm;
   const size_t N = P.N, n = P.n, lb = st.lboot;
@@ -445,7 +455,7 @@ int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t
   {
     StageTimer tm(tctx, 1, s);
     FD_TRY(launch_keyswitch_q(ctx, st, sgn, items, (int)N, (const uint32_t*)st.pk_split.p, P.lpk,
-                              P.log2Bpk, (int)(2 * N), sums_pk, 0, cR, s));
+                              P.log2Bpk, (int)(2 * N), sums_pk, 0, cR, s, &st.tc_pk, dig));
   }
   PubMuxQParams pm{};
   pm.S = st.base().S;
@@ -478,7 +488,8 @@ int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t
   {
     StageTimer tm(tctx, 4, s);
     FD_TRY(launch_keyswitch_q(ctx, st, cQ, batch, (int)N, (const uint32_t*)st.ksk_split.p, P.lks,
-                              P.log2Bks, (int)n + 1, sums_ks, (int)st.L + 1, (uint64_t*)ct_out, s));
+                              P.log2Bks, (int)n + 1, sums_ks, (int)st.L + 1, (uint64_t*)ct_out, s, &st.tc_ksk,
+                              dig));
     if (dbg && dbg->cKS) {
       const int64_t total = batch * (int64_t)(n + 1);
       const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->sms);
@@ -507,14 +518,8 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
   if (!st.keys) return FDFB_ENOKEYS;
   if (st.n_luts == 0) return FDFB_EBADLUT;
   if (batch * (int64_t)k > 0x7fffffff) return FDFB_EINVAL;
-  if (st.mq.Q) return run_pipeline_q(ctx, st, ct_in, lut_ids, batch, k, ct_out, dbg, s, fixed_scratch, timed);
-  const fdfb_params& P = st.prm;
-  const size_t N = P.N, wb = st.wbytes();
-  const int64_t items = batch * k;
-  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, k));
-  unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
   // Digit matrices of the tensor-core key switches (a slice given by a
-  // chunked caller, else the set's buffer grown to this call's rows).
+  // chunked caller, else the set's buffer grown to this call's inputs).
   void* dig = nullptr;
   if (use_tc && tc_digit_row_bytes(st) && !(ctx->test_flags & 2)) {
     if (!tc_digits) {
@@ -523,6 +528,12 @@ int run_pipeline(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t* 
     }
     dig = tc_digits;
   }
+  if (st.mq.Q) return run_pipeline_q(ctx, st, ct_in, lut_ids, batch, k, ct_out, dbg, s, fixed_scratch, timed, dig);
+  const fdfb_params& P = st.prm;
+  const size_t N = P.N, wb = st.wbytes();
+  const int64_t items = batch * k;
+  if (!fixed_scratch) FD_TRY(ensure_scratch(st, batch, k));
+  unsigned char* base = fixed_scratch ? (unsigned char*)fixed_scratch : (unsigned char*)st.scratch.p;
   // The measurement hook creates CUDA events; the no-allocation path stays
   // free of any runtime object creation.
   fdfb_ctx* tctx = timed ? ctx : nullptr;
@@ -920,6 +931,7 @@ int keys_generate_q(fdfb_ctx* ctx, SetState* st, const fdfb_keygen_inputs* in, c
   }
   FD_TRY(install_bsk_ntt(*st, s));
   FD_TRY(install_split_keys(*st, s));
+  FD_TRY(install_tc_keys(*st, s));
   FD_CUDA(cudaStreamSynchronize(s));
   st->keys = true;
   return FDFB_OK;
@@ -1335,9 +1347,14 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
     if (st->mq.Q) {
       // exact half sums after cQ, then mod Q and ModSwitch(Q -> 2N)
       uint64_t* sums = (uint64_t*)((unsigned char*)cQ + (size_t)batch * (N + 1) * wb);
+      void* dig = nullptr;
+      if (tc_digit_row_bytes(*st) && !(ctx->test_flags & 2)) {
+        FD_TRY(ensure_tc_digits(*st, batch));
+        dig = st->tc_digits.p;
+      }
       FD_TRY(launch_keyswitch_q(ctx, *st, (const uint64_t*)cQ, batch, (int)N,
                                 (const uint32_t*)st->ksk_split.p, P.lks, P.log2Bks, (int)P.n + 1, sums,
-                                st->L + 1, (uint64_t*)ct_out, s));
+                                st->L + 1, (uint64_t*)ct_out, s, &st->tc_ksk, dig));
     } else {
       void* dig = nullptr;
       if (tc_digit_row_bytes(*st) && !(ctx->test_flags & 2)) {
@@ -1479,9 +1496,14 @@ int fdfb_keyswitch(fdfb_ctx* ctx, int set_id, const void* ct_in, int64_t batch, 
   if (st->mq.Q) {
     DevBuf sums;
     FD_TRY(sums.ensure((size_t)batch * 2 * (P.n + 1) * 8));
+    void* dig = nullptr;
+    if (tc_digit_row_bytes(*st) && !(ctx->test_flags & 2)) {
+      FD_TRY(ensure_tc_digits(*st, batch));
+      dig = st->tc_digits.p;
+    }
     FD_TRY(launch_keyswitch_q(ctx, *st, (const uint64_t*)ct_in, batch, (int)P.N,
                               (const uint32_t*)st->ksk_split.p, P.lks, P.log2Bks, (int)P.n + 1,
-                              (uint64_t*)sums.p, 0, (uint64_t*)ct_out, s));
+                              (uint64_t*)sums.p, 0, (uint64_t*)ct_out, s, &st->tc_ksk, dig));
     FD_CUDA(cudaStreamSynchronize(s));  // the sums buffer is released on return
     return FDFB_OK;
   }

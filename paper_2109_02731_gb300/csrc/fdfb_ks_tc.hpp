@@ -23,34 +23,50 @@
 namespace fdfb {
 
 // Tensor-core form of one key-switching key.
+//
+// Two kinds.  Power-of-two sets (exact = false): the words are residues mod
+// 2^w and the result is [b, 0] - D K mod 2^w.  Prime-modulus sets (exact =
+// true): the words are residues mod Q < 2^63 and the kernel writes the exact
+// non-negative integer S = D K (below 2^96) as the two 64-bit words S mod
+// 2^32 and S >> 32, the layout of the CUDA-core contraction's sums, for the
+// reduction mod Q that follows; digits of more than 11 bits are split into
+// two halves below 2^h and 2^(log2B - h) (D = D_lo + 2^h D_hi), and the limbs
+// cover 65 bits so that their sum is the key word as an integer, not only
+// modulo a power of two.
 struct TcKsKey {
   void* limbs = nullptr;   // device [S][cols][K] f16
   size_t bytes = 0;
-  CUtensorMap tmap;        // 3-D map of `limbs`: {K, cols, S}, 64 x 128 x 1 boxes, 128-byte swizzle
+  CUtensorMap tmap;        // 3-D map of `limbs`: {K, cols, S}, 64 x BN x 1 boxes, 128-byte swizzle
   int S = 0, b = 0, kappa = 0;
   int K = 0, cols = 0, w = 0, ell = 0, log2B = 0, n_in = 0;
+  bool exact = false;      // prime-modulus form
+  int halves = 1, h = 0;   // digit halves (exact form, log2B > 11) and the low half's bits
   bool ready = false;
 };
 
-// Limb width, limb count and chunk length for digits below B = 2^log2B,
-// K = n_in * ell terms and w-bit words (host).  Returns false if no split
-// keeps the chunks at least 64 terms long.
-bool tc_ks_split(int log2B, int w, int n_in, int ell, int* b, int* S, int* kappa);
+// Limb width, limb count and chunk length for digits below 2^dbits, K =
+// n_in * ell terms and limbs covering `span` bits (host).  Returns false if
+// no split keeps the chunks at least 64 terms long.
+bool tc_ks_split(int dbits, int span, int n_in, int ell, int* b, int* S, int* kappa);
 
 // Builds the limb form of a key given on the device in canonical layout
 // [K][cols] words (K = n_in ell) and its tensor map; synchronises `s`.
+// exact selects the prime-modulus form (w = 64, words in [0, Q), Q < 2^63).
 // FDFB_ENOMEM / FDFB_ECUDA / FDFB_EINVAL on failure (then k.ready is false).
-int tc_ks_prepare(TcKsKey& k, const void* key, int w, int n_in, int ell, int log2B, int cols, cudaStream_t s);
+int tc_ks_prepare(TcKsKey& k, const void* key, int w, int n_in, int ell, int log2B, int cols, cudaStream_t s,
+                  bool exact = false);
 void tc_ks_release(TcKsKey& k);
 
-// Bytes of the digit matrix a call on `batch` rows needs (f16 [batch][K]).
+// Bytes of the digit matrix a call on `batch` rows needs (f16 [halves][batch][K]).
 size_t tc_ks_digits_bytes(const TcKsKey& k, int64_t batch);
 
-// out[m] = KeySwitch(ct[m]) for m < batch: ct device [batch][n_in + 1] words,
-// out device [batch][cols] words, digits device scratch of
-// tc_ks_digits_bytes(k, batch) bytes, rtrunc the decomposition's rounding
-// bits (w - l log2 B when positive).  A bounded device-side wait that
-// expires latches FDFB_ETIMEOUT in *err.  Stream ordered.
+// KeySwitch of ct[m] for m < batch: ct device [batch][n_in + 1] words,
+// digits device scratch of tc_ks_digits_bytes(k, batch) bytes, rtrunc the
+// decomposition's rounding bits (w - l log2 B when positive; 0 for the exact
+// form).  Power-of-two form: out device [batch][cols] words, the key-switched
+// samples.  Exact form: out device [batch][2 cols] uint64, the sums (S mod
+// 2^32 at [m][c], S >> 32 at [m][cols + c]).  A bounded device-side wait
+// that expires latches FDFB_ETIMEOUT in *err.  Stream ordered.
 int tc_keyswitch(const TcKsKey& k, const void* ct, int64_t batch, int rtrunc, void* out, void* digits,
                  int* err, cudaStream_t s);
 

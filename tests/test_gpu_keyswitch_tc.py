@@ -103,3 +103,40 @@ def test_partial_sums_at_their_bound(env, oracle):
                 want = ref.copy()
                 want[0] = (int(ref[0]) + int(x[i, 0]) - int(x[0, 0])) % (1 << w)
                 assert np.array_equal(y[i], want), (b, negative, i)
+
+
+@pytest.mark.parametrize("base,n", [("QZ", 24), ("FDFB-80-6", 16), ("FDFB-100-6", 8)])
+def test_prime_set_keyswitch_on_tensor_cores(env, base, n):
+    """The prime-modulus form: the tensor cores compute the exact integer sums
+    of digit times key residue (limbs covering 65 bits), reduced mod Q after.
+    Random residues, and rows whose digits and key words are all Q - 1 (the
+    largest sums there are), against the oracle and the CUDA-core path.  The
+    packing keys of these sets have 13-bit digits (split into two halves);
+    FDFB-100-6's LWE key has 62 binary digits."""
+    import oracle.prime_q as OQ
+    torch, F, ctx = env
+    ps = dataclasses.replace(S.Q_PARAM_SETS[base], name=f"{base}-ks{n}", n=n)
+    Q, N = ps.Q, ps.N
+    bsk, pk, ksk = S.q_uniform_key_words(ps, 41)
+    ksk[:N // 2] = Q - 1
+    sid = ctx.register(ps)
+    ctx.keys_upload(sid, bsk, pk, ksk)
+    assert ctx.keyswitch_path(sid) == (1, 1)
+    batch = 70
+    x = S.Stream(42, 1).raw(batch * (N + 1)).reshape(batch, N + 1) % np.uint64(Q)
+    x[:3] = Q - 1
+    x_d = F.to_device_words(ps, x)
+    y_d = torch.empty((batch, n + 1), dtype=torch.int64, device="cuda")
+    ctx.keyswitch(sid, x_d, y_d)
+    ctx.sync()
+    y = F.to_host_words(ps, y_d).astype(np.uint64)
+    for i in (0, 2, 3, batch - 1):
+        assert np.array_equal(y[i], OQ.keyswitch(Q, ps.log2Bks, ps.lks, ksk, x[i])), i
+    ctx.test_hooks(2)
+    try:
+        z_d = torch.empty_like(y_d)
+        ctx.keyswitch(sid, x_d, z_d)
+        ctx.sync()
+    finally:
+        ctx.test_hooks(0)
+    assert torch.equal(z_d, y_d)
