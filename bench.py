@@ -67,7 +67,8 @@ def is_prime_set(ps) -> bool:
 # bootstrap, not parallelised, on a 60-core Xeon Cascade Lake VM with a
 # 64-bit prime-modulus NTT): context for the prime-modulus workloads.
 PAPER_MS_PER_BOOTSTRAP = {"FDFB-80-6": 3655.0, "FDFB-100-6": 4838.0, "FDFB-80-7": 9278.0,
-                          "FDFB-100-7": 13781.0, "TFHE-100-7": 7757.0, "TFHE-80-2": 306.0,
+                          "FDFB-100-7": 13781.0, "FDFB-80-8": 33117.0, "FDFB-100-8": 45266.0,
+                          "TFHE-100-7": 7757.0, "TFHE-80-2": 306.0,
                           "TFHE-100-2": 321.0}
 
 
@@ -138,7 +139,8 @@ def opmix_roofline(parts, br_ms: float, probe):
     total = F + I + M
     peak = total / t_alg / 1e12
     achieved = total / (br_ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak,
+    kernel = "blind_rotate_n13_kernel" if any(ps.N == 8192 for ps, _ in parts) else "blind_rotate_kernel"
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
             "unit": "T modular ops/s (butterflies + key products)", "frac": achieved / peak,
             "peak_source": "measured in this run: probe of the kernels' own forward and inverse butterflies "
                            "and 32x32->64 key products at full occupancy (probe/int_pipe.cu), combined in the "

@@ -105,7 +105,9 @@ typedef struct {
    *     representation, Section "Extending the Arithmetic", need not divide
    *     2N): Delta_q = round(2N / t), and fdfb_lwe_decrypt returns
    *     round(t (b - <a, s>) / 2N) mod t;
-   *   - N is 256, 1024, 2048 or 4096; signed_digits and t_out must be 0;
+   *   - N is 256, 1024, 2048, 4096 or 8192 (Table 1's FDFB:80:8 and
+   *     FDFB:100:8; at N = 8192 the blind rotation keeps the accumulator in
+   *     shared memory and needs n <= 1536); signed_digits and t_out must be 0;
    *     fdfb_bootstrap_multi (k > 1) and fdfb_lwe_affine are not available
    *     (FDFB_EINVAL);
    *   - the TFHE bootstrap takes polynomials of residues mod Q and, like the
@@ -134,7 +136,7 @@ int fdfb_destroy(fdfb_ctx* ctx);
 
 /* Registers a parameter set; *set_id_out receives its id.  Fails with
  * FDFB_EINVAL for unsupported shapes (prime-modulus sets: the rules given
- * with fdfb_params.Q, lg <= 7): N not in {256, 512, 1024, 2048, 4096},
+ * with fdfb_params.Q, lg <= 7, N up to 8192): N not in {256, 512, 1024, 2048, 4096},
  * n > 4096, lg > 4, signed_digits > 1, or a negacyclic product whose exact
  * value could exceed what the 30-bit primes lift exactly (2l N (B-1) q/2 for
  * the blind rotation, N (t-1) q for PubMux).  Registration also builds the

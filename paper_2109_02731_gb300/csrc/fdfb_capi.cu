@@ -28,6 +28,7 @@ const Ops* ops_q_n8(int variant);
 const Ops* ops_q_n10(int variant);
 const Ops* ops_q_n11(int variant);
 const Ops* ops_q_n12(int variant);
+const Ops* ops_q_n13(int variant);
 
 const Ops* find_ops_q(int L, int variant) {
   switch (L) {
@@ -35,6 +36,7 @@ const Ops* find_ops_q(int L, int variant) {
     case 10: return ops_q_n10(variant);
     case 11: return ops_q_n11(variant);
     case 12: return ops_q_n12(variant);
+    case 13: return ops_q_n13(variant);
     default: return nullptr;
   }
 }
@@ -281,13 +283,29 @@ int ensure_tc_digits(SetState& st, int64_t rows) {
 // accumulator [2N] and the extracted LWE [N+1].
 // Prime-modulus sets (k = 1): per input lboot sign LWEs [N+1], their raw
 // packing key-switch sums [4N] and packed RLWEs [2N], then accF [2N], cQ
-// [N+1] and the raw LWE key-switch sums [2(n+1)], all 64-bit words.
+// [N+1] and the raw LWE key-switch sums [2(n+1)], all 64-bit words; at N =
+// 2^13 then per sign item the blind rotation's half results (n13_half_words).
+size_t mq_scratch_words(const SetState& st, int64_t batch) {
+  const size_t N = st.prm.N, lb = st.lboot, n = st.prm.n;
+  return (size_t)batch * (lb * ((N + 1) + 4 * N + 2 * N) + 2 * N + (N + 1) + 2 * (n + 1));
+}
+// 32-bit words of one item's BRParams::half_y at N = 2^13 ([P][2][2][4096]
+// for the largest prime count of the set's variants), else 0.
+size_t n13_half_words(const SetState& st) {
+  if (st.L != 13) return 0;
+  int P = 0;
+  for (const auto& v : st.var) P = std::max(P, v->ops->P);
+  return (size_t)P * 4 * 4096;
+}
+// The half-result region of a prime-modulus scratch area laid out for `batch`
+// inputs (after the 64-bit words above), or nullptr below N = 2^13.
+uint32_t* n13_half_region(const SetState& st, void* base, int64_t batch) {
+  if (!n13_half_words(st)) return nullptr;
+  return (uint32_t*)((unsigned char*)base + mq_scratch_words(st, batch) * 8);
+}
 size_t scratch_bytes(const SetState& st, int64_t batch, int k) {
   const size_t N = st.prm.N;
-  if (st.mq.Q) {
-    const size_t lb = st.lboot, n = st.prm.n;
-    return (size_t)batch * (lb * ((N + 1) + 4 * N + 2 * N) + 2 * N + (N + 1) + 2 * (n + 1)) * 8;
-  }
+  if (st.mq.Q) return mq_scratch_words(st, batch) * 8 + (size_t)batch * st.lboot * n13_half_words(st) * 4;
   return ((size_t)batch * ((N + 1) + 2 * N) + (size_t)batch * k * (2 * N + (N + 1))) * st.wbytes();
 }
 
@@ -448,6 +466,7 @@ int run_pipeline_q(fdfb_ctx* ctx, SetState& st, const void* ct_in, const int32_t
   br.signed_digits = 0;
   br.err = ctx->d_err;
   fill_br_q(br, st);
+  br.half_y = n13_half_region(st, base, batch);
   {
     StageTimer tm(tctx, 0, s);
     FD_CUDA(bv.ops->br(br, items, bv.br_smem, s));
@@ -768,7 +787,7 @@ int tune_chunks(fdfb_ctx* ctx, SetState& st, int64_t batch, cudaStream_t s) {
 // every lift with the primes of each variant, and builds the variants.
 int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
   if (P.k != 1 || P.log2q != 64) return FDFB_EINVAL;
-  if (P.N != 256 && P.N != 1024 && P.N != 2048 && P.N != 4096) return FDFB_EINVAL;
+  if (P.N != 256 && P.N != 1024 && P.N != 2048 && P.N != 4096 && P.N != 8192) return FDFB_EINVAL;
   if (P.n < 1 || P.n > 4096) return FDFB_EINVAL;
   if (P.t < 2 || P.t > P.N) return FDFB_EINVAL;  // any t: CRT moduli need not divide q = 2N
   if (P.signed_digits || P.t_out) return FDFB_EINVAL;
@@ -829,7 +848,10 @@ int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
     if (v->br_smem > (size_t)max_smem) continue;
     FD_CUDA(ops->br_prepare(v->br_smem));
     std::vector<uint2> fwd, inv;
-    host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv, ops->family);
+    if (L == 13)
+      host::make_prime_set_n13(ops->P, ops->EL, v->S, fwd, inv);
+    else
+      host::make_prime_set(ops->P, L, ops->EL, v->S, fwd, inv, ops->family);
     FD_TRY(v->tw.ensure((fwd.size() + inv.size()) * sizeof(uint2)));
     FD_CUDA(cudaMemcpy(v->tw.p, fwd.data(), fwd.size() * sizeof(uint2), cudaMemcpyHostToDevice));
     FD_CUDA(cudaMemcpy((uint2*)v->tw.p + fwd.size(), inv.data(), inv.size() * sizeof(uint2),
@@ -947,6 +969,7 @@ cudaError_t launch_tfhe_acc(int L, int64_t batch, cudaStream_t s, const W* ct, i
     case 10: tfhe_acc_kernel<W, 10><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
     case 11: tfhe_acc_kernel<W, 11><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
     case 12: tfhe_acc_kernel<W, 12><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
+    case 13: tfhe_acc_kernel<W, 13><<<(unsigned)batch, 256, 0, s>>>(ct, n, ids, polys, n_polys, acc, err, Q); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1337,7 +1360,10 @@ int fdfb_tfhe_bootstrap(fdfb_ctx* ctx, int set_id, const void* ct_in, const int3
   br.rep = 1;
   br.signed_digits = (int)P.signed_digits;
   br.err = ctx->d_err;
-  if (st->mq.Q) fill_br_q(br, *st);
+  if (st->mq.Q) {
+    fill_br_q(br, *st);
+    br.half_y = n13_half_region(*st, base, batch);
+  }
   {
     StageTimer tm(ctx, 3, s);
     FD_CUDA(bv.ops->br(br, batch, bv.br_smem, s));
@@ -1642,7 +1668,10 @@ int fdfb_autotune(fdfb_ctx* ctx, int set_id, int64_t batch, void* cuda_stream, i
     br.rep = 1;
     br.signed_digits = (int)st->prm.signed_digits;
     br.err = ctx->d_err;
-    if (st->mq.Q) fill_br_q(br, *st);
+    if (st->mq.Q) {
+      fill_br_q(br, *st);
+      br.half_y = n13_half_region(*st, base, batch);
+    }
     float ms_v = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, s);

@@ -49,6 +49,20 @@ inline uint32_t generator(uint32_t p) {
   }
 }
 
+// Stores the blocks [2^s, 2^(s+1)) of one 2^L-entry twiddle table that the
+// last register pass of a transform with 2^EL coefficients per thread reads
+// transposed: entry 2^s + t C + c moves to 2^s + c G + t (see tw_index).
+inline void transpose_last_pass(uint2* tab, int L, int EL) {
+  const int K = (L + EL - 1) / EL, last = L - (K - 1) * EL;
+  const uint32_t G = 1u << (L - EL);
+  for (int s = L - last; s < L; ++s) {
+    const uint32_t base = 1u << s, C = base / G;
+    std::vector<uint2> blk(tab + base, tab + 2 * base);
+    for (uint32_t t = 0; t < G; ++t)
+      for (uint32_t c = 0; c < C; ++c) tab[base + c * G + t] = blk[t * C + c];
+  }
+}
+
 // Fills S (except the table pointers) and the [P][N] forward/inverse twiddle
 // tables for ring degree N = 2^L with the first P primes, for transforms that
 // keep 2^EL coefficients per thread: the blocks [2^s, 2^(s+1)) read by the
@@ -98,16 +112,52 @@ inline void make_prime_set(int P, int L, int EL, PrimeSet& S, std::vector<uint2>
       fwd[(size_t)i * N + k] = uint2{wf, shoup(wf, p)};
       inv[(size_t)i * N + k] = uint2{wi, shoup(wi, p)};
     }
-    // transpose the last-pass blocks: entry 2^s + t C + c -> 2^s + c G + t
-    const int K = (L + EL - 1) / EL, last = L - (K - 1) * EL;
-    const uint32_t G = 1u << (L - EL);
-    for (int s = L - last; s < L; ++s) {
-      const uint32_t base = 1u << s, C = base / G;
-      for (std::vector<uint2>* tab : {&fwd, &inv}) {
-        std::vector<uint2> blk(tab->begin() + (size_t)i * N + base, tab->begin() + (size_t)i * N + 2 * base);
-        for (uint32_t t = 0; t < G; ++t)
-          for (uint32_t c = 0; c < C; ++c) (*tab)[(size_t)i * N + base + c * G + t] = blk[t * C + c];
-      }
+    transpose_last_pass(&fwd[(size_t)i * N], L, EL);
+    transpose_last_pass(&inv[(size_t)i * N], L, EL);
+  }
+}
+
+// Constants and twiddle tables of the N = 2^13 transforms (fdfb_n13.cuh),
+// which run as one split stage plus two 4096-point transforms: per prime a
+// [2][4096] table for each direction whose half h holds, at 2^s + i (s < 12,
+// i < 2^s), the N = 8192 table's entry 2^(s+1) + h 2^s + i (the twiddles the
+// 8192-point transform applies to that half), with the last-pass blocks
+// transposed for 2^EL coefficients per thread, and at entry 0 (read by no
+// 4096-point pass) the split stage's twiddle, entry 1 of the 8192 table.
+// S.ninv_m is 8192^-1 2^32.
+inline void make_prime_set_n13(int P, int EL, PrimeSet& S, std::vector<uint2>& fwd, std::vector<uint2>& inv) {
+  constexpr uint32_t NF = 8192, NH = 4096;
+  std::vector<uint2> f12, i12;
+  make_prime_set(P, 12, EL, S, f12, i12, 0);
+  for (int i = 0; i < kMaxPrimes; ++i) {
+    const uint32_t p = kPrimes[i];
+    S.ninv_m[i] = (uint32_t)mulmod(inv_mod(NF % p, p), S.r32[i], p);
+    S.ninv_ms[i] = shoup(S.ninv_m[i], p);
+  }
+  fwd.assign((size_t)P * NF, uint2{0, 0});
+  inv.assign((size_t)P * NF, uint2{0, 0});
+  std::vector<uint32_t> ff(NF), fi(NF);
+  for (int i = 0; i < P; ++i) {
+    const uint32_t p = kPrimes[i];
+    const uint32_t psi = (uint32_t)powmod(generator(p), (p - 1) / (2 * NF), p);  // primitive 2N-th root
+    const uint32_t psi_inv = inv_mod(psi, p);
+    for (uint32_t k = 0; k < NF; ++k) {
+      ff[k] = (uint32_t)powmod(psi, bitrev(k, 13), p);
+      fi[k] = (uint32_t)powmod(psi_inv, bitrev(k, 13), p);
+    }
+    for (uint32_t h = 0; h < 2; ++h) {
+      uint2* hf = &fwd[((size_t)i * 2 + h) * NH];
+      uint2* hi = &inv[((size_t)i * 2 + h) * NH];
+      hf[0] = uint2{ff[1], shoup(ff[1], p)};
+      hi[0] = uint2{fi[1], shoup(fi[1], p)};
+      for (int s = 0; s < 12; ++s)
+        for (uint32_t x = 0; x < (1u << s); ++x) {
+          const uint32_t e = (2u << s) + h * (1u << s) + x;
+          hf[(1u << s) + x] = uint2{ff[e], shoup(ff[e], p)};
+          hi[(1u << s) + x] = uint2{fi[e], shoup(fi[e], p)};
+        }
+      transpose_last_pass(hf, 12, EL);
+      transpose_last_pass(hi, 12, EL);
     }
   }
 }

@@ -248,6 +248,9 @@ struct BRParams {
   // delta_half
   ModQ mq;
   uint64_t sgn_scale[8];
+  // N = 2^13 (fdfb_n13.cuh): per item [P][2 halves][2][4096] residues of the
+  // halves' inverse transforms, kept until both are done
+  uint32_t* half_y;
 };
 
 template <int L, int EL, int P, typename W, typename DT, int M = 1, bool PP = false, int KH = 1,

@@ -128,6 +128,8 @@ WORKLOADS: Dict[str, Workload] = {
     # l_boot = 6 sign rotations and one function rotation per input
     "paper_80_6": Workload("paper_80_6", 5, [Group("FDFB-80-6", 1000, 4, "uniform")]),
     "paper_80_7": Workload("paper_80_7", 6, [Group("FDFB-80-7", 456, 4, "uniform")]),
+    # N = 2^13 (split transforms): l_boot = 8 sign rotations per input
+    "paper_80_8": Workload("paper_80_8", 8, [Group("FDFB-80-8", 152, 4, "uniform")]),
     # Table 1's TFHE:80:2 through the TFHE bootstrap (one rotation)
     "paper_tfhe_80_2": Workload("paper_tfhe_80_2", 7, [Group("TFHE-80-2", 1024, 4, "round_robin",
                                                              mode="tfhe")]),
@@ -372,9 +374,8 @@ class QParamSet:
         return 2 * self.N
 
 
-# Table 1 columns with N <= 4096 (ring degree 2^13 needs more shared memory
-# per ciphertext than one SM has), and QZ, a small set of the same shape for
-# the exhaustive checks.  t is the largest plaintext modulus the paper's
+# Table 1's columns, and QZ, a small set of the same shape for the
+# exhaustive checks.  t is the largest plaintext modulus the paper's
 # correctness table gives a negligible error probability for.
 Q_PARAM_SETS: Dict[str, QParamSet] = {
     "FDFB-80-6": QParamSet("FDFB-80-6", n=700, N=2048, Q=Q1, t=64, log2Bg=11, lg=6, log2Bks=6, lks=11,
@@ -385,6 +386,10 @@ Q_PARAM_SETS: Dict[str, QParamSet] = {
                            log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 39, sigma_glwe=3.2),
     "FDFB-100-7": QParamSet("FDFB-100-7", n=1100, N=4096, Q=Q2, t=128, log2Bg=9, lg=7, log2Bks=1, lks=63,
                             log2Bpk=13, lpk=5, log2Lboot=11, lboot=6, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
+    "FDFB-80-8": QParamSet("FDFB-80-8", n=700, N=8192, Q=Q2, t=256, log2Bg=9, lg=7, log2Bks=4, lks=16,
+                           log2Bpk=13, lpk=5, log2Lboot=8, lboot=8, sigma_lwe=2.0 ** 39, sigma_glwe=3.2),
+    "FDFB-100-8": QParamSet("FDFB-100-8", n=1100, N=8192, Q=Q2, t=256, log2Bg=9, lg=7, log2Bks=1, lks=63,
+                            log2Bpk=13, lpk=5, log2Lboot=8, lboot=8, sigma_lwe=2.0 ** 41, sigma_glwe=3.2),
     "QZ": QParamSet("QZ", n=24, N=256, Q=Q1, t=8, log2Bg=11, lg=6, log2Bks=6, lks=11, log2Bpk=13, lpk=5,
                     log2Lboot=11, lboot=6,
                     sigma_lwe=2.0 ** 38, sigma_glwe=3.2),

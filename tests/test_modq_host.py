@@ -16,3 +16,15 @@ def test_modq_helpers_on_the_host(tmp_path):
                            "-o", exe, os.path.join(ROOT, "tests", "host_modq.cpp")])
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_n13_split_transforms_on_the_host(tmp_path):
+    """The N = 2^13 transforms as the kernels run them (split stage, two
+    4096-point register transforms on the half tables, joining stage), for
+    both register layouts and all three primes, against the schoolbook
+    negacyclic product mod p."""
+    exe = str(tmp_path / "host_n13")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2109_02731_gb300", "csrc"),
+                           "-o", exe, os.path.join(ROOT, "tests", "host_n13.cpp")])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
