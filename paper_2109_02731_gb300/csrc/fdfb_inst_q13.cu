@@ -15,12 +15,12 @@ struct InstN13 {
   static constexpr size_t region_bytes() {
     return (size_t)P * kN13 * 4 > XB ? (size_t)P * kN13 * 4 : XB;
   }
-  // acc | a_N | one region: exchange buffers, then the lift's stage [P][8192]
+  // d | a_N | one region: exchange buffers, then the lift's stage [P][8192]
   static size_t br_smem(int n, int, uint32_t* r1, uint32_t* ex) {
-    const size_t acc = 2 * (size_t)kN13 * 8;
+    const size_t d = 2 * (size_t)kN13 * 8;
     const size_t an = ((size_t)n * 2 + 15) & ~(size_t)15;
-    *r1 = *ex = (uint32_t)(acc + an);
-    return acc + an + region_bytes();
+    *r1 = *ex = (uint32_t)(d + an);
+    return d + an + region_bytes();
   }
   static cudaError_t br_prepare(size_t smem) {
     return cudaFuncSetAttribute(blind_rotate_n13_kernel<EL, P, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,

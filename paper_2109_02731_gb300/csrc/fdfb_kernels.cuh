@@ -248,8 +248,8 @@ struct BRParams {
   // delta_half
   ModQ mq;
   uint64_t sgn_scale[8];
-  // N = 2^13 (fdfb_n13.cuh): per item [P][2 halves][2][4096] residues of the
-  // halves' inverse transforms, kept until both are done
+  // N = 2^13 (fdfb_n13.cuh): per item global scratch, the residues of the
+  // halves' inverse transforms and the accumulator (n13_scratch_words)
   uint32_t* half_y;
 };
 

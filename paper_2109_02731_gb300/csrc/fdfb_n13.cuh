@@ -18,18 +18,26 @@
 //
 // One CTA per item runs the two halves one after the other, so a CTA holds
 // the same thread groups as at N = 4096 (one group of 4096 / E threads per
-// prime).  Shared memory: the accumulator [2][8192] words, the mask a_N,
-// and one region that is the groups' exchange buffers during the transforms
-// and the lift's staging area [P][8192] afterwards (227 KB for n <= 1536).
-// The digits of d = acc X^{-a} - acc are cut out of the accumulator as each
-// transform loads them (there is no room to keep d), and the halves' inverse
-// results wait in global memory (L2) until both exist.
+// prime).  Shared memory: d = acc X^{-a} - acc of the current step ([2][8192]
+// words, from which every transform cuts its digits), the mask a_N, and one
+// region that is the groups' exchange buffers during the transforms and the
+// lift's staging area [P][8192] afterwards (227 KB for n <= 1536).  The
+// accumulator itself lives in the item's global scratch (L2): it is read
+// once per step to form d and updated once by the lift, while d is read
+// 2 x 2 l_g times per step (every digit row, in both halves).  The halves'
+// inverse results wait there too until both exist.
 #pragma once
 #include "fdfb_kernels.cuh"
 
 namespace fdfb {
 
 constexpr int kN13 = 8192, kN13h = 4096;
+
+// 32-bit words of one item's global scratch of blind_rotate_n13_kernel.
+template <int P>
+constexpr int n13_scratch_words() {
+  return P * 4 * kN13h + 4 * kN13;
+}
 
 template <int EL>
 constexpr int n13_xwords() {
@@ -71,10 +79,12 @@ __device__ __forceinline__ void n13_join(uint32_t y0, uint32_t y1, uint2 wi, uin
 // and half, each group transforms the 2 lg digit polynomials modulo its
 // prime, sums the pointwise products with the key rows (each reduced as it
 // is formed), and transforms the two column sums back into the item's
-// global scratch (half_y: [P][2 halves][2][4096]); the joined residues of
-// all primes are lifted to the exact integer (Garner) and reduced mod Q.
+// global scratch; the joined residues of all primes are lifted to the exact
+// integer (Garner) and reduced mod Q.
 // Key rows: [n][P][2][2 lg][2][4096] words, half h of row r and column c in
-// the 4096-point last-pass order of bsk_to_ntt_n13_kernel.
+// the 4096-point last-pass order of bsk_to_ntt_n13_kernel.  Global scratch
+// per item (half_y, n13_scratch_words): [P][2 halves][2][4096] residues, then
+// the accumulator [2][8192] words.
 // ---------------------------------------------------------------------------
 template <int EL, int P, int MINB>
 __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_kernel(const BRParams prm) {
@@ -82,7 +92,7 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
   constexpr int NF = kN13, NH = kN13h, E = Y::E, G = Y::G, THREADS = P * G;
   constexpr int XW = n13_xwords<EL>();
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* acc = reinterpret_cast<uint64_t*>(smem);                    // [2][NF]
+  uint64_t* dq = reinterpret_cast<uint64_t*>(smem);                     // [2][NF] d of the step
   uint16_t* aN = reinterpret_cast<uint16_t*>(smem + 2 * NF * 8);       // [n]
   uint32_t* region = reinterpret_cast<uint32_t*>(smem + prm.smem_r1);  // [P][XW] exchange | [P][NF] stage
 
@@ -93,6 +103,9 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
   const int n = prm.n, lg = prm.lg, log2Bg = prm.log2Bg;
   const uint64_t Q = prm.mq.Q;
   const uint64_t* ct = reinterpret_cast<const uint64_t*>(prm.ct) + (ci / prm.rep) * (n + 1);
+  // the item's global scratch: half results, then the accumulator
+  uint32_t* scratch = prm.half_y + (size_t)ci * n13_scratch_words<P>();
+  uint64_t* acc = reinterpret_cast<uint64_t*>(scratch + P * 4 * NH);  // [2][NF]
 
   // the input words already lie in [0, 2N) (q = 2N)
   for (int i = tid; i < n; i += THREADS) aN[i] = (uint16_t)((uint32_t)ct[1 + i] & (2 * NF - 1));
@@ -120,13 +133,23 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
   const int bar = 1 + grp;
   const int R = 2 * lg;
   const uint32_t dmask = (1u << log2Bg) - 1;
-  uint32_t* ys = prm.half_y + ((size_t)ci * P + grp) * 4 * NH;  // this group's [2 halves][2][NH]
+  uint32_t* ys = scratch + (size_t)grp * 4 * NH;  // this group's [2 halves][2][NH]
   const size_t kblk = (size_t)R * 2 * NH;                        // words of one (step, prime, half) block
   const uint2 wfi = prm.S.tw_inv[(size_t)grp * 2 * NH];         // the split stage's inverse twiddle
   if (t == 0 && n > 0) prefetch_l2_bulk(prm.bsk + (size_t)grp * 2 * kblk, (uint32_t)(kblk * 4));
 
   for (int i = 0; i < n; ++i) {
     const int a = aN[i];
+    // d = acc X^{-a} - acc mod Q: (acc X^{-a})_j = acc_{j+a}, negated when j +
+    // a wraps past N (X^N = -1); the previous step's lift ended in a barrier,
+    // so every thread's accumulator writes are visible here
+    for (int idx = tid; idx < 2 * NF; idx += THREADS) {
+      const int c = idx >> 13, j = idx & (NF - 1);
+      const int m = (j + a) & (2 * NF - 1);
+      const uint64_t sv = acc[c * NF + (m & (NF - 1))];
+      dq[idx] = subq((m & NF) ? negq(sv, Q) : sv, acc[idx], Q);
+    }
+    __syncthreads();
     for (int h = 0; h < 2; ++h) {
       const uint2* twf = prm.S.tw_fwd + ((size_t)grp * 2 + h) * NH;
       const uint2* twi = prm.S.tw_inv + ((size_t)grp * 2 + h) * NH;
@@ -141,15 +164,8 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
       for (int r = 0; r < R; ++r) {
         const int cc = r >= lg ? 1 : 0;
         const int sh = (r - cc * lg) * log2Bg;
-        const uint64_t* ac = acc + cc * NF;
-        // digit l of coefficient j of d_cc: (acc X^{-a})_j = acc_{j+a}, negated
-        // when j + a wraps past N (X^N = -1)
-        auto digit = [&](int j) -> uint32_t {
-          const int m = (j + a) & (2 * NF - 1);
-          const uint64_t sv = ac[m & (NF - 1)];
-          const uint64_t rv = (m & NF) ? negq(sv, Q) : sv;
-          return (uint32_t)(subq(rv, ac[j], Q) >> sh) & dmask;
-        };
+        const uint64_t* dc = dq + cc * NF;  // digit l of coefficient j of d_cc
+        auto digit = [&](int j) -> uint32_t { return (uint32_t)(dc[j] >> sh) & dmask; };
         uint32_t v[E];
         n13_fwd_half<EL>(v, h, digit, t, twf, p, xb, bar, z);
 #pragma unroll
