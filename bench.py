@@ -88,6 +88,12 @@ KERNEL_TRAFFIC = {
     # FDFB-80-6 sign rotation (variant 3, one CTA per SM): a 384-item capture
     # (three waves) read 1.2074 GB
     ("FDFB-80-6", 3): (1.2074e9 / 3, 152, "ncu capture of a 384-item sign rotation (3 waves), FDFB-80-6"),
+    # FDFB-80-8 (N = 2^13, variant 0): a 152-item capture of the small-case
+    # driver with n = 64 steps read 302 MB and wrote 5.04 GB; both grow with
+    # the steps (key rows and the items' scratch, once per step), so a wave
+    # of n = 700 steps moves 700 / 64 of that
+    ("FDFB-80-8", 0): ((301.879e6 + 5042.725e6) * 700 / 64, 152,
+                       "ncu capture of a 152-item, 64-step sign rotation (probe/n13_rotate.cu), scaled to 700 steps"),
 }
 
 

@@ -290,13 +290,13 @@ size_t mq_scratch_words(const SetState& st, int64_t batch) {
   return (size_t)batch * (lb * ((N + 1) + 4 * N + 2 * N) + 2 * N + (N + 1) + 2 * (n + 1));
 }
 // 32-bit words of one item's BRParams::half_y at N = 2^13 (half results
-// [P][2][2][4096] and the accumulator [2][8192] words, for the largest prime
-// count of the set's variants), else 0.
+// [P][2][2][KH][4096] and the accumulator [2][8192] words, the largest over
+// the set's variants), else 0.
 size_t n13_half_words(const SetState& st) {
   if (st.L != 13) return 0;
-  int P = 0;
-  for (const auto& v : st.var) P = std::max(P, v->ops->P);
-  return (size_t)P * 4 * 4096 + 4 * 8192;
+  int pk = 0;
+  for (const auto& v : st.var) pk = std::max(pk, v->ops->P * v->ops->key_halves);
+  return (size_t)pk * 4 * 4096 + 4 * 8192;
 }
 // The half-result region of a prime-modulus scratch area laid out for `batch`
 // inputs (after the 64-bit words above), or nullptr below N = 2^13.

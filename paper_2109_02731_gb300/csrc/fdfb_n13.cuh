@@ -34,9 +34,9 @@ namespace fdfb {
 constexpr int kN13 = 8192, kN13h = 4096;
 
 // 32-bit words of one item's global scratch of blind_rotate_n13_kernel.
-template <int P>
+template <int P, int KH = 1>
 constexpr int n13_scratch_words() {
-  return P * 4 * kN13h + 4 * kN13;
+  return P * 4 * KH * kN13h + 4 * kN13;
 }
 
 template <int EL>
@@ -81,13 +81,18 @@ __device__ __forceinline__ void n13_join(uint32_t y0, uint32_t y1, uint2 wi, uin
 // is formed), and transforms the two column sums back into the item's
 // global scratch; the joined residues of all primes are lifted to the exact
 // integer (Garner) and reduced mod Q.
-// Key rows: [n][P][2][2 lg][2][4096] words, half h of row r and column c in
-// the 4096-point last-pass order of bsk_to_ntt_n13_kernel.  Global scratch
-// per item (half_y, n13_scratch_words): [P][2 halves][2][4096] residues, then
-// the accumulator [2][8192] words.
+// Key rows: [n][P][2][2 lg][2][KH][4096] words, half h of row r, column c
+// and key half kh in the 4096-point last-pass order of bsk_to_ntt_n13_kernel.
+// Global scratch per item (half_y, n13_scratch_words): [P][2 halves][2][KH]
+// [4096] residues, then the accumulator [2][8192] words.
+// KH = 2 (two primes): every key word K is split into centred 32-bit halves,
+// K = K_lo + 2^32 K_hi, both sharing the digits' transforms; each half's
+// product sum (at most 2 l N (B - 1) 2^31 < 2^57) lifts exactly from two
+// primes and acc += X_lo + 2^32 X_hi mod Q.
 // ---------------------------------------------------------------------------
-template <int EL, int P, int MINB>
+template <int EL, int P, int MINB, int KH = 1>
 __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_kernel(const BRParams prm) {
+  static_assert(KH == 1 || P == 2, "split keys: two primes");
   using Y = Layout<12, EL>;
   constexpr int NF = kN13, NH = kN13h, E = Y::E, G = Y::G, THREADS = P * G;
   constexpr int XW = n13_xwords<EL>();
@@ -104,8 +109,8 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
   const uint64_t Q = prm.mq.Q;
   const uint64_t* ct = reinterpret_cast<const uint64_t*>(prm.ct) + (ci / prm.rep) * (n + 1);
   // the item's global scratch: half results, then the accumulator
-  uint32_t* scratch = prm.half_y + (size_t)ci * n13_scratch_words<P>();
-  uint64_t* acc = reinterpret_cast<uint64_t*>(scratch + P * 4 * NH);  // [2][NF]
+  uint32_t* scratch = prm.half_y + (size_t)ci * n13_scratch_words<P, KH>();
+  uint64_t* acc = reinterpret_cast<uint64_t*>(scratch + P * 4 * KH * NH);  // [2][NF]
 
   // the input words already lie in [0, 2N) (q = 2N)
   for (int i = tid; i < n; i += THREADS) aN[i] = (uint16_t)((uint32_t)ct[1 + i] & (2 * NF - 1));
@@ -133,8 +138,8 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
   const int bar = 1 + grp;
   const int R = 2 * lg;
   const uint32_t dmask = (1u << log2Bg) - 1;
-  uint32_t* ys = scratch + (size_t)grp * 4 * NH;  // this group's [2 halves][2][NH]
-  const size_t kblk = (size_t)R * 2 * NH;                        // words of one (step, prime, half) block
+  uint32_t* ys = scratch + (size_t)grp * 4 * KH * NH;  // this group's [2 halves][2][KH][NH]
+  const size_t kblk = (size_t)R * 2 * KH * NH;              // words of one (step, prime, half) block
   const uint2 wfi = prm.S.tw_inv[(size_t)grp * 2 * NH];         // the split stage's inverse twiddle
   if (t == 0 && n > 0) prefetch_l2_bulk(prm.bsk + (size_t)grp * 2 * kblk, (uint32_t)(kblk * 4));
 
@@ -158,9 +163,11 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
         if (h == 0) prefetch_l2_bulk(kb + kblk, (uint32_t)(kblk * 4));
         else if (i + 1 < n) prefetch_l2_bulk(prm.bsk + ((size_t)(i + 1) * P + grp) * 2 * kblk, (uint32_t)(kblk * 4));
       }
-      uint32_t macc[2][E];
+      uint32_t macc[KH][2][E];
 #pragma unroll
-      for (int k = 0; k < E; ++k) { macc[0][k] = 0; macc[1][k] = 0; }
+      for (int kh = 0; kh < KH; ++kh)
+#pragma unroll
+        for (int k = 0; k < E; ++k) { macc[kh][0][k] = 0; macc[kh][1][k] = 0; }
       for (int r = 0; r < R; ++r) {
         const int cc = r >= lg ? 1 : 0;
         const int sh = (r - cc * lg) * log2Bg;
@@ -170,46 +177,54 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
         n13_fwd_half<EL>(v, h, digit, t, twf, p, xb, bar, z);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const uint4* kp = reinterpret_cast<const uint4*>(kb + ((size_t)r * 2 + c) * NH) + t;
 #pragma unroll
-          for (int q4 = 0; q4 < E / 4; ++q4) {
-            const uint4 kk = ldg_stream(kp + q4 * G);
-            const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+          for (int kh = 0; kh < KH; ++kh) {
+            const uint4* kp = reinterpret_cast<const uint4*>(kb + (((size_t)r * 2 + c) * KH + kh) * NH) + t;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              // v < 4p, K < p: v K < 2^62, reduced below 2p; the sum stays in [0, 2p)
-              const uint32_t mm = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);
-              const uint32_t s2 = macc[c][q4 * 4 + u] + mm + z;
-              macc[c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+            for (int q4 = 0; q4 < E / 4; ++q4) {
+              const uint4 kk = ldg_stream(kp + q4 * G);
+              const uint32_t kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                // v < 4p, K < p: v K < 2^62, reduced below 2p; the sum stays in [0, 2p)
+                const uint32_t mm = redc((uint64_t)v[q4 * 4 + u] * kv[u], p, pneg);
+                const uint32_t s2 = macc[kh][c][q4 * 4 + u] + mm + z;
+                macc[kh][c][q4 * 4 + u] = umin32(s2, s2 - 2 * p + z);
+              }
             }
           }
         }
       }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) v[k] = macc[c][k];
-        ntt_inv<12, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+        for (int kh = 0; kh < KH; ++kh) {
+          uint32_t v[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) ys[(h * 2 + c) * NH + Y::j_of(0, t, k)] = csub(v[k], p);
+          for (int k = 0; k < E; ++k) v[k] = macc[kh][c][k];
+          ntt_inv<12, EL, Y::K - 1>(v, t, twi, p, xb, bar, z);
+#pragma unroll
+          for (int k = 0; k < E; ++k) ys[((h * 2 + c) * KH + kh) * NH + Y::j_of(0, t, k)] = csub(v[k], p);
+        }
       }
     }
     __syncthreads();  // every group is done with its exchange buffer: the region becomes the stage
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int ck = 0; ck < 2 * KH; ++ck) {  // column c, key half kh
+      const int c = ck / KH, kh = ck - c * KH;
       // the same thread wrote ys at these positions: no barrier needed for it
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const int j = Y::j_of(0, t, k);
-        n13_join(ys[c * NH + j], ys[(2 + c) * NH + j], wfi, p, z, region + grp * NF, j);
+        n13_join(ys[(c * KH + kh) * NH + j], ys[((2 + c) * KH + kh) * NH + j], wfi, p, z, region + grp * NF, j);
       }
       __syncthreads();
       for (int j = tid; j < NF; j += THREADS) {
         uint32_t x[P];
 #pragma unroll
         for (int g = 0; g < P; ++g) x[g] = region[g * NF + j];
-        acc[c * NF + j] = addq(acc[c * NF + j], modq_lift(garner_exact<P>(x, prm.S), prm.mq), Q);
+        __int128 X = garner_exact<P>(x, prm.S);
+        if (kh) X *= (__int128)1 << 32;
+        acc[c * NF + j] = addq(acc[c * NF + j], modq_lift(X, prm.mq), Q);
       }
       __syncthreads();
     }
@@ -227,11 +242,13 @@ __global__ void __launch_bounds__(P * (1 << (12 - EL)), MINB) blind_rotate_n13_k
 }
 
 // Canonical GGSW rows [n][2 lg][2][8192] words mod Q to the transform domain
-// of blind_rotate_n13_kernel: out[i][g][h][r][c][.] = half h of
-// NTT(centred(bsk[i][r][c]) mod p_g) * 8192^-1 * 2^32 mod p_g, output j = t E
-// + k of the 4096-point last pass stored at (k / 4) 4G + 4t + k % 4.  With R =
-// 1 it converts the key limbs of rlwe_encrypt_q_n13_kernel.
-template <int EL, int P>
+// of blind_rotate_n13_kernel: out[i][g][h][r][c][kh][.] = half h of
+// NTT(centred(bsk[i][r][c]) mod p_g) * 8192^-1 * 2^32 mod p_g (KH = 2: of the
+// centred 32-bit halves K_lo = (int32) K and K_hi = (K >> 32) + [K_lo < 0]
+// of the centred word K), output j = t E + k of the 4096-point last pass
+// stored at (k / 4) 4G + 4t + k % 4.  With R = 1 and KH = 1 it converts the
+// key limbs of rlwe_encrypt_q_n13_kernel.
+template <int EL, int P, int KH = 1>
 __global__ void __launch_bounds__(P * (1 << (12 - EL)))
 bsk_to_ntt_n13_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out, uint64_t Q) {
   using Y = Layout<12, EL>;
@@ -246,13 +263,20 @@ bsk_to_ntt_n13_kernel(PrimeSet S, const void* bsk, int R, uint32_t* out, uint64_
   const uint32_t p = S.p[grp];
   const uint64_t* src = reinterpret_cast<const uint64_t*>(bsk) + row * 2 * NF;
   for (int c = 0; c < 2; ++c) {
-    for (int h = 0; h < 2; ++h) {
-      const uint2* twf = S.tw_fwd + ((size_t)grp * 2 + h) * NH;
+    for (int h = 0; h < 2 * KH; ++h) {
+      const int hh = h / KH, kh = h - hh * KH;  // spectrum half, key half
+      const uint2* twf = S.tw_fwd + ((size_t)grp * 2 + hh) * NH;
       uint32_t v[E];
-      n13_fwd_half<EL>(v, h,
-                       [&](int j) -> uint32_t { return mod_centred<uint64_t>(centre_q(src[c * NF + j], Q), S, grp); },
+      n13_fwd_half<EL>(v, hh,
+                       [&](int j) -> uint32_t {
+                         const uint64_t u = centre_q(src[c * NF + j], Q);
+                         if (KH == 1) return mod_centred<uint64_t>(u, S, grp);
+                         if (kh == 0) return mod_centred<uint32_t>((uint32_t)u, S, grp);
+                         const int64_t hi = ((int64_t)u >> 32) + (((uint32_t)u >> 31) ? 1 : 0);
+                         return mod_centred<uint64_t>((uint64_t)hi, S, grp);
+                       },
                        t, twf, p, exch + grp * XW, 1 + grp, S.zero);
-      uint32_t* dst = out + ((((size_t)i * P + grp) * 2 + h) * R + r) * 2 * NH + (size_t)c * NH;
+      uint32_t* dst = out + (((((size_t)i * P + grp) * 2 + hh) * R + r) * 2 + c) * KH * NH + (size_t)kh * NH;
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const uint32_t y = csub(csub(v[k], 2 * p), p);

@@ -90,7 +90,7 @@ def run_q(F, torch, ctx, sid, ps, cts, ids, debug=True):
 def test_registers_with_the_n13_variants(ctx, reduced):
     ps, sid, _ = reduced
     cur, count, _ = ctx.variant_info(sid)
-    assert count == 2 and 0 <= cur < count
+    assert count == 3 and 0 <= cur < count
 
 
 def test_full_geometry_matches_the_oracle(F, torch_cuda, ctx, OQ, reduced):
@@ -193,3 +193,22 @@ def test_full_size_keygen_and_decryption(F, torch_cuda, ctx, OQ):
     ctx.autotune(sid, batch)
     out, _ = run_q(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
     assert np.array_equal(out, outs[0])
+
+
+def test_fdfb_100_8_full_size_decrypts(F, torch_cuda, ctx, OQ):
+    """FDFB:100:8 at full size (n = 1100, l_ks = 63 binary key-switch digits,
+    keys generated on the GPU): every output decrypts to f(m)."""
+    ps = S.Q_PARAM_SETS["FDFB-100-8"]
+    kr = S.q_key_randomness(ps, 68)
+    sid = ctx.register(ps)
+    ctx.keys_generate(sid, kr)
+    tables = S.q_lut_tables(ps, 68, 2)
+    for f in tables:
+        ctx.lut_setup(sid, f)
+    batch = 16
+    mr = S.q_message_randomness(ps, 69, batch)
+    cts = OQ.encrypt_messages(ps, kr.s, mr)
+    ids = S.lut_assignment(69, batch, 2, "uniform")
+    out, _ = run_q(F, torch_cuda, ctx, sid, ps, cts, ids, debug=False)
+    dec = [OQ.decrypt(ps, kr.s, o) for o in out]
+    assert dec == [int(tables[i][m]) for m, i in zip(mr.m, ids)]
