@@ -286,7 +286,8 @@ int fdfb_bootstrap_debug(fdfb_ctx* ctx, int set_id, const void* ct_in, const int
  *       q = 2^32 and 170 at N = 4096, q = 2^64;
  *       prime-modulus sets: l_boot (7N + 1) + 3N + 1 + 2(n + 1) 64-bit
  *       words, e.g. 44 ciphertexts for FDFB-80-6 (n = 700, N = 2048,
- *       l_boot = 6).
+ *       l_boot = 6); at N = 8192 also l_boot x 98,304 32-bit words of
+ *       blind-rotation scratch, e.g. 4 ciphertexts for FDFB-80-8.
  *     Larger batches return FDFB_EINVAL.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call

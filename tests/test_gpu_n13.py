@@ -141,6 +141,35 @@ def test_tfhe_bootstrap_matches_the_oracle(F, torch_cuda, ctx, OQ, reduced):
     ctx.set_variant(sid, base[0])
 
 
+def test_no_allocation_entry_at_n13(F, torch_cuda, ctx, reduced):
+    """fdfb_bootstrap_noalloc at N = 8192 (the blind rotation's per-item
+    scratch carved from the fixed array too): its cap is 32 MiB over one
+    input's intermediates, and at the cap it returns fdfb_bootstrap's bits on
+    two calls in a row."""
+    torch = torch_cuda
+    ps, sid, _ = reduced
+    N, n, lb = ps.N, ps.n, ps.lboot
+    per_input = (lb * (7 * N + 1) + 3 * N + 1 + 2 * (n + 1)) * 8 + lb * (4 * 4 * 4096 + 4 * 8192) * 4
+    cap = ctx.noalloc_max_batch(sid)
+    assert cap == (32 << 20) // per_input
+    lid = ctx.lut_setup(sid, (np.arange(ps.t) * 5 + 1) % ps.t)
+    rng = np.random.default_rng(70)
+    for call in range(2):
+        cts = rng.integers(0, ps.q, (cap, n + 1), dtype=np.int64).astype(np.uint64)
+        ids = torch.full((cap,), lid, dtype=torch.int32, device="cuda")
+        ct_d = F.to_device_words(ps, cts)
+        ref = torch.empty_like(ct_d)
+        got = torch.empty_like(ct_d)
+        ctx.bootstrap(sid, ct_d, ids, ref)
+        ctx.bootstrap_noalloc(sid, ct_d, ids, got)
+        ctx.sync()
+        assert torch.equal(ref, got), f"call {call}"
+    ct_d = torch.zeros((cap + 1, n + 1), dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FDFBError):
+        ctx.bootstrap_noalloc(sid, ct_d, torch.full((cap + 1,), lid, dtype=torch.int32, device="cuda"),
+                              torch.empty_like(ct_d))
+
+
 def test_shared_memory_bounds_n(F, ctx):
     """At N = 8192 the accumulator stays in shared memory: n = 1536 registers,
     n = 1537 leaves no layout that fits and is refused."""
