@@ -130,6 +130,7 @@ WORKLOADS: Dict[str, Workload] = {
     "paper_80_7": Workload("paper_80_7", 6, [Group("FDFB-80-7", 456, 4, "uniform")]),
     # N = 2^13 (split transforms): l_boot = 8 sign rotations per input
     "paper_80_8": Workload("paper_80_8", 8, [Group("FDFB-80-8", 152, 4, "uniform")]),
+    "paper_100_8": Workload("paper_100_8", 9, [Group("FDFB-100-8", 152, 4, "uniform")]),
     # Table 1's TFHE:80:2 through the TFHE bootstrap (one rotation)
     "paper_tfhe_80_2": Workload("paper_tfhe_80_2", 7, [Group("TFHE-80-2", 1024, 4, "round_robin",
                                                              mode="tfhe")]),
