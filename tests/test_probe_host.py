@@ -47,3 +47,19 @@ def test_tcgen05_f16_mma_compiles_for_sm103a():
 
 def test_probe_builds():
     assert os.path.exists(B.build_probe())
+
+
+def test_n13_rotation_driver_builds_for_sm103a(tmp_path):
+    """The small-case driver of the N = 2^13 blind rotation (used for profiler
+    captures on a case of a few hundred MB) builds against the library's own
+    kernel header."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2109_02731_gb300")
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O1", "-std", "c++17",
+                        "--expt-relaxed-constexpr", "-I", os.path.join(root, "include"), "-I",
+                        os.path.join(pkg, "csrc"), "-o", str(tmp_path / "n13_rotate"),
+                        os.path.join(pkg, "probe", "n13_rotate.cu")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
