@@ -825,7 +825,7 @@ int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
   st->logt = ilog2(P.t);
   st->tout = (int)P.t;
   st->logtout = st->logt;
-  st->mq = ModQ{Q, c, kbits, modq_folds(Q, c, kbits)};
+  st->mq = ModQ{Q, c, kbits, modq_folds(Q, c, kbits), modq_folds64(Q, c, kbits)};
   st->lboot = (int)P.lboot;
   const uint64_t h = (uint64_t)(((unsigned __int128)Q + P.t) / (2 * (uint64_t)P.t));  // round(Q / 2t)
   st->delta_q = (uint64_t)(((unsigned __int128)Q + P.t / 2) / P.t);                // round(Q / t)
@@ -843,6 +843,8 @@ int register_q(fdfb_ctx* ctx, const fdfb_params& P, int* set_id_out) {
     if (ops->key_halves == 2 && !host::lift_is_exact(ops->P, 2.0L * P.lg * P.N * (B - 1) * ldexpl(1.0L, 31)))
       continue;
     if (ops->key_halves == 1 && !host::lift_is_exact(ops->P, br_max)) continue;
+    // two primes with whole key words reduce their lift in 64 bits (k <= 60)
+    if (ops->P == 2 && ops->key_halves == 1 && kbits > 60) continue;
     auto v = std::make_unique<Variant>();
     v->ops = ops;
     v->br_smem = ops->br_smem((int)P.n, (int)P.lg, &v->br_r1, &v->br_ex);

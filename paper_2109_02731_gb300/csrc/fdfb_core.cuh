@@ -177,6 +177,7 @@ struct ModQ {
   uint64_t c;  // Q = 2^k - c
   int k;
   int folds;   // folds that bring any value below 2^98 under 2Q (modq_lift)
+  int folds64; // folds that bring any value below 2^62 under 2Q (modq_lift64)
 };
 
 // The fold count of modq_lift: the smallest f with F^f(2^98 - 1) < 2Q for
@@ -184,6 +185,18 @@ struct ModQ {
 // 5 for Q_4).
 inline int modq_folds(uint64_t Q, uint64_t c, int k) {
   unsigned __int128 ub = (((unsigned __int128)1) << 98) - 1;
+  int f = 0;
+  while (ub >= (unsigned __int128)2 * Q && f < 16) {
+    ub = (ub >> k) * c + ((((unsigned __int128)1) << k) - 1);
+    ++f;
+  }
+  return f;
+}
+
+// The fold count of modq_lift64: the same map started from 2^62 - 1 (3 for
+// Q_4; only used where registration has shown |x| < 2^59).
+inline int modq_folds64(uint64_t Q, uint64_t c, int k) {
+  unsigned __int128 ub = (((unsigned __int128)1) << 62) - 1;
   int f = 0;
   while (ub >= (unsigned __int128)2 * Q && f < 16) {
     ub = (ub >> k) * c + ((((unsigned __int128)1) << k) - 1);
@@ -220,6 +233,16 @@ FD_HD uint64_t modq_lift(__int128 x, const ModQ& m) {
   for (int f = 0; f < m.folds; ++f) y = (y >> m.k) * m.c + (y & lo_mask);
   const uint64_t r = (uint64_t)y;
   return r >= m.Q ? r - m.Q : r;
+}
+// Residue of a lifted sum that fits 64 bits, |x| < 2^59 (two primes at k =
+// 32): x + Q 2^(60-k) lies in (0, 2^62) (Q 2^(60-k) is in [2^59, 2^60)), and
+// m.folds64 folds of the 64-bit value bring it below 2Q.  Needs k <= 60.
+FD_HD uint64_t modq_lift64(int64_t x, const ModQ& m) {
+  const uint64_t lo_mask = (1ull << m.k) - 1;
+  uint64_t y = (uint64_t)(x + (int64_t)(m.Q << (60 - m.k)));
+#pragma unroll 1
+  for (int f = 0; f < m.folds64; ++f) y = (y >> m.k) * m.c + (y & lo_mask);
+  return y >= m.Q ? y - m.Q : y;
 }
 FD_HD uint64_t addq(uint64_t a, uint64_t b, uint64_t Q) {
   const uint64_t s = a + b;  // < 2Q < 2^64

@@ -341,7 +341,8 @@ __device__ __forceinline__ int stage_slot(int g, int c) {
 // phase (bounded wait, FDFB_ETIMEOUT on expiry).
 // MQ: prime modulus Q (Table 1): d = acc X^{-a} - acc mod Q, exact digits
 // (l log2 B >= log2 Q), the products lifted to the exact integer and reduced
-// mod Q; the input ciphertext is already modulo 2N.
+// mod Q; the input ciphertext is already modulo 2N.  With P = 2 and whole
+// key words (KH = 1) the lift fits 64 bits (k = 32: |X| < 2^55).
 template <int L, int EL, int P, typename W, typename DT, bool WIDE = false,
           int MINB = br_min_blocks(P * (1 << (L - EL))), int M = 1, bool LZ = false, bool PP = false,
           int KH = 1, bool SG = false, bool TK = false, bool MQ = false>
@@ -656,7 +657,11 @@ blind_rotate_kernel(const BRParams prm) {
             const __int128 Xh = garner_exact<P>(x, prm.S);
             X += h == 0 ? Xh : Xh * ((__int128)1 << 32);
           }
-          acc[c * N + j] = (W)addq(acc[c * N + j], modq_lift(X, prm.mq), Qm);
+          // two primes, whole key words: registration admits this layout only
+          // where the sum lifts exactly from two primes, |X| < 2^59, so the
+          // 64-bit reduction serves (k = 32, Q_4)
+          const uint64_t r = (P == 2 && KH == 1) ? modq_lift64((int64_t)X, prm.mq) : modq_lift(X, prm.mq);
+          acc[c * N + j] = (W)addq(acc[c * N + j], r, Qm);
           continue;
         }
         W add = 0;

@@ -84,7 +84,7 @@ int main(int argc, char** argv) {
   const size_t smem = d + an + (size_t)P * kN13 * 4;
   prm.rep = 1;
   prm.err = derr;
-  prm.mq = ModQ{Q, c, 63, modq_folds(Q, c, 63)};
+  prm.mq = ModQ{Q, c, 63, modq_folds(Q, c, 63), modq_folds64(Q, c, 63)};
   for (int i = 0; i < 8; ++i) prm.sgn_scale[i] = g() % Q;
   prm.half_y = dy;
   auto k = blind_rotate_n13_kernel<EL, P, 1>;

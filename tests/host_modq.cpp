@@ -29,7 +29,7 @@ int main() {
   std::mt19937_64 g(2109);
   long bad = 0;
   for (int i = 0; i < 4; ++i) {
-    ModQ m{Qs[i][0], Qs[i][1], ks[i], modq_folds(Qs[i][0], Qs[i][1], ks[i])};
+    ModQ m{Qs[i][0], Qs[i][1], ks[i], modq_folds(Qs[i][0], Qs[i][1], ks[i]), 0};
     if (m.folds != want_folds[i]) {
       printf("k=%d: %d folds, expected %d\n", m.k, m.folds, want_folds[i]);
       ++bad;
@@ -52,6 +52,20 @@ int main() {
       bad += mulq(a, b, m) != (uint64_t)(((unsigned __int128)a * b) % m.Q);
       bad += addq(a, b, m.Q) != (uint64_t)(((unsigned __int128)a + b) % m.Q);
       bad += subq(a, b, m.Q) != ref_mod((__int128)a - (__int128)b, m.Q);
+    }
+  }
+  // the 64-bit lift reduction of the two-prime layouts (k <= 60, |x| < 2^59)
+  for (int i = 2; i < 4; ++i) {
+    ModQ m{Qs[i][0], Qs[i][1], ks[i], modq_folds(Qs[i][0], Qs[i][1], ks[i]),
+           modq_folds64(Qs[i][0], Qs[i][1], ks[i])};
+    const int64_t lim = ((int64_t)1 << 59) - 1;
+    const int64_t edges[] = {0, 1, -1, lim, -lim, (int64_t)m.Q, -(int64_t)m.Q, (int64_t)m.Q - 1};
+    for (int64_t x : edges) bad += modq_lift64(x, m) != ref_mod(x, m.Q);
+    for (int it = 0; it < 300000; ++it) {
+      const int bits = 1 + (int)(g() % 59);
+      int64_t x = (int64_t)(g() & (((uint64_t)1 << bits) - 1));
+      if (g() & 1) x = -x;
+      bad += modq_lift64(x, m) != ref_mod(x, m.Q);
     }
   }
   // Garner's exact lift with two and three 30-bit primes
