@@ -476,3 +476,19 @@ def test_fdfb_noiseless_phase_within_the_rounding_of_delta():
             else:
                 assert abs(dev) <= 2 * ps.t
             assert OQ.decrypt(ps, kr.s, out) == int(f[m])
+
+
+def test_poly_mul_by_a_monomial_at_n_8192():
+    """At Table 1's largest ring degree (FDFB:80:8, 100:8) the oracle's
+    schoolbook product by +-X^k equals multiplication by X^k in
+    Z_Q[X]/(X^N + 1): coefficient j receives p[j - k], negated where j - k
+    wraps below 0 (X^N = -1)."""
+    N = 8192
+    rng = np.random.default_rng(3)
+    p = rng.integers(0, 2 ** 62, N, dtype=np.uint64) % np.uint64(Q)
+    for k, sgn in ((0, 1), (1, 1), (4095, Q - 1), (4096, 1), (8191, Q - 1)):
+        mono = np.zeros(N, dtype=np.uint64)
+        mono[k] = sgn
+        got = [int(x) for x in OQ.poly_mul(Q, mono, p)]
+        want = [(sgn * (int(p[j - k]) if j >= k else Q - int(p[j - k + N]))) % Q for j in range(N)]
+        assert got == want, k
