@@ -170,6 +170,37 @@ def test_no_allocation_entry_at_n13(F, torch_cuda, ctx, reduced):
                               torch.empty_like(ct_d))
 
 
+def test_mixed_call_with_an_n13_group(F, torch_cuda, OQ, ctx, reduced):
+    """fdfb_bootstrap_mixed with an N = 8192 group beside a small prime set
+    (their pipelines run concurrently on the library's side streams, each in
+    its own scratch): every group returns the bits of its own
+    fdfb_bootstrap call."""
+    torch = torch_cuda
+    ps, sid, _ = reduced
+    qz = S.Q_PARAM_SETS["QZ"]
+    kr = S.q_key_randomness(qz, 81)
+    K = OQ.QKeys(qz, kr)
+    sq = ctx.register(qz)
+    ctx.keys_upload(sq, K.bsk, K.pk, K.ksk)
+    lq = ctx.lut_setup(sq, np.arange(qz.t)[::-1] % qz.t)
+    l8 = ctx.lut_setup(sid, (np.arange(ps.t) * 3 + 2) % ps.t)
+    rng = np.random.default_rng(82)
+    groups, refs = [], []
+    for s_id, pset, lid, count in ((sid, ps, l8, 3), (sq, qz, lq, 40)):
+        cts = rng.integers(0, pset.q, (count, pset.n + 1), dtype=np.int64).astype(np.uint64)
+        ct_d = F.to_device_words(pset, cts)
+        ids = torch.full((count,), lid, dtype=torch.int32, device="cuda")
+        ref = torch.empty_like(ct_d)
+        ctx.bootstrap(s_id, ct_d, ids, ref)
+        ctx.sync()
+        refs.append(ref)
+        groups.append((s_id, ct_d, ids, torch.empty_like(ct_d)))
+    ctx.bootstrap_mixed(groups)
+    ctx.sync()
+    for (s_id, _, _, out), ref in zip(groups, refs):
+        assert torch.equal(out, ref), f"set {s_id}"
+
+
 def test_shared_memory_bounds_n(F, ctx):
     """At N = 8192 the accumulator stays in shared memory: n = 1536 registers,
     n = 1537 leaves no layout that fits and is refused."""
